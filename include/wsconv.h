@@ -1,0 +1,169 @@
+/*
+ * wsconv.h -- C ABI of the GB300 (sm_103a) library for the FFT convolution with weakly singular
+ * kernels of Tiwari, Pandey, Paul & Anand (arXiv 2107.03958), and its use as the matvec of the
+ * Lippmann-Schwinger Nystrom solver.
+ *
+ * Operation (Sec. 2.1, eq. (An)): for grid data u_j = u(j/n), j in G_n = [0,n)^2, on D = [0,1]^2,
+ *     (A_n u)(x_j) = sum_{k in F_n} ghat(k) hat u_{e,n}(k) e^{2 pi i k.j/M},   M = n b,
+ * with u_e the zero extension of u to the period-b square and hat u_{e,n} its trapezoidal Fourier
+ * coefficients.  Equivalently A_n u = crop_n(ifft2(ghat (.) fft2(zero-extend_M(u)))) where ifft2
+ * carries 1/M^2.  ghat(k) = int_{B_a(0)} g(y) e^{-2 pi i k.y/b} dy (eq. (bk), (ghat), Sec. 2.2).
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are row-major, first index <-> x1.  A density batch is batch x n x n.
+ *   - Complex data are interleaved (re, im) pairs of the plan's real type.
+ *   - Data pointers (u, mask, out, workspace, m, f, x) are DEVICE pointers owned by the caller,
+ *     unless the name says host.  The plan owns ghat, the twiddle table and a default workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  conv_apply is
+ *     asynchronous; ls_solve synchronises at restart boundaries.
+ *   - No exception or abort crosses the ABI.  On failure a status is returned and
+ *     conv_last_error() gives a message (thread-local).
+ */
+#ifndef WSCONV_H
+#define WSCONV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CONV_OK = 0,
+    CONV_EINVAL = 1,          /* bad argument, or a (b, a) pair outside eq. (io)'s admissible range */
+    CONV_EUNSUPPORTED = 2,    /* valid but not implemented: e.g. M = n b odd or with a prime factor > 5,
+                                 or a transform length beyond one CTA's shared memory */
+    CONV_ENOMEM = 3,          /* device allocation failed */
+    CONV_ECUDA = 4,           /* a CUDA call or kernel launch failed */
+    CONV_ETIMEOUT = 5,        /* a bounded device-side wait gave up */
+    CONV_ENOTCONVERGED = 6,   /* GMRES hit its iteration limit */
+    CONV_ENONFINITE = 7       /* NaN/Inf detected */
+} conv_status;
+
+/* Kernel families (Sec. 2.2).  g(x) = scale * log|x|, scale * |x|^gamma (gamma > -2, 2 gamma an
+ * integer), or scale * (i/4) H0^(1)(kappa |x|).  The paper's Laplace kernel is LOG with
+ * scale = -1/(2 pi). */
+typedef enum { CONV_K_LOG = 0, CONV_K_POW = 1, CONV_K_HELMHOLTZ = 2 } conv_kernel_family;
+
+typedef struct {
+    int family;      /* conv_kernel_family */
+    double gamma;    /* CONV_K_POW exponent */
+    double kappa;    /* CONV_K_HELMHOLTZ wavenumber (> 0) */
+    double scale;    /* multiplies g; 0 is read as 1 */
+} conv_kernel;
+
+/* Arithmetic of the transform passes.  ghat is always built in FP64; an FP32 plan keeps an FP32
+ * copy.  FP64 meets 1e-12 relative L-infinity against the FP64 oracle; FP32 about 1e-6. */
+typedef enum { CONV_P_FP64 = 0, CONV_P_FP32 = 1 } conv_precision;
+
+/* Input/output types.  R2R needs a real ghat (LOG, POW). */
+typedef enum {
+    CONV_IO_R2R = 0,   /* real u -> real A_n u */
+    CONV_IO_R2C = 1,   /* real u -> complex A_n u (any kernel) */
+    CONV_IO_C2C = 2    /* complex u -> complex A_n u (any kernel) */
+} conv_io;
+
+typedef struct conv_plan_s *conv_plan_t;
+
+/* Build a plan: validates the period b = period_num/period_den and the truncation radius a
+ * (eq. (io), Sec. 2.1: sqrt 2 <= a <= b - 1 for support D), computes the FP64 moment table
+ * ghat(|k1|, |k2|) for 0 <= k1, k2 <= M/2 on the GPU (Sec. 2.2; the Helmholtz k = 0 value with the
+ * sign of its 2/(kappa pi) term corrected), the twiddle table, and allocates a workspace for
+ * batch_max densities.
+ *   trunc_a <= 0 selects the midpoint (sqrt 2 + b - 1)/2 and requires b >= 1 + sqrt 2.
+ *   An explicit trunc_a > 0 is accepted as given (the caller vouches that the density's support
+ *   keeps B_a(x) inside the period for all x in D).
+ * Returns CONV_EINVAL for bad arguments, CONV_EUNSUPPORTED for M odd, M with a prime factor > 5, a
+ * transform beyond shared memory, or POW with 2 gamma not an integer. */
+conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den, int n,
+                      double trunc_a, conv_precision precision, conv_io io, int batch_max,
+                      conv_plan_t *plan);
+
+/* Bytes of workspace conv_apply needs for `batch` densities (the n x (M/2+1) or n x M spectra). */
+conv_status conv_workspace_size(conv_plan_t plan, int batch, size_t *bytes);
+
+/* out = A_n(u . mask) for `batch` densities (Sec. 2.1, eq. (An)).
+ *   u:    batch x n x n, real (R2R, R2C) or complex (C2C), plan precision.
+ *   mask: NULL or an n x n real array (plan precision) shared by the batch; it multiplies u at the
+ *         load (the Fourier-smoothed indicator chi^n psi of Sec. 2.4, or a contrast).
+ *   out:  batch x n x n, real (R2R) or complex (R2C, C2C); must not alias u.
+ *   workspace: NULL (use the plan's, valid for batch <= batch_max) or conv_workspace_size bytes.
+ * Asynchronous on `stream`.  Three kernel launches. */
+conv_status conv_apply(conv_plan_t plan, const void *u, const void *mask, void *out, int batch,
+                       void *workspace, void *stream);
+
+/* Generalised apply used by the Lippmann-Schwinger operator (Sec. 3.3, eq. (descretls)):
+ *     out = beta * u + alpha * A_n(u . mask)
+ * with complex alpha (alpha_re, alpha_im) and real beta; C2C/R2C plans only when beta != 0 needs a
+ * complex u.  conv_apply is the case alpha = 1, beta = 0. */
+conv_status conv_apply_axpby(conv_plan_t plan, const void *u, const void *mask, void *out,
+                             int batch, double alpha_re, double alpha_im, double beta,
+                             void *workspace, void *stream);
+
+typedef struct {
+    int n, M, period_num, period_den;
+    double b, a;
+    int precision, io, family, batch_max;
+    int nstages;
+    int radices[16];
+    size_t ghat_bytes, workspace_bytes;
+    int threads_rows, groups_rows, threads_cols, groups_cols;
+} conv_plan_info;
+
+conv_status conv_get_info(conv_plan_t plan, conv_plan_info *info);
+
+/* Copy the FP64 moment table ghat(|k1|, |k2|), 0 <= k1, k2 <= M/2, to host memory:
+ * (M/2+1)^2 doubles (real kernels) or (M/2+1)^2 interleaved complex doubles (Helmholtz),
+ * index [k2 * (M/2+1) + k1].  Synchronous. */
+conv_status conv_ghat_to_host(conv_plan_t plan, double *host_out);
+
+void conv_destroy(conv_plan_t plan);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *conv_last_error(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Lippmann-Schwinger solve (Sec. 3.3, eq. (lippsch) discretised as eq. (descretls)):
+ *     u + kappa^2 A_n(m u) = f   on G_n,
+ * by restarted GMRES with matrix-free matvecs (Arnoldi by classical Gram-Schmidt with one
+ * re-orthogonalisation, Givens rotations, all in FP64 on the device).
+ *   plan: a C2C Helmholtz plan (its precision is the matvec precision of the inner solve).
+ *   m:    n x n real contrast m = 1 - mu, FP64, device.
+ *   f:    n x n complex128 right-hand side (u_inc on the grid), device.
+ *   x:    n x n complex128, device: initial guess on entry (ignored when opts->zero_guess),
+ *         solution on exit.
+ * With an FP32 plan and opts->refine != 0 the solve is mixed precision: an outer FP64 residual
+ * r = f - L x (FP64 matvec built internally), an inner FP32-matvec GMRES on L d = r to
+ * opts->inner_tol, x += d, until ||r|| / ||f|| <= opts->tol.
+ * Returns CONV_ENOTCONVERGED (with info filled) when max_iters is reached. */
+typedef struct {
+    int restart;       /* Krylov dimension per cycle (default 50) */
+    int max_iters;     /* total matvec limit (default 2000) */
+    double tol;        /* relative residual target ||f - L x||_2 / ||f||_2 (default 1e-10) */
+    int refine;        /* mixed precision: 1 = FP64 iterative refinement around an FP32 inner solve */
+    double inner_tol;  /* inner relative tolerance for refinement (default 1e-5) */
+    int zero_guess;    /* 1: start from x = 0 */
+} ls_opts;
+
+typedef struct {
+    int iters;            /* matvecs in the Krylov iterations */
+    int restarts;         /* GMRES cycles */
+    int refinements;      /* outer refinement steps (mixed precision) */
+    double rel_residual;  /* final true relative residual (FP64 operator) */
+} ls_info;
+
+conv_status ls_solve(conv_plan_t plan, const double *m, const void *f, void *x, const ls_opts *opts,
+                     ls_info *info, void *stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Roofline denominators measured on the running GPU (no counterpart in the paper):
+ *   copy:  bytes read + written per second by a grid-stride float4 copy of `bytes` bytes;
+ *   fma:   FP64 and FP32 fused multiply-add throughput (flops/s, an FMA counts 2).
+ * Synchronous; allocates and frees its own buffers. */
+conv_status conv_measure_peaks(size_t bytes, double *copy_gbs, double *fp64_tflops,
+                               double *fp32_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WSCONV_H */

@@ -1,0 +1,96 @@
+"""ctypes view of the C ABI in include/wsconv.h (argument marshalling only).
+
+The CUDA library must have been built (``paper_2107_03958_gb300.build.build()``); there is no CPU
+fallback, and loading fails loudly when the library is missing.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+_lib = None
+
+
+class ConvKernel(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int), ("gamma", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("scale", ctypes.c_double)]
+
+
+class ConvPlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("M", ctypes.c_int), ("period_num", ctypes.c_int),
+                ("period_den", ctypes.c_int), ("b", ctypes.c_double), ("a", ctypes.c_double),
+                ("precision", ctypes.c_int), ("io", ctypes.c_int), ("family", ctypes.c_int),
+                ("batch_max", ctypes.c_int), ("nstages", ctypes.c_int),
+                ("radices", ctypes.c_int * 16), ("ghat_bytes", ctypes.c_size_t),
+                ("workspace_bytes", ctypes.c_size_t), ("threads_rows", ctypes.c_int),
+                ("groups_rows", ctypes.c_int), ("threads_cols", ctypes.c_int),
+                ("groups_cols", ctypes.c_int)]
+
+
+class LsOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("tol", ctypes.c_double),
+                ("refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("zero_guess", ctypes.c_int)]
+
+
+class LsInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+
+# every exported symbol of include/wsconv.h with its prototype
+PROTOTYPES = {
+    "conv_plan": (ctypes.c_int, [ctypes.POINTER(ConvKernel), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_void_p)]),
+    "conv_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "conv_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "conv_apply_axpby": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "conv_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ConvPlanInfo)]),
+    "conv_ghat_to_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "conv_destroy": (None, [ctypes.c_void_p]),
+    "conv_last_error": (ctypes.c_char_p, []),
+    "ls_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.POINTER(LsOpts), ctypes.POINTER(LsInfo), ctypes.c_void_p]),
+    "conv_measure_peaks": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
+}
+
+STATUS = {0: "CONV_OK", 1: "CONV_EINVAL", 2: "CONV_EUNSUPPORTED", 3: "CONV_ENOMEM", 4: "CONV_ECUDA",
+          5: "CONV_ETIMEOUT", 6: "CONV_ENOTCONVERGED", 7: "CONV_ENONFINITE"}
+
+
+class ConvError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library (no fallback: raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("CUDA library %s is missing: run paper_2107_03958_gb300.build.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in PROTOTYPES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != 0:
+        raise ConvError(status, load().conv_last_error().decode(errors="replace"))

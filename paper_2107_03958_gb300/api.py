@@ -1,0 +1,164 @@
+"""Torch-facing binding of the C ABI (argument marshalling only; every step runs in the CUDA library).
+
+    plan = ConvPlan("log", n=1024, period=3, precision="fp32", io="r2r", batch_max=16, scale=-1/(2*pi))
+    out = plan.apply(u)            # u: CUDA tensor (B, n, n) or (n, n)
+    x, info = ls_solve(plan_c2c_helmholtz, m, f)
+
+Names follow the paper: n grid points per side on D = [0,1]^2, period b, truncation radius a,
+moments ghat (Sec. 2.1-2.2).
+"""
+import ctypes
+import math
+from fractions import Fraction
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+FAMILY = {"log": 0, "pow": 1, "helmholtz": 2, "helm": 2}
+PRECISION = {"fp64": 0, "fp32": 1}
+IO = {"r2r": 0, "r2c": 1, "c2c": 2}
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class ConvPlan:
+    """A plan for A_n on an n x n grid with period b (Sec. 2.1, eq. (An))."""
+
+    def __init__(self, kernel="log", n=64, period=3, trunc_a=0.0, precision="fp64", io="r2r",
+                 batch_max=1, gamma=0.0, kappa=0.0, scale=1.0, device=None):
+        self._lib = N.load()
+        if device is not None:
+            torch.cuda.set_device(device)
+        frac = Fraction(period).limit_denominator(64)
+        self.kernel, self.n, self.b = kernel, int(n), float(frac)
+        self.precision, self.io = precision, io
+        self.period = (frac.numerator, frac.denominator)
+        k = N.ConvKernel(FAMILY[kernel], float(gamma), float(kappa), float(scale))
+        h = ctypes.c_void_p()
+        N.check(self._lib.conv_plan(ctypes.byref(k), frac.numerator, frac.denominator, int(n),
+                                    float(trunc_a), PRECISION[precision], IO[io], int(batch_max),
+                                    ctypes.byref(h)))
+        self._h = h
+        self.info = self._info()
+        self.M, self.a = self.info.M, self.info.a
+        self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.cplx_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.batch_max = int(batch_max)
+
+    def _info(self):
+        inf = N.ConvPlanInfo()
+        N.check(self._lib.conv_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.conv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def in_dtype(self):
+        return self.cplx_dtype if self.io == "c2c" else self.real_dtype
+
+    def out_dtype(self):
+        return self.real_dtype if self.io == "r2r" else self.cplx_dtype
+
+    def workspace_bytes(self, batch):
+        b = ctypes.c_size_t()
+        N.check(self._lib.conv_workspace_size(self._h, int(batch), ctypes.byref(b)))
+        return b.value
+
+    def _check_grid(self, t, dtype, name):
+        if not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.dtype != dtype:
+            raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.shape[-2:] != (self.n, self.n):
+            raise ValueError("%s must end in (%d, %d)" % (name, self.n, self.n))
+
+    def apply(self, u, mask=None, out=None, workspace=None, stream=None, alpha=1.0, beta=0.0):
+        """out = beta u + alpha A_n(u * mask), batched over the leading dimension."""
+        self._check_grid(u, self.in_dtype(), "u")
+        batch = 1 if u.dim() == 2 else int(np.prod(u.shape[:-2]))
+        if out is None:
+            out = torch.empty(u.shape, dtype=self.out_dtype(), device=u.device)
+        self._check_grid(out, self.out_dtype(), "out")
+        if mask is not None:
+            self._check_grid(mask, self.real_dtype, "mask")
+            if mask.dim() != 2:
+                raise ValueError("mask is one n x n array shared by the batch")
+        ws = None
+        if workspace is not None:
+            if workspace.numel() * workspace.element_size() < self.workspace_bytes(batch):
+                raise ValueError("workspace too small")
+            ws = ctypes.c_void_p(workspace.data_ptr())
+        a = complex(alpha)
+        N.check(self._lib.conv_apply_axpby(
+            self._h, ctypes.c_void_p(u.data_ptr()),
+            ctypes.c_void_p(mask.data_ptr()) if mask is not None else None,
+            ctypes.c_void_p(out.data_ptr()), batch, a.real, a.imag, float(beta), ws,
+            _stream_ptr(stream)))
+        return out
+
+    __call__ = apply
+
+    def ghat_quadrant(self):
+        """FP64 moment table ghat(|k1|, |k2|), 0 <= k1, k2 <= M/2, as numpy [k2, k1]."""
+        h = self.M // 2 + 1
+        cplx = self.kernel in ("helmholtz", "helm")
+        buf = np.zeros((h, h), dtype=np.complex128 if cplx else np.float64)
+        N.check(self._lib.conv_ghat_to_host(self._h, buf.ctypes.data_as(ctypes.c_void_p)))
+        return buf
+
+
+def ls_solve(plan, m, f, x=None, restart=50, max_iters=2000, tol=1e-10, refine=False,
+             inner_tol=1e-5, stream=None):
+    """Solve u + kappa^2 A_n(m u) = f (Sec. 3.3, eq. (descretls)) by restarted GMRES.
+    m: (n, n) float64 CUDA tensor; f: (n, n) complex128 CUDA tensor; x: optional initial guess."""
+    if plan.io != "c2c" or plan.kernel not in ("helmholtz", "helm"):
+        raise ValueError("ls_solve needs a C2C Helmholtz plan")
+    plan._check_grid(m, torch.float64, "m")
+    plan._check_grid(f, torch.complex128, "f")
+    zero = x is None
+    if x is None:
+        x = torch.zeros_like(f)
+    plan._check_grid(x, torch.complex128, "x")
+    o = N.LsOpts(int(restart), int(max_iters), float(tol), int(bool(refine)), float(inner_tol), int(zero))
+    inf = N.LsInfo()
+    st = plan._lib.ls_solve(plan.handle, ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+                            ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), ctypes.byref(inf),
+                            _stream_ptr(stream))
+    info = {"iters": inf.iters, "restarts": inf.restarts, "refinements": inf.refinements,
+            "rel_residual": inf.rel_residual, "status": N.STATUS.get(st, st)}
+    if st not in (0, 6):
+        N.check(st)
+    return x, info
+
+
+def measure_peaks(nbytes=1 << 30):
+    """Measured HBM copy GB/s and FP64/FP32 FMA TFLOP/s on the current GPU."""
+    lib = N.load()
+    c, d, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    N.check(lib.conv_measure_peaks(int(nbytes), ctypes.byref(c), ctypes.byref(d), ctypes.byref(s)))
+    return {"copy_gbs": c.value, "fp64_tflops": d.value, "fp32_tflops": s.value}
+
+
+def default_scale(kernel):
+    """The paper's Laplace kernel is -(1/2pi) log|x|."""
+    return -1.0 / (2.0 * math.pi) if kernel == "log" else 1.0

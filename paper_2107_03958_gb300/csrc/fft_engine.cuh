@@ -1,0 +1,252 @@
+// fft_engine.cuh -- shared-memory Stockham FFT used by the three convolution passes.
+//
+// A CTA holds G independent length-L transforms in shared memory, each worked on by `tpt`
+// threads.  Every radix-R stage (R in {2,3,4,5,8}) is the self-sorting Stockham step
+//   y[(j / Ns) Ns R + (j mod Ns) + p Ns] = sum_q w^{pq}_R  t_q x[j + q L/R],
+//   t_q = exp(-/+ 2 pi i q (j mod Ns) / (Ns R)),  j in [0, L/R),
+// so the result comes out in natural order.  A stage reads its R inputs into registers, meets a
+// barrier, then writes its R outputs, so one buffer suffices.  Shared memory is padded by one
+// element per 128 bytes, which makes both the unit-stride reads and the stride-Ns writes
+// bank-conflict free for Ns = 1 and Ns >= 32.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wsc {
+
+template <typename T> struct cvec;
+template <> struct cvec<float> { typedef float2 t; };
+template <> struct cvec<double> { typedef double2 t; };
+
+template <typename V> __host__ __device__ __forceinline__ V cmk(decltype(V::x) a, decltype(V::x) b) { V r; r.x = a; r.y = b; return r; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) { return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return cmk<V>(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename V> __device__ __forceinline__ V rot(V x) { return INV ? cmk<V>(-x.y, x.x) : cmk<V>(x.y, -x.x); }
+
+// padding: one element per 128 bytes
+template <typename T> struct pad_shift;
+template <> struct pad_shift<float> { static const int v = 4; };   // 16 x 8 B
+template <> struct pad_shift<double> { static const int v = 3; };  // 8 x 16 B
+template <typename T> __device__ __forceinline__ int pidx(int e) { return e + (e >> pad_shift<T>::v); }
+template <typename T> __host__ __device__ inline int padded_len(int L) { return L + (L >> (sizeof(T) == 4 ? 4 : 3)) + 1; }
+
+#define WSC_MAX_STAGES 24
+
+// Per-length stage table, passed by value as a kernel parameter.
+struct FFTDesc {
+    int L;
+    int nst;
+    int R[WSC_MAX_STAGES];
+    int Ns[WSC_MAX_STAGES];
+    int tws[WSC_MAX_STAGES];                  // L / (Ns R): twiddle table stride
+    unsigned long long mag[WSC_MAX_STAGES];  // ceil(2^40 / Ns): j / Ns == (j * mag) >> 40 for j < 2^24, Ns < 2^16
+};
+
+// ---------------------------------------------------------------- small DFTs
+template <bool INV, typename V> __device__ __forceinline__ void dft2(V *x) {
+    V a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft3(V *x) {
+    typedef decltype(V::x) T;
+    const T h = (T)0.8660254037844386467637231707529362;  // sin(2 pi / 3)
+    V t = cadd(x[1], x[2]);
+    V d = csub(x[1], x[2]);
+    V y0 = cadd(x[0], t);
+    V m = cmk<V>(x[0].x - (T)0.5 * t.x, x[0].y - (T)0.5 * t.y);
+    V r = cscale(rot<INV>(d), h);
+    x[0] = y0;
+    x[1] = cadd(m, r);
+    x[2] = csub(m, r);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft4(V *x) {
+    V a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
+    V a2 = cadd(x[1], x[3]), a3 = rot<INV>(csub(x[1], x[3]));
+    x[0] = cadd(a0, a2);
+    x[2] = csub(a0, a2);
+    x[1] = cadd(a1, a3);
+    x[3] = csub(a1, a3);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft5(V *x) {
+    typedef decltype(V::x) T;
+    const T c1 = (T)0.3090169943749474241022934171828191;   // cos(2 pi/5)
+    const T c2 = (T)-0.8090169943749474241022934171828191;  // cos(4 pi/5)
+    const T s1 = (T)0.9510565162951535721164393333793821;   // sin(2 pi/5)
+    const T s2 = (T)0.5877852522924731291687059546390728;   // sin(4 pi/5)
+    V t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
+    V d1 = csub(x[1], x[4]), d2 = csub(x[2], x[3]);
+    V y0 = cadd(x[0], cadd(t1, t2));
+    V a1 = cmk<V>(x[0].x + c1 * t1.x + c2 * t2.x, x[0].y + c1 * t1.y + c2 * t2.y);
+    V a2 = cmk<V>(x[0].x + c2 * t1.x + c1 * t2.x, x[0].y + c2 * t1.y + c1 * t2.y);
+    V b1 = cmk<V>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+    V b2 = cmk<V>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+    V r1 = rot<INV>(b1), r2 = rot<INV>(b2);
+    x[0] = y0;
+    x[1] = cadd(a1, r1);
+    x[4] = csub(a1, r1);
+    x[2] = cadd(a2, r2);
+    x[3] = csub(a2, r2);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft8(V *x) {
+    typedef decltype(V::x) T;
+    const T r2 = (T)0.7071067811865475244008443621048490;
+    V e[4] = {x[0], x[2], x[4], x[6]};
+    V o[4] = {x[1], x[3], x[5], x[7]};
+    dft4<INV>(e);
+    dft4<INV>(o);
+    // o[k] *= w8^{k} (forward w8 = e^{-i pi/4}; inverse conjugate)
+    V o1 = INV ? cmk<V>((o[1].x - o[1].y) * r2, (o[1].x + o[1].y) * r2)
+               : cmk<V>((o[1].x + o[1].y) * r2, (o[1].y - o[1].x) * r2);
+    V o2 = rot<INV>(o[2]);
+    V o3 = INV ? cmk<V>((-o[3].x - o[3].y) * r2, (o[3].x - o[3].y) * r2)
+               : cmk<V>((o[3].y - o[3].x) * r2, (-o[3].x - o[3].y) * r2);
+    x[0] = cadd(e[0], o[0]);
+    x[4] = csub(e[0], o[0]);
+    x[1] = cadd(e[1], o1);
+    x[5] = csub(e[1], o1);
+    x[2] = cadd(e[2], o2);
+    x[6] = csub(e[2], o2);
+    x[3] = cadd(e[3], o3);
+    x[7] = csub(e[3], o3);
+}
+
+template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x) {
+    if (R == 2) dft2<INV>(x);
+    else if (R == 3) dft3<INV>(x);
+    else if (R == 4) dft4<INV>(x);
+    else if (R == 5) dft5<INV>(x);
+    else dft8<INV>(x);
+}
+
+// ---------------------------------------------------------------- one Stockham stage
+// Every thread owns exactly E elements of a length-L transform (L = E * tpt); a radix-R stage
+// gives it E/R butterflies j = lt + b tpt.  tw[t] = exp(-2 pi i t / L).
+template <typename T, int E, int R, bool INV>
+__device__ __forceinline__ void stockham_stage(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P, int s,
+                                               const typename cvec<T>::t *__restrict__ tw, int lt,
+                                               int tpt)
+{
+    typedef typename cvec<T>::t V;
+    constexpr int NB = E / R;
+    const int nbf = NB * tpt;
+    const int Ns = __ldg(&P->Ns[s]), tws = __ldg(&P->tws[s]);
+    const unsigned long long mg = __ldg(&P->mag[s]);
+    V v[NB][R];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = lt + b * tpt;
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[b][q] = buf[pidx<T>(j + q * nbf)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = lt + b * tpt;
+        const int jq = (int)(((unsigned long long)j * mg) >> 40);
+        const int k = j - jq * Ns;
+        if (Ns > 1) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                V w = __ldg(&tw[q * k * tws]);
+                if (INV) w.y = -w.y;
+                v[b][q] = cmul(v[b][q], w);
+            }
+        }
+        dftR<R, INV>(v[b]);
+        const int base = jq * Ns * R + k;
+#pragma unroll
+        for (int p = 0; p < R; ++p) buf[pidx<T>(base + p * Ns)] = v[b][p];
+    }
+    __syncthreads();
+}
+
+// Generic stage for lengths without an exact per-thread split (E = 0 below): up to GMAXE elements
+// per thread, butterflies guarded by j < L/R.
+#define WSC_GMAXE 24
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void stockham_stage_guarded(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P, int s,
+                                                       const typename cvec<T>::t *__restrict__ tw, int lt,
+                                                       int tpt)
+{
+    typedef typename cvec<T>::t V;
+    constexpr int NB = WSC_GMAXE / R;
+    const int nbf = __ldg(&P->L) / R;
+    const int Ns = __ldg(&P->Ns[s]), tws = __ldg(&P->tws[s]);
+    const unsigned long long mg = __ldg(&P->mag[s]);
+    V v[NB][R];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = lt + b * tpt;
+        if (j < nbf) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[b][q] = buf[pidx<T>(j + q * nbf)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = lt + b * tpt;
+        if (j < nbf) {
+            const int jq = (int)(((unsigned long long)j * mg) >> 40);
+            const int k = j - jq * Ns;
+            if (Ns > 1) {
+#pragma unroll
+                for (int q = 1; q < R; ++q) {
+                    V w = __ldg(&tw[q * k * tws]);
+                    if (INV) w.y = -w.y;
+                    v[b][q] = cmul(v[b][q], w);
+                }
+            }
+            dftR<R, INV>(v[b]);
+            const int base = jq * Ns * R + k;
+#pragma unroll
+            for (int p = 0; p < R; ++p) buf[pidx<T>(base + p * Ns)] = v[b][p];
+        }
+    }
+    __syncthreads();
+}
+
+// Radices a given E supports: R must divide E (E = 0: the guarded generic stage takes any R).
+template <int E, int R> struct radix_ok { static const bool v = E == 0 || (E % R) == 0; };
+
+template <typename T, int E, int R, bool INV, bool OK = radix_ok<E, R>::v> struct stage_call;
+template <typename T, int E, int R, bool INV> struct stage_call<T, E, R, INV, true> {
+    static __device__ __forceinline__ void run(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P, int s,
+                                               const typename cvec<T>::t *__restrict__ tw, int lt, int tpt)
+    {
+        if constexpr (E == 0) stockham_stage_guarded<T, R, INV>(buf, P, s, tw, lt, tpt);
+        else stockham_stage<T, E, R, INV>(buf, P, s, tw, lt, tpt);
+    }
+};
+template <typename T, int E, int R, bool INV> struct stage_call<T, E, R, INV, false> {
+    static __device__ __forceinline__ void run(typename cvec<T>::t *, const FFTDesc *__restrict__, int,
+                                               const typename cvec<T>::t *__restrict__, int, int) {}
+};
+
+// Whole transform (unnormalised).  All threads of the CTA must call it (barriers inside).  The
+// host only builds radix sequences whose radices divide E.
+template <typename T, int E, bool INV>
+__device__ __forceinline__ void fft_smem(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
+                                         const typename cvec<T>::t *__restrict__ tw, int lt, int tpt)
+{
+    const int nst = __ldg(&P->nst);
+    for (int s = 0; s < nst; ++s) {
+        switch (__ldg(&P->R[s])) {
+        case 8: stage_call<T, E, 8, INV>::run(buf, P, s, tw, lt, tpt); break;
+        case 4: stage_call<T, E, 4, INV>::run(buf, P, s, tw, lt, tpt); break;
+        case 2: stage_call<T, E, 2, INV>::run(buf, P, s, tw, lt, tpt); break;
+        case 3: stage_call<T, E, 3, INV>::run(buf, P, s, tw, lt, tpt); break;
+        default: stage_call<T, E, 5, INV>::run(buf, P, s, tw, lt, tpt); break;
+        }
+    }
+}
+
+}  // namespace wsc

@@ -1,0 +1,243 @@
+// plan.cu -- conv_plan / conv_apply and the rest of the C ABI's host side (Sec. 2.1, eq. (io), (An)).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wsconv_internal.h"
+
+namespace wsc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+conv_status fail(conv_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+conv_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return CONV_ECUDA;
+}
+
+size_t spectrum_elems(const conv_plan_s *p)
+{
+    return (size_t)(p->io == CONV_IO_R2R ? p->h : p->M) * p->n;
+}
+
+static conv_status upload_twiddles(conv_plan_s *p)
+{
+    const int L = p->M;
+    const long double PI_L = 3.141592653589793238462643383279502884L;
+    if (p->prec == CONV_P_FP64) {
+        std::vector<double> h(2 * (size_t)L);
+        for (int t = 0; t < L; ++t) {
+            long double ang = 2.0L * PI_L * (long double)t / (long double)L;
+            h[2 * t] = (double)cosl(ang);
+            h[2 * t + 1] = (double)-sinl(ang);
+        }
+        if (cudaMalloc(&p->tw, h.size() * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CONV_ENOMEM, "cudaMalloc of the twiddle table failed");
+        }
+        WSC_CUDA(cudaMemcpy(p->tw, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> h(2 * (size_t)L);
+        for (int t = 0; t < L; ++t) {
+            long double ang = 2.0L * PI_L * (long double)t / (long double)L;
+            h[2 * t] = (float)cosl(ang);
+            h[2 * t + 1] = (float)-sinl(ang);
+        }
+        if (cudaMalloc(&p->tw, h.size() * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CONV_ENOMEM, "cudaMalloc of the twiddle table failed");
+        }
+        WSC_CUDA(cudaMemcpy(p->tw, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return CONV_OK;
+}
+
+static size_t elem_bytes(const conv_plan_s *p) { return p->prec == CONV_P_FP64 ? 16 : 8; }
+
+}  // namespace wsc
+
+using namespace wsc;
+
+extern "C" {
+
+const char *conv_last_error(void) { return g_last_error.c_str(); }
+
+void conv_destroy(conv_plan_t p)
+{
+    if (!p) return;
+    if (p->ghat64) cudaFree(p->ghat64);
+    if (p->ghat32) cudaFree(p->ghat32);
+    if (p->tw) cudaFree(p->tw);
+    if (p->fft_dev) cudaFree(p->fft_dev);
+    if (p->ws) cudaFree(p->ws);
+    if (p->fp64_twin) conv_destroy(p->fp64_twin);
+    delete p;
+}
+
+conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den, int n,
+                      double trunc_a, conv_precision precision, conv_io io, int batch_max,
+                      conv_plan_t *plan)
+{
+    g_last_error.clear();
+    if (!plan) return fail(CONV_EINVAL, "plan output pointer is NULL");
+    *plan = nullptr;
+    if (!kernel) return fail(CONV_EINVAL, "kernel is NULL");
+    if (n < 1) return fail(CONV_EINVAL, "n must be >= 1");
+    if (period_num < 1 || period_den < 1) return fail(CONV_EINVAL, "period must be positive");
+    if ((long long)n * period_num % period_den != 0)
+        return fail(CONV_EINVAL, "M = n * b must be an integer");
+    long long Mll = (long long)n * period_num / period_den;
+    if (Mll <= n) return fail(CONV_EINVAL, "period b must exceed 1");
+    if (Mll > (1 << 24)) return fail(CONV_EUNSUPPORTED, "M too large");
+    if (precision != CONV_P_FP64 && precision != CONV_P_FP32)
+        return fail(CONV_EINVAL, "unknown precision");
+    if (io != CONV_IO_R2R && io != CONV_IO_R2C && io != CONV_IO_C2C)
+        return fail(CONV_EINVAL, "unknown io mode");
+    if (batch_max < 1) return fail(CONV_EINVAL, "batch_max must be >= 1");
+    const int fam = kernel->family;
+    if (fam != CONV_K_LOG && fam != CONV_K_POW && fam != CONV_K_HELMHOLTZ)
+        return fail(CONV_EINVAL, "unknown kernel family");
+    if (fam == CONV_K_HELMHOLTZ && !(kernel->kappa > 0.0))
+        return fail(CONV_EINVAL, "Helmholtz kernel needs kappa > 0");
+    if (fam == CONV_K_HELMHOLTZ && io == CONV_IO_R2R)
+        return fail(CONV_EINVAL, "Helmholtz kernel has a complex ghat: use R2C or C2C");
+    if (fam == CONV_K_POW) {
+        if (!(kernel->gamma > -2.0)) return fail(CONV_EINVAL, "|x|^gamma needs gamma > -2");
+        double tg = 2.0 * kernel->gamma;
+        if (std::fabs(tg - std::round(tg)) > 1e-12)
+            return fail(CONV_EUNSUPPORTED, "|x|^gamma moments need 2*gamma integer");
+    }
+    const int M = (int)Mll;
+    if (M % 2) return fail(CONV_EUNSUPPORTED, "M = n b must be even");
+    const double b = (double)period_num / period_den;
+    double a = trunc_a;
+    if (!(a > 0.0)) {
+        if (b - 1.0 < std::sqrt(2.0))
+            return fail(CONV_EINVAL, "period b < 1 + sqrt 2 admits no default truncation radius; pass trunc_a");
+        a = 0.5 * (std::sqrt(2.0) + b - 1.0);
+    }
+    conv_plan_s *p = new conv_plan_s();
+    p->kern = *kernel;
+    p->pnum = period_num;
+    p->pden = period_den;
+    p->n = n;
+    p->M = M;
+    p->h = M / 2 + 1;
+    p->b = b;
+    p->a = a;
+    p->prec = precision;
+    p->io = io;
+    p->batch_max = batch_max;
+    p->complex_ghat = fam == CONV_K_HELMHOLTZ;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(CONV_ECUDA, "no CUDA device");
+    }
+    if (M < 4) {
+        delete p;
+        return fail(CONV_EUNSUPPORTED, "transform length M = n b must be at least 4");
+    }
+    conv_status rc = select_transform(p);
+    if (rc == CONV_OK) {
+        if (cudaMalloc(&p->fft_dev, sizeof(FFTDesc)) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(CONV_ENOMEM, "cudaMalloc of the stage table failed");
+        } else if (cudaMemcpy(p->fft_dev, &p->fft, sizeof(FFTDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "stage table upload");
+        }
+    }
+    if (rc == CONV_OK) rc = upload_twiddles(p);
+    if (rc == CONV_OK) rc = build_ghat(p);
+    if (rc == CONV_OK) {
+        p->ws_bytes = spectrum_elems(p) * elem_bytes(p) * (size_t)batch_max;
+        if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(CONV_ENOMEM, "cudaMalloc of the workspace failed");
+        }
+    }
+    if (rc != CONV_OK) {
+        conv_destroy(p);
+        return rc;
+    }
+    *plan = p;
+    return CONV_OK;
+}
+
+conv_status conv_workspace_size(conv_plan_t p, int batch, size_t *bytes)
+{
+    if (!p || !bytes || batch < 0) return fail(CONV_EINVAL, "bad argument");
+    *bytes = spectrum_elems(p) * elem_bytes(p) * (size_t)batch;
+    return CONV_OK;
+}
+
+conv_status conv_apply_axpby(conv_plan_t p, const void *u, const void *mask, void *out, int batch,
+                             double alpha_re, double alpha_im, double beta, void *workspace,
+                             void *stream)
+{
+    if (!p) return fail(CONV_EINVAL, "plan is NULL");
+    if (batch < 0) return fail(CONV_EINVAL, "batch must be >= 0");
+    if (batch == 0) return CONV_OK;
+    if (!u || !out) return fail(CONV_EINVAL, "u and out must be device pointers");
+    if (u == out) return fail(CONV_EINVAL, "out must not alias u");
+    if (p->io == CONV_IO_R2R && alpha_im != 0.0)
+        return fail(CONV_EINVAL, "a real-to-real plan needs a real alpha");
+    if (batch > 65535) return fail(CONV_EINVAL, "batch must be <= 65535");
+    void *ws = workspace;
+    if (!ws) {
+        if (batch > p->batch_max)
+            return fail(CONV_EINVAL, "batch exceeds the plan's batch_max; pass a workspace");
+        ws = p->ws;
+    }
+    return launch_pipeline(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws,
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+conv_status conv_apply(conv_plan_t p, const void *u, const void *mask, void *out, int batch,
+                       void *workspace, void *stream)
+{
+    return conv_apply_axpby(p, u, mask, out, batch, 1.0, 0.0, 0.0, workspace, stream);
+}
+
+conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
+{
+    if (!p || !info) return fail(CONV_EINVAL, "bad argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n = p->n;
+    info->M = p->M;
+    info->period_num = p->pnum;
+    info->period_den = p->pden;
+    info->b = p->b;
+    info->a = p->a;
+    info->precision = p->prec;
+    info->io = p->io;
+    info->family = p->kern.family;
+    info->batch_max = p->batch_max;
+    info->nstages = p->fft.nst;
+    for (int s = 0; s < p->fft.nst && s < 16; ++s) info->radices[s] = p->fft.R[s];
+    info->ghat_bytes = p->ghat_bytes;
+    info->workspace_bytes = p->ws_bytes;
+    info->threads_rows = p->rows.tpt;
+    info->groups_rows = p->rows.groups;
+    info->threads_cols = p->cols.tpt;
+    info->groups_cols = p->cols.groups;
+    return CONV_OK;
+}
+
+conv_status conv_ghat_to_host(conv_plan_t p, double *host_out)
+{
+    if (!p || !host_out) return fail(CONV_EINVAL, "bad argument");
+    WSC_CUDA(cudaMemcpy(host_out, p->ghat64, p->ghat_bytes, cudaMemcpyDeviceToHost));
+    return CONV_OK;
+}
+
+}  // extern "C"

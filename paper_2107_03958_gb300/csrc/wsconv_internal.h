@@ -1,0 +1,78 @@
+// wsconv_internal.h -- plan object and helpers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/wsconv.h"
+#include "fft_engine.cuh"
+
+struct conv_plan_s;
+
+namespace wsc {
+
+// Error message of the last failing call on this thread.
+void set_error(const std::string &msg);
+conv_status fail(conv_status st, const std::string &msg);
+conv_status cuda_fail(cudaError_t e, const char *what);
+
+#define WSC_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t _e = (call);                                    \
+        if (_e != cudaSuccess) return ::wsc::cuda_fail(_e, #call);  \
+    } while (0)
+
+// Threads-per-CTA bound of the pass kernels for E complex elements per thread (E = 0: generic
+// guarded stages): keeps the E values in registers.
+template <typename T, int E> struct maxt { static const int v = (E == 0 || (int)(2 * sizeof(T) * E) > 160) ? 512 : 1024; };
+
+template <typename T, int E>
+conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
+                         double are, double aim, double beta, void *ws, cudaStream_t st);
+template <typename T, int E> conv_status set_attrs(int smem);
+
+// Launch shape of one pass family (rows or columns).
+struct LaunchShape {
+    int tpt;      // threads per transform
+    int groups;   // transforms per CTA
+    size_t smem;  // dynamic shared memory bytes
+};
+
+}  // namespace wsc
+
+struct conv_plan_s {
+    conv_kernel kern;
+    int pnum, pden, n, M, h;  // h = M/2 + 1
+    double b, a;
+    conv_precision prec;
+    conv_io io;
+    int batch_max;
+    bool complex_ghat;
+    int device;
+    int elems;  // complex elements per thread in the transform kernels
+    wsc::FFTDesc fft;
+    wsc::FFTDesc *fft_dev = nullptr;  // device copy read by the pass kernels
+    // FP64 moment quadrant [k2][k1], k1, k2 in [0, h): real (h*h doubles) or complex (h*h double2)
+    double *ghat64 = nullptr;
+    // FP32 copy for FP32 plans (float or float2)
+    void *ghat32 = nullptr;
+    size_t ghat_bytes = 0;
+    // twiddle table exp(-2 pi i t / M), t in [0, M), plan precision
+    void *tw = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    wsc::LaunchShape rows, cols;
+    // FP64 companion plan used as the outer operator of mixed-precision refinement (owned)
+    conv_plan_s *fp64_twin = nullptr;
+};
+
+namespace wsc {
+// passes.cu
+conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
+                            double alpha_re, double alpha_im, double beta, void *ws,
+                            cudaStream_t st);
+conv_status select_transform(conv_plan_s *p);
+// ghat.cu
+conv_status build_ghat(conv_plan_s *p);
+size_t spectrum_elems(const conv_plan_s *p);  // complex elements of the workspace per density
+}  // namespace wsc

@@ -1,0 +1,188 @@
+"""Parity of the CUDA convolution path (through the C ABI) with the CPU oracle, element by element.
+
+Tolerances (relative L-infinity, eq. (rel-err) normalisation by max |oracle|):
+  FP64 passes: 1e-12.   FP32 passes: 2e-6 (single-precision FFTs of length up to 3*8192: about
+  log2(M) * 6e-8 * a few, measured well below this bound).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2107_03958_gb300 import inputs
+from paper_2107_03958_gb300.api import ConvPlan
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-6}
+INV2PI = 1.0 / (2.0 * math.pi)
+KERNELS = {
+    "log": dict(kernel="log", scale=-INV2PI),
+    "pow-0.5": dict(kernel="pow", gamma=-0.5),
+    "pow-1": dict(kernel="pow", gamma=-1.0),
+    "pow-1.5": dict(kernel="pow", gamma=-1.5),
+    "helm20": dict(kernel="helmholtz", kappa=20.0),
+}
+
+
+def _oracle_kw(kw):
+    kind = {"log": "log", "pow": "pow", "helmholtz": "helm"}[kw["kernel"]]
+    return kind, {k: v for k, v in kw.items() if k in ("gamma", "kappa", "scale")}
+
+
+def _relerr(ref, got):
+    return float(np.max(np.abs(ref - got)) / np.max(np.abs(ref)))
+
+
+def _oracle_conv(u, plan, kw):
+    kind, okw = _oracle_kw(kw)
+    g = O.ghat_full(kind, plan.M, plan.b, plan.a, **okw)
+    return O.conv(u, plan.M, g)
+
+
+# ------------------------------------------------------------------ moments
+@pytest.mark.parametrize("name", list(KERNELS))
+@pytest.mark.parametrize("n", [16, 128])
+def test_ghat_table_matches_oracle(name, n):
+    kw = KERNELS[name]
+    plan = ConvPlan(n=n, period=3, precision="fp64", io="r2c" if kw["kernel"] == "helmholtz" else "r2r", **kw)
+    got = plan.ghat_quadrant()
+    kind, okw = _oracle_kw(kw)
+    h = plan.M // 2 + 1
+    ref = np.zeros((h, h), dtype=complex)
+    for k2 in range(h):
+        for k1 in range(h):
+            ref[k2, k1] = O.ghat_radial(kind, math.hypot(k1, k2), plan.b, plan.a, **okw)
+    if kind != "helm":
+        ref = ref.real
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_helmholtz_ghat_near_resonance():
+    """kappa chosen so that |k| = (3,4) sits 1e-6 from the resonance circle s = kappa."""
+    b = 3.0
+    kappa = 2 * math.pi * 5.0 / b * (1 + 1e-6)
+    plan = ConvPlan("helmholtz", n=8, period=3, precision="fp64", io="c2c", kappa=kappa)
+    got = plan.ghat_quadrant()
+    ref = O.ghat_radial("helm", 5.0, b, plan.a, kappa=kappa)
+    assert abs(got[4, 3] - ref) <= 1e-12 * abs(ref)
+    assert abs(got[0, 0] - O.ghat_radial("helm", 0.0, b, plan.a, kappa=kappa)) <= 1e-13 * abs(ref)
+
+
+# ------------------------------------------------------------------ the scheme
+CASES = [
+    # n, period, kernel, io
+    (8, 3, "log", "r2r"), (16, 3, "pow-1", "r2r"), (32, 3, "pow-0.5", "r2r"), (64, 2, "log", "r2r"),
+    (96, 3, "pow-1.5", "r2r"), (128, 3, "log", "r2r"), (256, 3, "pow-1", "r2r"),
+    (48, 3, "helm20", "r2c"), (128, 3, "helm20", "c2c"), (64, 3, "log", "c2c"), (32, 3, "pow-1", "r2c"),
+    (15, 2, "log", "r2r"),  # odd n: the last row pair is ragged
+    (5, 3, "log", "r2r"), (1, 2, "pow-1", "r2r"), (2, 3, "log", "c2c"),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,period,name,io", CASES)
+def test_conv_matches_oracle(n, period, name, io, prec):
+    kw = KERNELS[name]
+    a = 0.0 if period == 3 else 0.45 * 2  # b = 2 needs an explicit radius
+    plan = ConvPlan(n=n, period=period, trunc_a=a, precision=prec, io=io, batch_max=3, **kw)
+    rng = np.random.default_rng(n * 7 + period)
+    B = 3
+    u = rng.standard_normal((B, n, n))
+    if io == "c2c":
+        u = u + 1j * rng.standard_normal((B, n, n))
+    ut = torch.tensor(u, dtype=plan.in_dtype(), device="cuda")
+    out = plan.apply(ut).cpu().numpy()
+    ref = _oracle_conv(u, plan, kw)
+    if io == "r2r":
+        assert np.max(np.abs(ref.imag)) <= 1e-12 * np.max(np.abs(ref))
+        ref = ref.real
+    for i in range(B):
+        assert _relerr(ref[i], out[i]) <= TOL[prec], (i, _relerr(ref[i], out[i]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mask_and_axpby(prec):
+    n = 64
+    kw = KERNELS["helm20"]
+    plan = ConvPlan(n=n, period=3, precision=prec, io="c2c", batch_max=2, **kw)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((2, n, n)) + 1j * rng.standard_normal((2, n, n))
+    m = rng.uniform(0, 1, (n, n))
+    ut = torch.tensor(u, dtype=plan.cplx_dtype, device="cuda")
+    mt = torch.tensor(m, dtype=plan.real_dtype, device="cuda")
+    alpha, beta = 400.0 + 3.0j, 1.0
+    out = plan.apply(ut, mask=mt, alpha=alpha, beta=beta).cpu().numpy()
+    ref = beta * u + alpha * _oracle_conv(u * m, plan, kw)
+    for i in range(2):
+        assert _relerr(ref[i], out[i]) <= TOL[prec]
+
+
+def test_poisson_bump_config():
+    """Single bump, -(1/2pi) log, n = 64, b = 2, a = 1.1: GPU == oracle, and both near the radial
+    Poisson potential."""
+    n = 64
+    plan = ConvPlan("log", n=n, period=2, trunc_a=1.1, precision="fp64", io="r2r", scale=-INV2PI)
+    u = inputs.poisson_bump(n)
+    out = plan.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    ref = O.conv(u, plan.M, O.ghat_full("log", plan.M, 2.0, 1.1, scale=-INV2PI)).real
+    assert _relerr(ref, out) <= 1e-12
+
+
+def test_batch_results_independent_of_batch_position():
+    n = 96
+    plan = ConvPlan("pow", n=n, period=3, precision="fp32", io="r2r", batch_max=8, gamma=-1.0)
+    u = torch.tensor(inputs.bump_sums(n, 8, seed=11), dtype=torch.float32, device="cuda")
+    full = plan.apply(u)
+    for i in (0, 5, 7):
+        alone = plan.apply(u[i].contiguous())
+        assert torch.equal(alone, full[i])
+
+
+def test_caller_workspace_and_empty_batch():
+    n = 32
+    plan = ConvPlan("log", n=n, period=3, precision="fp64", io="r2r", batch_max=1, scale=-INV2PI)
+    u = torch.randn(4, n, n, dtype=torch.float64, device="cuda")
+    ws = torch.empty(plan.workspace_bytes(4), dtype=torch.uint8, device="cuda")
+    out = plan.apply(u, workspace=ws)
+    ref = np.stack([plan.apply(u[i].contiguous()).cpu().numpy() for i in range(4)])
+    assert np.array_equal(out.cpu().numpy(), ref)
+    empty = torch.empty(0, n, n, dtype=torch.float64, device="cuda")
+    assert plan.apply(empty).shape == (0, n, n)
+
+
+def test_invalid_arguments_are_reported():
+    from paper_2107_03958_gb300._native import ConvError
+    with pytest.raises(ConvError, match="EINVAL"):
+        ConvPlan("log", n=0, period=3)
+    with pytest.raises(ConvError, match="EINVAL"):
+        ConvPlan("log", n=16, period=2)  # b < 1 + sqrt 2 and no explicit radius
+    with pytest.raises(ConvError, match="EUNSUPPORTED"):
+        ConvPlan("log", n=14, period=3)  # M = 42 = 2 * 3 * 7
+    with pytest.raises(ConvError, match="EINVAL"):
+        ConvPlan("helmholtz", n=16, period=3, io="r2r", kappa=5.0)
+    with pytest.raises(ConvError, match="EUNSUPPORTED"):
+        ConvPlan("pow", n=16, period=3, gamma=-0.3)
+    plan = ConvPlan("log", n=16, period=3, batch_max=1)
+    u = torch.zeros(2, 16, 16, dtype=torch.float64, device="cuda")
+    with pytest.raises(ConvError, match="EINVAL"):
+        plan.apply(u)  # batch > batch_max without a workspace
+    with pytest.raises(ConvError, match="EINVAL"):
+        plan.apply(u[0], out=u[0])  # aliasing
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_kernel_sweep(prec):
+    """n = 4096, b = 3, batch 16 (the benchmark's launch configuration): densities 0 and 9 against
+    the oracle's full FFT convolution."""
+    n, B = 4096, 16
+    kw = KERNELS["log"]
+    plan = ConvPlan(n=n, period=3, precision=prec, io="r2r", batch_max=B, **kw)
+    u = inputs.bump_sums(n, B)
+    out = plan.apply(torch.tensor(u, dtype=plan.real_dtype, device="cuda"))
+    g = O.ghat_full("log", plan.M, plan.b, plan.a, scale=-INV2PI)
+    for i in (0, 9):
+        ref = O.conv(u[i], plan.M, g).real
+        assert _relerr(ref, out[i].cpu().numpy()) <= TOL[prec]
