@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark: the five-kernel convolution sweep on batches of 16 seeded densities (Sec. 2.1,
+eq. (An)), on one GB300 per rank.
+
+One step = the batch of 16 densities (sums of 1-8 C-infinity bumps, n x n, b = 3) convolved with
+each of log|x|, |x|^-1/2, |x|^-1, |x|^-3/2 and (i/4) H0(20 |x|): 80 convolutions.  The headline is
+the FP32 path at n = 4096; the FP64 path, n = 2048 and the Lippmann-Schwinger solver are reported
+beside it.  Inputs (16 x 4096^2 x 4 B = 1.07 GB) exceed the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("convolutions/s & HBM-roofline % at N=2048²/4096² (FP64 vs mixed); "
+          "LS solves/s, p99 latency")
+SWEEP = [("log", {"scale": 1.0}), ("pow", {"gamma": -0.5}), ("pow", {"gamma": -1.0}),
+         ("pow", {"gamma": -1.5}), ("helmholtz", {"kappa": 20.0})]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--no-extras", action="store_true", help="headline only (no FP64/n=2048/LS legs)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "mine" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, value):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = ["-i", str(device_index)]
+        self.cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                    "-lms", "200"] + sel
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_median": statistics.median(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- traffic record
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2107_03958_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name):
+    """dram bytes per launch from the committed ncu summary, if it was taken on the current kernel
+    sources (the summary records the hash of csrc/); else None."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(rec["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- measured peaks
+def peaks_file():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def hbm_peak():
+    p = peaks_file()
+    for k in ("hbm_gbs", "copy_gbs", "hbm_copy_gbs"):
+        if k in p:
+            return float(p[k]), "measured (MEASURED_PEAKS.json)"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+def cpu_oracle_rate(n, reps=1):
+    """The oracle's full FFT convolution (eq. (An)) of one density with log|x|, FP64, all host
+    threads; returns (conv/s, threads, seconds)."""
+    import oracle as O
+    from paper_2107_03958_gb300 import inputs
+    O.set_threads(os.cpu_count() or 1)
+    threads = O.threads()
+    M = 3 * n
+    g = O.ghat_full("log", M, 3.0, O.default_trunc_radius(3.0), scale=1.0)
+    u = inputs.bump_sums(n, 1)[0]
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        O.conv(u, M, g)
+    dt = time.perf_counter() - t0
+    return reps / dt, threads, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2107_03958_gb300 import inputs
+    n = args.n
+    O.set_threads(os.cpu_count() or 1)
+    M = 3 * n
+    g = O.ghat_full("log", M, 3.0, O.default_trunc_radius(3.0), scale=1.0)
+    us = inputs.bump_sums(n, args.batch)
+    for w in range(args.warmup):
+        O.conv(us[w % args.batch], M, g)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.conv(us[k % args.batch], M, g)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    sample = "one density of the batch per step (log kernel, n=%d, b=3, FP64 C oracle)" % n
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "conv/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": v, "unit": "conv/s", "cores": O.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "conv/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": "kernel sweep batched: 16 seeded bump-sum densities x {log, |x|^-0.5, "
+                        "|x|^-1, |x|^-1.5, Helmholtz kappa=20}, n=%d, b=3" % args.n,
+            "n": args.n, "period_b": 3, "batch": args.batch, "kernels": 5,
+            "convolutions_per_step": 5 * args.batch, "precision": "fp32 (headline), fp64 reported",
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------- GPU legs
+def make_plans(n, batch, precision):
+    from paper_2107_03958_gb300.api import ConvPlan
+    plans = []
+    for kern, kw in SWEEP:
+        io = "r2c" if kern == "helmholtz" else "r2r"
+        plans.append(ConvPlan(kern, n=n, period=3, precision=precision, io=io, batch_max=batch, **kw))
+    return plans
+
+
+def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, host_io=False):
+    """Time `steps` sweeps; returns dict with ms/step, pass timings of the real-kernel plans."""
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    plans = make_plans(n, batch, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u_host = torch.from_numpy(inputs.bump_sums(n, batch)).to(dt)
+    u = u_host.cuda()
+    outs = [torch.empty((batch, n, n), dtype=p.out_dtype(), device="cuda") for p in plans]
+    pinned_in = pinned_out = None
+    if host_io:
+        pinned_in = u_host.pin_memory()
+        pinned_out = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+
+    def step():
+        if host_io:
+            u.copy_(pinned_in, non_blocking=True)
+        for p, o in zip(plans, outs):
+            p.apply(u, out=o, stream=stream)
+        if host_io:
+            for o, h in zip(outs, pinned_out):
+                h.copy_(o, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    if timing:
+        for p in plans:
+            p.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    res = {"ms": ms, "plans": plans, "launches": 3 * len(plans) * steps}
+    if timing:
+        res["passes"] = [p.timing_read() for p in plans]
+        for p in plans:
+            p.timing(False)
+    if host_io:
+        res["h2d"] = u_host.numel() * u_host.element_size()
+        res["d2h"] = sum(o.numel() * o.element_size() for o in outs)
+    return res
+
+
+def r2r_bytes(plan, batch):
+    """Algorithmic HBM bytes of one column-pass launch (R2R): read and write the n x (M/2+1)
+    spectra of the batch, read the moment quadrant once."""
+    n, M = plan.n, plan.M
+    h = M // 2 + 1
+    esz = 16 if plan.precision == "fp64" else 8
+    return batch * 2 * h * n * esz + h * h * (esz // 2)
+
+
+def ls_leg(n, kappa, repeats, stream):
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import ConvPlan, ls_solve
+    m = torch.tensor(inputs.lippmann_contrast(n, "bump"), device="cuda")
+    f = torch.tensor(inputs.plane_wave(n, kappa), device="cuda")
+    out = {}
+    for mode in ("fp64", "mixed"):
+        plan = ConvPlan("helmholtz", n=n, period=3, precision="fp64" if mode == "fp64" else "fp32",
+                        io="c2c", kappa=kappa)
+        ls_solve(plan, m, f, refine=(mode == "mixed"), stream=stream)  # warm-up
+        lat, info = [], None
+        for _ in range(repeats):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = ls_solve(plan, m, f, refine=(mode == "mixed"), stream=stream)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - t0)
+        lat.sort()
+        out[mode] = {"solves_per_s": len(lat) / sum(lat), "p50_ms": 1e3 * lat[len(lat) // 2],
+                     "p99_ms": 1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                     "iters": info["iters"], "rel_residual": info["rel_residual"]}
+    return {"n": n, "kappa": kappa, "contrast": "0.5 bump(0.4)", "tol": 1e-10, "restart": 50,
+            "repeats": repeats, **out}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    import paper_2107_03958_gb300.build as B
+    B.build()
+    from paper_2107_03958_gb300.api import measure_peaks
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, threads, secs = cpu_oracle_rate(args.n)
+        cpu = {"value": rate, "unit": "conv/s", "cores": threads, "kind": "oracle",
+               "sample": "1 of the step's 80 convolutions (density 0, log kernel, n=%d, b=3), FP64 C "
+                         "oracle, %.1f s" % (args.n, secs)}
+
+    peaks = measure_peaks(1 << 30)
+    hbm, hbm_src = hbm_peak()
+
+    # headline: FP32 sweep at n, device-resident inputs, per-pass events
+    clocks = ClockSampler(local)
+    barrier(ws)
+    clocks.start()
+    head = sweep_leg(args.n, args.batch, "fp32", args.steps, args.warmup, stream, timing=True)
+    clk = clocks.stop()
+    ms = max_over_ranks(ws, head["ms"])
+    convs = 5 * args.batch * args.steps
+    value = ws * convs / (ms * 1e-3)
+
+    # dominant kernel: the R2R column pass
+    r2r = [(p, t) for p, t in zip(head["plans"], head["passes"]) if p.io == "r2r"]
+    tot = [0.0, 0.0, 0.0]
+    cnt = 0
+    for p, (passes, applies) in r2r:
+        for i in range(3):
+            tot[i] += passes[i]
+        cnt += applies
+    col_ms = tot[1] / cnt
+    col_bytes = r2r_bytes(r2r[0][0], args.batch)
+    achieved = col_bytes / (col_ms * 1e-3) / 1e9
+    share = [t / sum(tot) for t in tot]
+    roofline = {"bound": "hbm", "kernel": "k_r2r_cols<float> (column pass)", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src,
+                "traffic": recorded_traffic("k_r2r_cols_fp32_n4096.txt"),
+                "algorithmic_bytes_per_launch": col_bytes, "avg_launch_ms": col_ms,
+                "pass_share_r2r": {"rows_fwd": share[0], "cols": share[1], "rows_inv": share[2]},
+                "live_peaks": peaks}
+
+    # end to end: pinned host inputs and results, copies inside the timed region
+    e2e_leg = sweep_leg(args.n, args.batch, "fp32", max(2, args.steps // 2), 1, stream, host_io=True)
+    e2e_ms = max_over_ranks(ws, e2e_leg["ms"])
+    e2e_steps = max(2, args.steps // 2)
+    e2e = {"value": ws * 5 * args.batch * e2e_steps / (e2e_ms * 1e-3), "unit": "conv/s",
+           "h2d_bytes_per_step": e2e_leg["h2d"], "d2h_bytes_per_step": e2e_leg["d2h"]}
+
+    extras = {}
+    if not args.no_extras:
+        k64 = max(1, args.steps // 5)
+        f64 = sweep_leg(args.n, args.batch, "fp64", k64, 1, stream, timing=True)
+        f64_ms = max_over_ranks(ws, f64["ms"])
+        r64 = [(p, t) for p, t in zip(f64["plans"], f64["passes"]) if p.io == "r2r"]
+        c64 = sum(t[0][1] for _, t in r64) / sum(t[1] for _, t in r64)
+        flops = 5 * (r64[0][0].M) * math.log2(r64[0][0].M) * 2 * (r64[0][0].M // 2 + 1) * args.batch
+        extras["fp64"] = {"value": ws * 5 * args.batch * k64 / (f64_ms * 1e-3), "unit": "conv/s",
+                          "ms_per_step": f64_ms / k64, "steps": k64,
+                          "roofline_cols": {"bound": "alu", "achieved": flops / (c64 * 1e-3) / 1e12,
+                                            "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                                            "frac": flops / (c64 * 1e-3) / 1e12 / peaks["fp64_tflops"],
+                                            "flops_model": "5 M log2 M per complex length-M FFT, 2 per column",
+                                            "peak_source": "measured FP64 FMA microbenchmark"},
+                          "hbm_frac_cols": r2r_bytes(r64[0][0], args.batch) / (c64 * 1e-3) / 1e9 / hbm}
+        n2 = args.n // 2
+        l2 = sweep_leg(n2, args.batch, "fp32", args.steps, args.warmup, stream)
+        l2_ms = max_over_ranks(ws, l2["ms"])
+        extras["fp32_n%d" % n2] = {"value": ws * 5 * args.batch * args.steps / (l2_ms * 1e-3),
+                                   "unit": "conv/s", "ms_per_step": l2_ms / args.steps}
+        extras["ls"] = ls_leg(512, 40.0, 5, stream)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "conv/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "clocks": clk, "gpu_launches": head["launches"]}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -155,6 +155,14 @@ typedef struct {
 conv_status ls_solve(conv_plan_t plan, const double *m, const void *f, void *x, const ls_opts *opts,
                      ls_info *info, void *stream);
 
+/* Per-pass device timing (benchmark instrumentation; no counterpart in the paper).  While enabled,
+ * every apply on this plan records CUDA events around its three kernel launches on the apply's
+ * stream (no synchronisation).  conv_timing_read waits for the recorded events, returns the summed
+ * milliseconds of pass 1 (rows forward), pass 2 (columns) and pass 3 (rows inverse) and the number
+ * of applies recorded, and clears the record. */
+conv_status conv_timing_enable(conv_plan_t plan, int enable);
+conv_status conv_timing_read(conv_plan_t plan, double ms_out[3], long long *applies);
+
 /* ------------------------------------------------------------------------------------------
  * Roofline denominators measured on the running GPU (no counterpart in the paper):
  *   copy:  bytes read + written per second by a grid-stride float4 copy of `bytes` bytes;

@@ -56,6 +56,9 @@ PROTOTYPES = {
     "conv_last_error": (ctypes.c_char_p, []),
     "ls_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.POINTER(LsOpts), ctypes.POINTER(LsInfo), ctypes.c_void_p]),
+    "conv_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "conv_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_longlong)]),
     "conv_measure_peaks": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]),

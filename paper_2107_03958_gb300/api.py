@@ -118,6 +118,17 @@ class ConvPlan:
 
     __call__ = apply
 
+    def timing(self, enable):
+        """Record per-pass CUDA events on every apply (benchmark instrumentation)."""
+        N.check(self._lib.conv_timing_enable(self._h, int(bool(enable))))
+
+    def timing_read(self):
+        """(ms per pass summed over recorded applies [3], number of applies); clears the record."""
+        ms = (ctypes.c_double * 3)()
+        cnt = ctypes.c_longlong()
+        N.check(self._lib.conv_timing_read(self._h, ms, ctypes.byref(cnt)))
+        return [ms[0], ms[1], ms[2]], cnt.value
+
     def ghat_quadrant(self):
         """FP64 moment table ghat(|k1|, |k2|), 0 <= k1, k2 <= M/2, as numpy [k2, k1]."""
         h = self.M // 2 + 1

@@ -259,12 +259,16 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
     const void *gh = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
     const LaunchShape &R = p->rows, &C = p->cols;
     const FFTDesc *fd = p->fft_dev;
+    cudaEvent_t *ev = timing_slot(p);
+    if (ev) cudaEventRecord(ev[0], st);
     if (p->io == CONV_IO_R2R) {
         int units = (n + 1) / 2;
         dim3 g1((units + R.groups - 1) / R.groups, batch);
         k_r2r_rows_fwd<T, E><<<g1, R.tpt * R.groups, R.smem, st>>>(reinterpret_cast<const T *>(u), mk, W, n, h, fd, tw, R.tpt);
+        if (ev) cudaEventRecord(ev[1], st);
         dim3 g2(batch, (h + C.groups - 1) / C.groups);
         k_r2r_cols<T, E><<<g2, C.tpt * C.groups, C.smem, st>>>(W, reinterpret_cast<const T *>(gh), n, h, fd, tw, C.tpt);
+        if (ev) cudaEventRecord(ev[2], st);
         k_r2r_rows_inv<T, E><<<g1, R.tpt * R.groups, R.smem, st>>>(W, reinterpret_cast<const T *>(u), reinterpret_cast<T *>(out), n, h, fd, tw, R.tpt, (T)(are * sc), (T)beta);
     } else {
         const bool in_real = p->io == CONV_IO_R2C;
@@ -273,17 +277,20 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
             k_c2c_rows_fwd<T, E, true><<<g1, R.tpt * R.groups, R.smem, st>>>(u, mk, W, n, fd, tw, R.tpt);
         else
             k_c2c_rows_fwd<T, E, false><<<g1, R.tpt * R.groups, R.smem, st>>>(u, mk, W, n, fd, tw, R.tpt);
+        if (ev) cudaEventRecord(ev[1], st);
         dim3 g2(batch, (M + C.groups - 1) / C.groups);
         if (p->complex_ghat)
             k_c2c_cols<T, E, true><<<g2, C.tpt * C.groups, C.smem, st>>>(W, gh, n, h, fd, tw, C.tpt);
         else
             k_c2c_cols<T, E, false><<<g2, C.tpt * C.groups, C.smem, st>>>(W, gh, n, h, fd, tw, C.tpt);
+        if (ev) cudaEventRecord(ev[2], st);
         V al = cmk<V>((T)(are * sc), (T)(aim * sc));
         if (in_real)
             k_c2c_rows_inv<T, E, true><<<g1, R.tpt * R.groups, R.smem, st>>>(W, u, reinterpret_cast<V *>(out), n, fd, tw, R.tpt, al, (T)beta);
         else
             k_c2c_rows_inv<T, E, false><<<g1, R.tpt * R.groups, R.smem, st>>>(W, u, reinterpret_cast<V *>(out), n, fd, tw, R.tpt, al, (T)beta);
     }
+    if (ev) cudaEventRecord(ev[3], st);
     WSC_CUDA(cudaGetLastError());
     return CONV_OK;
 }

@@ -61,6 +61,23 @@ static conv_status upload_twiddles(conv_plan_s *p)
     return CONV_OK;
 }
 
+cudaEvent_t *timing_slot(conv_plan_s *p)
+{
+    if (!p->timing) return nullptr;
+    if (p->tev_free.empty()) {
+        std::array<cudaEvent_t, 4> e;
+        for (auto &x : e)
+            if (cudaEventCreate(&x) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+        p->tev_free.push_back(e);
+    }
+    p->tev_used.push_back(p->tev_free.back());
+    p->tev_free.pop_back();
+    return p->tev_used.back().data();
+}
+
 static size_t elem_bytes(const conv_plan_s *p) { return p->prec == CONV_P_FP64 ? 16 : 8; }
 
 }  // namespace wsc
@@ -80,6 +97,9 @@ void conv_destroy(conv_plan_t p)
     if (p->fft_dev) cudaFree(p->fft_dev);
     if (p->ws) cudaFree(p->ws);
     if (p->fp64_twin) conv_destroy(p->fp64_twin);
+    for (auto &v : {&p->tev_used, &p->tev_free})
+        for (auto &e : *v)
+            for (auto x : e) cudaEventDestroy(x);
     delete p;
 }
 
@@ -237,6 +257,31 @@ conv_status conv_ghat_to_host(conv_plan_t p, double *host_out)
 {
     if (!p || !host_out) return fail(CONV_EINVAL, "bad argument");
     WSC_CUDA(cudaMemcpy(host_out, p->ghat64, p->ghat_bytes, cudaMemcpyDeviceToHost));
+    return CONV_OK;
+}
+
+conv_status conv_timing_enable(conv_plan_t p, int enable)
+{
+    if (!p) return fail(CONV_EINVAL, "plan is NULL");
+    p->timing = enable != 0;
+    return CONV_OK;
+}
+
+conv_status conv_timing_read(conv_plan_t p, double ms_out[3], long long *applies)
+{
+    if (!p || !ms_out) return fail(CONV_EINVAL, "bad argument");
+    ms_out[0] = ms_out[1] = ms_out[2] = 0.0;
+    for (auto &e : p->tev_used) {
+        WSC_CUDA(cudaEventSynchronize(e[3]));
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            WSC_CUDA(cudaEventElapsedTime(&ms, e[k], e[k + 1]));
+            ms_out[k] += ms;
+        }
+    }
+    if (applies) *applies = (long long)p->tev_used.size();
+    for (auto &e : p->tev_used) p->tev_free.push_back(e);
+    p->tev_used.clear();
     return CONV_OK;
 }
 

@@ -2,7 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <string>
+#include <vector>
 
 #include "../../include/wsconv.h"
 #include "fft_engine.cuh"
@@ -64,9 +66,14 @@ struct conv_plan_s {
     wsc::LaunchShape rows, cols;
     // FP64 companion plan used as the outer operator of mixed-precision refinement (owned)
     conv_plan_s *fp64_twin = nullptr;
+    // per-pass timing instrumentation
+    bool timing = false;
+    std::vector<std::array<cudaEvent_t, 4>> tev_used, tev_free;
 };
 
 namespace wsc {
+// plan.cu: timing marks; returns the event set for this apply (nullptr when timing is off)
+cudaEvent_t *timing_slot(conv_plan_s *p);
 // passes.cu
 conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
                             double alpha_re, double alpha_im, double beta, void *ws,

@@ -77,8 +77,9 @@ CASES = [
     (8, 3, "log", "r2r"), (16, 3, "pow-1", "r2r"), (32, 3, "pow-0.5", "r2r"), (64, 2, "log", "r2r"),
     (96, 3, "pow-1.5", "r2r"), (128, 3, "log", "r2r"), (256, 3, "pow-1", "r2r"),
     (48, 3, "helm20", "r2c"), (128, 3, "helm20", "c2c"), (64, 3, "log", "c2c"), (32, 3, "pow-1", "r2c"),
-    (15, 2, "log", "r2r"),  # odd n: the last row pair is ragged
-    (5, 3, "log", "r2r"), (1, 2, "pow-1", "r2r"), (2, 3, "log", "c2c"),
+    (15, 2, "log", "r2r"),  # odd n: the last row pair is ragged (M = 30: generic radix-5 path)
+    (9, 2, "pow-1", "r2r"),  # M = 18 = 2 * 3 * 3: generic path
+    (3, 4, "log", "r2r"), (4, 3, "log", "c2c"), (2, 3, "pow-1", "r2c"),  # tiny transforms
 ]
 
 
@@ -165,6 +166,10 @@ def test_invalid_arguments_are_reported():
         ConvPlan("helmholtz", n=16, period=3, io="r2r", kappa=5.0)
     with pytest.raises(ConvError, match="EUNSUPPORTED"):
         ConvPlan("pow", n=16, period=3, gamma=-0.3)
+    with pytest.raises(ConvError, match="EUNSUPPORTED"):
+        ConvPlan("log", n=5, period=3)  # M = 15 is odd
+    with pytest.raises(ConvError, match="EUNSUPPORTED"):
+        ConvPlan("log", n=1, period=3)  # M = 3
     plan = ConvPlan("log", n=16, period=3, batch_max=1)
     u = torch.zeros(2, 16, 16, dtype=torch.float64, device="cuda")
     with pytest.raises(ConvError, match="EINVAL"):
