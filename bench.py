@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--no-extras", action="store_true", help="headline only (no FP64/n=2048/LS legs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--only", choices=["r2r", "r2r64", "c2c"], default=None,
+                    help="profiling case: warmup + steps applies of one plan (log kernel R2R FP32, "
+                         "R2R FP64, or Helmholtz C2C FP32), no other legs")
     return ap.parse_args()
 
 
@@ -323,11 +326,39 @@ def ls_leg(n, kappa, repeats, stream):
             "repeats": repeats, **out}
 
 
+def profile_case(args):
+    """Small fixed case for ncu captures: one plan, warmup + steps applies, nothing else."""
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import ConvPlan
+    prec = "fp64" if args.only == "r2r64" else "fp32"
+    if args.only == "c2c":
+        plan = ConvPlan("helmholtz", n=args.n, period=3, precision=prec, io="c2c",
+                        batch_max=args.batch, kappa=20.0)
+        u = torch.tensor(inputs.bump_sums(args.n, args.batch), dtype=plan.cplx_dtype, device="cuda")
+    else:
+        plan = ConvPlan("log", n=args.n, period=3, precision=prec, io="r2r", batch_max=args.batch)
+        u = torch.tensor(inputs.bump_sums(args.n, args.batch), dtype=plan.real_dtype, device="cuda")
+    out = torch.empty(u.shape, dtype=plan.out_dtype(), device="cuda")
+    for _ in range(args.warmup + args.steps):
+        plan.apply(u, out=out)
+    torch.cuda.synchronize()
+    info = plan.info
+    print(json.dumps({"case": args.only, "n": args.n, "batch": args.batch, "M": plan.M,
+                      "threads_per_transform": info.threads_rows, "groups": info.groups_rows,
+                      "radices": list(info.radices)[:info.nstages]}))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.only:
+        import paper_2107_03958_gb300.build as B
+        B.build()
+        profile_case(args)
         return
     import torch
     import paper_2107_03958_gb300.build as B

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -130,8 +131,12 @@ conv_status select_transform(conv_plan_s *p)
         return fail(CONV_EUNSUPPORTED, "transform length M=" + std::to_string(M) +
                                            " exceeds one CTA's shared memory at this precision");
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
+    // optional overrides for tuning experiments: WSCONV_ELEMS (per-thread count), WSCONV_GROUPS
+    const char *env_e = getenv("WSCONV_ELEMS"), *env_g = getenv("WSCONV_GROUPS");
+    const int force_e = env_e ? atoi(env_e) : -1, force_g = env_g ? atoi(env_g) : 0;
     for (int i = 0; i < 4; ++i) {
         const int E = cand[i];
+        if (force_e >= 0 && E != force_e) continue;
         FFTDesc d;
         if (!factorize(M, E, d)) continue;
         const int maxT = max_threads(p->prec, E);
@@ -146,6 +151,7 @@ conv_status select_transform(conv_plan_s *p)
         int G = std::max(1, maxT / tpt);
         G = std::min<int>(G, (int)(smem_optin / per));
         G = std::min(G, 8);
+        if (force_g > 0 && force_g <= G) G = force_g;
         p->elems = E;
         p->fft = d;
         p->rows.tpt = p->cols.tpt = tpt;
