@@ -126,10 +126,44 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x
     else dft8<INV>(x);
 }
 
+// ---------------------------------------------------------------- twiddles
+// x[q] *= w^q, w = tw[t1] = exp(-/+ 2 pi i t1 / L), q = 1..R-1.  The powers 1, 2 and 4 are read
+// from the table (t1, 2 t1, 4 t1 < L since t1 < L/R); 3, 5, 6, 7 are products of two of them.
+template <typename T, bool TWS>
+__device__ __forceinline__ typename cvec<T>::t tw_load(const typename cvec<T>::t *__restrict__ tw, int t)
+{
+    if constexpr (TWS) return tw[t];
+    else return __ldg(&tw[t]);
+}
+
+template <typename T, int R, bool INV, bool TWS>
+__device__ __forceinline__ void apply_twiddles(typename cvec<T>::t *x, const typename cvec<T>::t *__restrict__ tw, int t1)
+{
+    typedef typename cvec<T>::t V;
+    V w1 = tw_load<T, TWS>(tw, t1);
+    if (INV) w1.y = -w1.y;
+    x[1] = cmul(x[1], w1);
+    if constexpr (R == 2) return;
+    V w2 = tw_load<T, TWS>(tw, 2 * t1);
+    if (INV) w2.y = -w2.y;
+    x[2] = cmul(x[2], w2);
+    if constexpr (R == 3) return;
+    V w3 = cmul(w1, w2);
+    x[3] = cmul(x[3], w3);
+    if constexpr (R == 4) return;
+    V w4 = tw_load<T, TWS>(tw, 4 * t1);
+    if (INV) w4.y = -w4.y;
+    x[4] = cmul(x[4], w4);
+    if constexpr (R == 5) return;
+    x[5] = cmul(x[5], cmul(w1, w4));
+    x[6] = cmul(x[6], cmul(w2, w4));
+    x[7] = cmul(x[7], cmul(w3, w4));
+}
+
 // ---------------------------------------------------------------- one Stockham stage
 // Every thread owns exactly E elements of a length-L transform (L = E * tpt); a radix-R stage
 // gives it E/R butterflies j = lt + b tpt.  tw[t] = exp(-2 pi i t / L).
-template <typename T, int E, int R, bool INV>
+template <typename T, int E, int R, bool INV, bool TWS>
 __device__ __forceinline__ void stockham_stage(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P, int s,
                                                const typename cvec<T>::t *__restrict__ tw, int lt,
                                                int tpt)
@@ -152,18 +186,13 @@ __device__ __forceinline__ void stockham_stage(typename cvec<T>::t *buf, const F
         const int j = lt + b * tpt;
         const int jq = (int)(((unsigned long long)j * mg) >> 40);
         const int k = j - jq * Ns;
-        if (Ns > 1) {
-#pragma unroll
-            for (int q = 1; q < R; ++q) {
-                V w = __ldg(&tw[q * k * tws]);
-                if (INV) w.y = -w.y;
-                v[b][q] = cmul(v[b][q], w);
-            }
-        }
+        if (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw, k * tws);
         dftR<R, INV>(v[b]);
         const int base = jq * Ns * R + k;
 #pragma unroll
         for (int p = 0; p < R; ++p) buf[pidx<T>(base + p * Ns)] = v[b][p];
+        // keep the next butterfly's twiddle loads after these stores (bounds live registers)
+        asm volatile("" ::: "memory");
     }
     __syncthreads();
 }
@@ -171,7 +200,7 @@ __device__ __forceinline__ void stockham_stage(typename cvec<T>::t *buf, const F
 // Generic stage for lengths without an exact per-thread split (E = 0 below): up to GMAXE elements
 // per thread, butterflies guarded by j < L/R.
 #define WSC_GMAXE 24
-template <typename T, int R, bool INV>
+template <typename T, int R, bool INV, bool TWS>
 __device__ __forceinline__ void stockham_stage_guarded(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P, int s,
                                                        const typename cvec<T>::t *__restrict__ tw, int lt,
                                                        int tpt)
@@ -197,14 +226,7 @@ __device__ __forceinline__ void stockham_stage_guarded(typename cvec<T>::t *buf,
         if (j < nbf) {
             const int jq = (int)(((unsigned long long)j * mg) >> 40);
             const int k = j - jq * Ns;
-            if (Ns > 1) {
-#pragma unroll
-                for (int q = 1; q < R; ++q) {
-                    V w = __ldg(&tw[q * k * tws]);
-                    if (INV) w.y = -w.y;
-                    v[b][q] = cmul(v[b][q], w);
-                }
-            }
+            if (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw, k * tws);
             dftR<R, INV>(v[b]);
             const int base = jq * Ns * R + k;
 #pragma unroll
@@ -217,34 +239,39 @@ __device__ __forceinline__ void stockham_stage_guarded(typename cvec<T>::t *buf,
 // Radices a given E supports: R must divide E (E = 0: the guarded generic stage takes any R).
 template <int E, int R> struct radix_ok { static const bool v = E == 0 || (E % R) == 0; };
 
-template <typename T, int E, int R, bool INV, bool OK = radix_ok<E, R>::v> struct stage_call;
-template <typename T, int E, int R, bool INV> struct stage_call<T, E, R, INV, true> {
+template <typename T, int E, int R, bool INV, bool TWS, bool OK = radix_ok<E, R>::v> struct stage_call;
+template <typename T, int E, int R, bool INV, bool TWS> struct stage_call<T, E, R, INV, TWS, true> {
     static __device__ __forceinline__ void run(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P, int s,
                                                const typename cvec<T>::t *__restrict__ tw, int lt, int tpt)
     {
-        if constexpr (E == 0) stockham_stage_guarded<T, R, INV>(buf, P, s, tw, lt, tpt);
-        else stockham_stage<T, E, R, INV>(buf, P, s, tw, lt, tpt);
+        if constexpr (E == 0) stockham_stage_guarded<T, R, INV, TWS>(buf, P, s, tw, lt, tpt);
+        else stockham_stage<T, E, R, INV, TWS>(buf, P, s, tw, lt, tpt);
     }
 };
-template <typename T, int E, int R, bool INV> struct stage_call<T, E, R, INV, false> {
+template <typename T, int E, int R, bool INV, bool TWS> struct stage_call<T, E, R, INV, TWS, false> {
     static __device__ __forceinline__ void run(typename cvec<T>::t *, const FFTDesc *__restrict__, int,
                                                const typename cvec<T>::t *__restrict__, int, int) {}
 };
 
 // Whole transform (unnormalised).  All threads of the CTA must call it (barriers inside).  The
-// host only builds radix sequences whose radices divide E.
-template <typename T, int E, bool INV>
+// host only builds radix sequences whose radices divide E.  TWS: tw points to shared memory.
+template <typename T, int E, bool INV, bool TWS>
 __device__ __forceinline__ void fft_smem(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
                                          const typename cvec<T>::t *__restrict__ tw, int lt, int tpt)
 {
     const int nst = __ldg(&P->nst);
     for (int s = 0; s < nst; ++s) {
+        // launder the thread index so per-stage address arithmetic is not hoisted out of the
+        // stage loop (hoisting every radix's addresses keeps dozens of registers live)
+        int lt_ = lt;
+        asm volatile("" : "+r"(lt_));
+        lt = lt_;
         switch (__ldg(&P->R[s])) {
-        case 8: stage_call<T, E, 8, INV>::run(buf, P, s, tw, lt, tpt); break;
-        case 4: stage_call<T, E, 4, INV>::run(buf, P, s, tw, lt, tpt); break;
-        case 2: stage_call<T, E, 2, INV>::run(buf, P, s, tw, lt, tpt); break;
-        case 3: stage_call<T, E, 3, INV>::run(buf, P, s, tw, lt, tpt); break;
-        default: stage_call<T, E, 5, INV>::run(buf, P, s, tw, lt, tpt); break;
+        case 8: stage_call<T, E, 8, INV, TWS>::run(buf, P, s, tw, lt, tpt); break;
+        case 4: stage_call<T, E, 4, INV, TWS>::run(buf, P, s, tw, lt, tpt); break;
+        case 2: stage_call<T, E, 2, INV, TWS>::run(buf, P, s, tw, lt, tpt); break;
+        case 3: stage_call<T, E, 3, INV, TWS>::run(buf, P, s, tw, lt, tpt); break;
+        default: stage_call<T, E, 5, INV, TWS>::run(buf, P, s, tw, lt, tpt); break;
         }
     }
 }

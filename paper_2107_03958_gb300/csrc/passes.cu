@@ -28,10 +28,10 @@ namespace wsc {
 
 // ============================================================================ host side
 // Per-thread element counts with exact (unguarded) kernels, in order of preference.  A count E
-// admits radices dividing E; FP64 prefers radix-4 stages (E = 12 or 8, 1024 threads), FP32 radix-8
-// (E = 24 or 16).  E = 0 is the generic guarded path (any 2^a 3^b 5^c).
-static const int kElems64[] = {12, 8, 24, 0};
-static const int kElems32[] = {24, 16, 12, 0};
+// admits radices dividing E; FP64 prefers radix-4 stages (E = 12 or 8), FP32 radix-8 (E = 24 or
+// 16).  E = 0 is the generic guarded path (any 2^a 3^b 5^c).
+static const int kElems64[] = {12, 24, 8, 0};
+static const int kElems32[] = {24, 16, 0};
 
 static int max_threads(conv_precision prec, int E)
 {
@@ -44,12 +44,45 @@ static int max_threads(conv_precision prec, int E)
         }
     }
     switch (E) {
-    case 12: return maxt<float, 12>::v;
     case 16: return maxt<float, 16>::v;
     case 24: return maxt<float, 24>::v;
     default: return maxt<float, 0>::v;
     }
 }
+
+// Dispatch on (precision, E, TWS) for the templated helpers.
+#define WSC_DISPATCH(prec, E, tws, CALL)                                                      \
+    do {                                                                                      \
+        if ((prec) == CONV_P_FP64) {                                                          \
+            if ((tws)) {                                                                      \
+                switch (E) {                                                                  \
+                case 8: { typedef double T_; constexpr int E_ = 8; constexpr bool W_ = true; CALL; } break;   \
+                case 12: { typedef double T_; constexpr int E_ = 12; constexpr bool W_ = true; CALL; } break; \
+                default: { typedef double T_; constexpr int E_ = 24; constexpr bool W_ = true; CALL; } break; \
+                }                                                                             \
+            } else {                                                                          \
+                switch (E) {                                                                  \
+                case 8: { typedef double T_; constexpr int E_ = 8; constexpr bool W_ = false; CALL; } break;   \
+                case 12: { typedef double T_; constexpr int E_ = 12; constexpr bool W_ = false; CALL; } break; \
+                case 24: { typedef double T_; constexpr int E_ = 24; constexpr bool W_ = false; CALL; } break; \
+                default: { typedef double T_; constexpr int E_ = 0; constexpr bool W_ = false; CALL; } break;  \
+                }                                                                             \
+            }                                                                                 \
+        } else {                                                                              \
+            if ((tws)) {                                                                      \
+                switch (E) {                                                                  \
+                case 16: { typedef float T_; constexpr int E_ = 16; constexpr bool W_ = true; CALL; } break;   \
+                default: { typedef float T_; constexpr int E_ = 24; constexpr bool W_ = true; CALL; } break;   \
+                }                                                                             \
+            } else {                                                                          \
+                switch (E) {                                                                  \
+                case 16: { typedef float T_; constexpr int E_ = 16; constexpr bool W_ = false; CALL; } break;  \
+                case 24: { typedef float T_; constexpr int E_ = 24; constexpr bool W_ = false; CALL; } break;  \
+                default: { typedef float T_; constexpr int E_ = 0; constexpr bool W_ = false; CALL; } break;   \
+                }                                                                             \
+            }                                                                                 \
+        }                                                                                     \
+    } while (0)
 
 // Radix sequence for L = 2^p 3^q 5^r whose radices divide E (E = 0: any of 8, 4, 2, 3, 5):
 // power-of-two radices first (8s when allowed, else 4s), then 3s, then 5s.
@@ -65,13 +98,12 @@ static bool factorize(int L, int E, FFTDesc &d)
     std::vector<int> R;
     if (ok(8)) {
         for (int i = 0; i < p2 / 3; ++i) R.push_back(8);
-        if (p2 % 3 == 2) R.push_back(ok(4) ? 4 : 2), (ok(4) ? (void)0 : R.push_back(2));
+        if (p2 % 3 == 2) R.push_back(4);
         if (p2 % 3 == 1) R.push_back(2);
     } else if (ok(4)) {
         for (int i = 0; i < p2 / 2; ++i) R.push_back(4);
         if (p2 % 2) R.push_back(2);
     } else {
-        if (p2 && !ok(2)) return false;
         for (int i = 0; i < p2; ++i) R.push_back(2);
     }
     for (int i = 0; i < p3; ++i) R.push_back(3);
@@ -103,38 +135,47 @@ static int generic_tpt(const FFTDesc &P)
     return (need + 31) / 32 * 32;
 }
 
+static conv_status set_all_attrs(int smem)
+{
+    conv_status rc = CONV_OK;
+    for (int prec = 0; prec < 2 && rc == CONV_OK; ++prec)
+        for (int tws = 0; tws < 2 && rc == CONV_OK; ++tws)
+            for (int E : {8, 12, 16, 24, 0}) {
+                if (rc != CONV_OK) break;
+                bool have = prec == CONV_P_FP64 ? (E == 8 || E == 12 || E == 24 || (E == 0 && !tws))
+                                                : (E == 16 || E == 24 || (E == 0 && !tws));
+                if (!have) continue;
+                WSC_DISPATCH((conv_precision)prec, E, tws, rc = (set_attrs<T_, E_, W_>(smem)));
+            }
+    return rc;
+}
+
 conv_status select_transform(conv_plan_s *p)
 {
     int dev = p->device;
-    int smem_optin = 0;
+    int smem_optin = 0, sms = 0;
     WSC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    WSC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     static bool attrs_set[64] = {false};
     if (dev >= 0 && dev < 64 && !attrs_set[dev]) {
-        conv_status rc = CONV_OK;
-        for (int E : kElems64) {
-            if (rc != CONV_OK) break;
-            rc = E == 8 ? set_attrs<double, 8>(smem_optin) : E == 12 ? set_attrs<double, 12>(smem_optin)
-               : E == 24 ? set_attrs<double, 24>(smem_optin) : set_attrs<double, 0>(smem_optin);
-        }
-        for (int E : kElems32) {
-            if (rc != CONV_OK) break;
-            rc = E == 12 ? set_attrs<float, 12>(smem_optin) : E == 16 ? set_attrs<float, 16>(smem_optin)
-               : E == 24 ? set_attrs<float, 24>(smem_optin) : set_attrs<float, 0>(smem_optin);
-        }
+        conv_status rc = set_all_attrs(smem_optin);
         if (rc != CONV_OK) return rc;
         attrs_set[dev] = true;
     }
     const int M = p->M;
     const size_t esz = p->prec == CONV_P_FP64 ? 16 : 8;
     const size_t per = (size_t)(p->prec == CONV_P_FP64 ? padded_len<double>(M) : padded_len<float>(M)) * esz;
+    const size_t twb = (size_t)M * esz;
     if (per > (size_t)smem_optin)
         return fail(CONV_EUNSUPPORTED, "transform length M=" + std::to_string(M) +
                                            " exceeds one CTA's shared memory at this precision");
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
-    // optional overrides for tuning experiments: WSCONV_ELEMS (per-thread count), WSCONV_GROUPS
-    const char *env_e = getenv("WSCONV_ELEMS"), *env_g = getenv("WSCONV_GROUPS");
+    const int ncand = p->prec == CONV_P_FP64 ? 4 : 3;
+    // optional overrides for tuning experiments: WSCONV_ELEMS, WSCONV_GROUPS, WSCONV_TWS (0/1)
+    const char *env_e = getenv("WSCONV_ELEMS"), *env_g = getenv("WSCONV_GROUPS"), *env_t = getenv("WSCONV_TWS");
     const int force_e = env_e ? atoi(env_e) : -1, force_g = env_g ? atoi(env_g) : 0;
-    for (int i = 0; i < 4; ++i) {
+    const int force_t = env_t ? atoi(env_t) : -1;
+    for (int i = 0; i < ncand; ++i) {
         const int E = cand[i];
         if (force_e >= 0 && E != force_e) continue;
         FFTDesc d;
@@ -148,15 +189,23 @@ conv_status select_transform(conv_plan_s *p)
             tpt = generic_tpt(d);
         }
         if (tpt > maxT) continue;
+        // twiddles in shared memory when the table and at least one transform buffer fit
+        bool tws = E > 0 && twb + per <= (size_t)smem_optin;
+        if (force_t == 0) tws = false;
+        const size_t avail = smem_optin - (tws ? twb : 0);
         int G = std::max(1, maxT / tpt);
-        G = std::min<int>(G, (int)(smem_optin / per));
+        G = std::min<int>(G, (int)(avail / per));
         G = std::min(G, 8);
         if (force_g > 0 && force_g <= G) G = force_g;
         p->elems = E;
+        p->tws = tws;
         p->fft = d;
         p->rows.tpt = p->cols.tpt = tpt;
         p->rows.groups = p->cols.groups = G;
-        p->rows.smem = p->cols.smem = per * G;
+        p->rows.smem = p->cols.smem = (tws ? twb : 0) + per * G;
+        int bps = 1;
+        WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, p->rows.smem)));
+        p->rows.max_ctas = p->cols.max_ctas = bps * sms;
         return CONV_OK;
     }
     return fail(CONV_EUNSUPPORTED, "M = " + std::to_string(M) +
@@ -166,20 +215,10 @@ conv_status select_transform(conv_plan_s *p)
 conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
                             double alpha_re, double alpha_im, double beta, void *ws, cudaStream_t st)
 {
-    if (p->prec == CONV_P_FP64) {
-        switch (p->elems) {
-        case 8: return run_pipeline<double, 8>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
-        case 12: return run_pipeline<double, 12>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
-        case 24: return run_pipeline<double, 24>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
-        default: return run_pipeline<double, 0>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
-        }
-    }
-    switch (p->elems) {
-    case 12: return run_pipeline<float, 12>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
-    case 16: return run_pipeline<float, 16>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
-    case 24: return run_pipeline<float, 24>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
-    default: return run_pipeline<float, 0>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
-    }
+    conv_status rc = CONV_OK;
+    WSC_DISPATCH(p->prec, p->elems, p->tws,
+                 rc = (run_pipeline<T_, E_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
+    return rc;
 }
 
 }  // namespace wsc

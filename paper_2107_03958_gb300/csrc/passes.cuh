@@ -1,5 +1,10 @@
 // passes.cuh -- kernel templates of the three fused convolution passes (instantiated per
-// precision in passes_f64.cu / passes_f32.cu; host dispatch in passes.cu).
+// precision in passes_f64*.cu / passes_f32*.cu; host dispatch in passes.cu).
+//
+// Every pass kernel is persistent: the grid holds as many CTAs as fit on the GPU at once, and
+// each CTA loops over work items (a row pair, a row or a column of one density), G items at a
+// time, one per thread group of `tpt` threads.  With TWS the CTA first copies the length-M
+// twiddle table into shared memory once, so the butterflies' twiddle reads never leave the SM.
 #pragma once
 #include "wsconv_internal.h"
 
@@ -7,293 +12,368 @@ namespace wsc {
 
 #define WSC_LB(T, E) __launch_bounds__(maxt<T, E>::v, 1)
 
-// ============================================================================ R2R pipeline
-template <typename T, int E>
-__global__ void WSC_LB(T, E)
-k_r2r_rows_fwd(const T *__restrict__ u, const T *__restrict__ mask, typename cvec<T>::t *__restrict__ W,
-               int n, int h, const FFTDesc *__restrict__ P, const typename cvec<T>::t *__restrict__ tw, int tpt)
+template <typename T> struct PassArgs {
+    typedef typename cvec<T>::t V;
+    const void *in;        // pass 1: u; passes 2, 3: the spectrum workspace
+    const T *mask;         // pass 1: optional n x n multiplier
+    void *out;             // passes 1, 2: the workspace; pass 3: the result
+    const void *ghat;      // pass 2: moment quadrant [k2][k1] (T or complex V)
+    const void *u;         // pass 3: u for the beta term
+    const V *tw;           // twiddles exp(-2 pi i t / M), global
+    const FFTDesc *P;
+    int n, h, M, tpt;
+    int units;             // work items over the whole batch
+    int batch;
+    V alpha;               // pass 3 scale (already times 1/M^2)
+    T beta;                // pass 3: out = beta u + alpha (.)
+};
+
+// Shared-memory carve-up: [twiddles (M) if TWS][group 0 buffer][group 1 buffer]...
+template <typename T, bool TWS>
+__device__ __forceinline__ typename cvec<T>::t *setup_smem(const PassArgs<T> &a, const typename cvec<T>::t *&twp,
+                                                           int g)
 {
     typedef typename cvec<T>::t V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = __ldg(&P->L);
-    const int g = threadIdx.x / tpt, lt = threadIdx.x - g * tpt;
-    const int G = blockDim.x / tpt;
-    V *buf = reinterpret_cast<V *>(smem_raw) + (size_t)g * padded_len<T>(M);
-    const int pair = blockIdx.x * G + g;
-    const int j1 = 2 * pair;
-    const bool valid = j1 < n, has2 = j1 + 1 < n;
-    const size_t bo = (size_t)blockIdx.y * n * n;
-    const T *ua = u + bo + (size_t)j1 * n, *ub = ua + n;
-    const T *ma = mask ? mask + (size_t)j1 * n : nullptr, *mb = mask ? ma + n : nullptr;
-    for (int e = lt; e < M; e += tpt) {
-        V z = cmk<V>(0, 0);
-        if (valid && e < n) {
-            T a = ua[e], b = has2 ? ub[e] : (T)0;
-            if (mask) {
-                a *= ma[e];
-                if (has2) b *= mb[e];
-            }
-            z = cmk<V>(a, b);
-        }
-        buf[pidx<T>(e)] = z;
+    V *base = reinterpret_cast<V *>(smem_raw);
+    if (TWS) {
+        for (int t = threadIdx.x; t < a.M; t += blockDim.x) base[t] = __ldg(&a.tw[t]);
+        __syncthreads();
+        twp = base;
+        base += a.M;
+    } else {
+        twp = a.tw;
     }
-    __syncthreads();
-    fft_smem<T, E, false>(buf, P, tw, lt, tpt);
-    if (!valid) return;
-    V *Wb = W + (size_t)blockIdx.y * h * n;
-    for (int k = lt; k < h; k += tpt) {
-        V Zk = buf[pidx<T>(k)], Zm = buf[pidx<T>(k == 0 ? 0 : M - k)];
-        // A = (Z_k + conj Z_{M-k}) / 2,  B = (Z_k - conj Z_{M-k}) / (2i)
-        V A = cmk<V>((T)0.5 * (Zk.x + Zm.x), (T)0.5 * (Zk.y - Zm.y));
-        Wb[(size_t)k * n + j1] = A;
-        if (has2) {
-            V B = cmk<V>((T)0.5 * (Zk.y + Zm.y), (T)-0.5 * (Zk.x - Zm.x));
-            Wb[(size_t)k * n + j1 + 1] = B;
+    return base + (size_t)g * padded_len<T>(a.M);
+}
+
+// ============================================================================ R2R pipeline
+// pass 1: two real rows j1, j1+1 packed as z = u_a + i u_b, zero-extended to M, forward FFT,
+// Hermitian split A_k = (Z_k + conj Z_{M-k})/2, B_k = (Z_k - conj Z_{M-k})/(2i), k <= M/2.
+template <typename T, int E, bool TWS>
+__global__ void WSC_LB(T, E) k_r2r_rows_fwd(const PassArgs<T> a)
+{
+    typedef typename cvec<T>::t V;
+    const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
+    const V *twp;
+    V *buf = setup_smem<T, TWS>(a, twp, g);
+    const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2;
+    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+        const int unit = base + g;
+        const bool valid = unit < a.units;
+        const int b = valid ? unit / pairs : 0, j1 = valid ? 2 * (unit - b * pairs) : 0;
+        const bool has2 = valid && j1 + 1 < n;
+        const T *ua = reinterpret_cast<const T *>(a.in) + (size_t)b * n * n + (size_t)j1 * n;
+        const T *ma = a.mask ? a.mask + (size_t)j1 * n : nullptr;
+        for (int e = lt; e < M; e += a.tpt) {
+            V z = cmk<V>(0, 0);
+            if (valid && e < n) {
+                T x = ua[e], y = has2 ? ua[n + e] : (T)0;
+                if (ma) {
+                    x *= ma[e];
+                    if (has2) y *= ma[n + e];
+                }
+                z = cmk<V>(x, y);
+            }
+            buf[pidx<T>(e)] = z;
         }
+        __syncthreads();
+        fft_smem<T, E, false, TWS>(buf, a.P, twp, lt, a.tpt);
+        if (valid) {
+            V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * h * n;
+            for (int k = lt; k < h; k += a.tpt) {
+                V Zk = buf[pidx<T>(k)], Zm = buf[pidx<T>(k == 0 ? 0 : M - k)];
+                Wb[(size_t)k * n + j1] = cmk<V>((T)0.5 * (Zk.x + Zm.x), (T)0.5 * (Zk.y - Zm.y));
+                if (has2) Wb[(size_t)k * n + j1 + 1] = cmk<V>((T)0.5 * (Zk.y + Zm.y), (T)-0.5 * (Zk.x - Zm.x));
+            }
+        }
+        __syncthreads();
     }
 }
 
-// Column pass, real ghat.  grid = (batch, column blocks): the batch's CTAs for one column block
-// run side by side, so each ghat column is fetched from HBM once per batch.
-template <typename T, int E>
-__global__ void WSC_LB(T, E)
-k_r2r_cols(typename cvec<T>::t *__restrict__ W, const T *__restrict__ ghat, int n, int h,
-           const FFTDesc *__restrict__ P, const typename cvec<T>::t *__restrict__ tw, int tpt)
+// pass 2: per column k2 <= M/2 of one density: forward FFT over the n stored rows, times the real
+// ghat(|k1|, k2), inverse FFT, keep rows j1 < n.  Work items run batch-fastest, so the CTAs
+// handling one column for all densities run side by side and share its ghat column in L2.
+template <typename T, int E, bool TWS>
+__global__ void WSC_LB(T, E) k_r2r_cols(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = __ldg(&P->L);
-    const int g = threadIdx.x / tpt, lt = threadIdx.x - g * tpt;
-    const int G = blockDim.x / tpt;
-    V *buf = reinterpret_cast<V *>(smem_raw) + (size_t)g * padded_len<T>(M);
-    const int k2 = blockIdx.y * G + g;
-    const bool valid = k2 < h;
-    V *col = W + (size_t)blockIdx.x * h * n + (size_t)k2 * n;
-    for (int e = lt; e < M; e += tpt) buf[pidx<T>(e)] = (valid && e < n) ? col[e] : cmk<V>(0, 0);
-    __syncthreads();
-    fft_smem<T, E, false>(buf, P, tw, lt, tpt);
-    if (valid) {
+    const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
+    const V *twp;
+    V *buf = setup_smem<T, TWS>(a, twp, g);
+    const int n = a.n, M = a.M, h = a.h;
+    const T *ghat = reinterpret_cast<const T *>(a.ghat);
+    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+        const int unit = base + g;
+        const bool valid = unit < a.units;
+        const int k2 = valid ? unit / a.batch : 0, b = valid ? unit - k2 * a.batch : 0;
+        V *col = reinterpret_cast<V *>(a.out) + (size_t)b * h * n + (size_t)k2 * n;
+        for (int e = lt; e < M; e += a.tpt) buf[pidx<T>(e)] = (valid && e < n) ? col[e] : cmk<V>(0, 0);
+        __syncthreads();
+        fft_smem<T, E, false, TWS>(buf, a.P, twp, lt, a.tpt);
         const T *gc = ghat + (size_t)k2 * h;
-        for (int e = lt; e < M; e += tpt) {
-            int k1 = e <= M / 2 ? e : M - e;
+        for (int e = lt; e < M; e += a.tpt) {
+            const int k1 = e <= M / 2 ? e : M - e;
             buf[pidx<T>(e)] = cscale(buf[pidx<T>(e)], __ldg(&gc[k1]));
         }
+        __syncthreads();
+        fft_smem<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt);
+        if (valid)
+            for (int e = lt; e < n; e += a.tpt) col[e] = buf[pidx<T>(e)];
+        __syncthreads();
     }
-    __syncthreads();
-    fft_smem<T, E, true>(buf, P, tw, lt, tpt);
-    if (valid)
-        for (int e = lt; e < n; e += tpt) col[e] = buf[pidx<T>(e)];
 }
 
-template <typename T, int E>
-__global__ void WSC_LB(T, E)
-k_r2r_rows_inv(const typename cvec<T>::t *__restrict__ W, const T *__restrict__ u, T *__restrict__ out,
-               int n, int h, const FFTDesc *__restrict__ P, const typename cvec<T>::t *__restrict__ tw, int tpt,
-               T alpha, T beta)
+// pass 3: rows j1, j1+1: Z_k = A_k + i B_k (k <= M/2), Z_{M-k} = conj A_k + i conj B_k, inverse FFT,
+// out_a = Re Z, out_b = Im Z on j2 < n, times alpha (1/M^2), plus beta u.
+template <typename T, int E, bool TWS>
+__global__ void WSC_LB(T, E) k_r2r_rows_inv(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = __ldg(&P->L);
-    const int g = threadIdx.x / tpt, lt = threadIdx.x - g * tpt;
-    const int G = blockDim.x / tpt;
-    V *buf = reinterpret_cast<V *>(smem_raw) + (size_t)g * padded_len<T>(M);
-    const int pair = blockIdx.x * G + g;
-    const int j1 = 2 * pair;
-    const bool valid = j1 < n, has2 = j1 + 1 < n;
-    const V *Wb = W + (size_t)blockIdx.y * h * n;
-    // Z_k = A_k + i B_k for k <= M/2 and Z_{M-k} = conj(A_k) + i conj(B_k)
-    for (int k = lt; k < h; k += tpt) {
-        V A = cmk<V>(0, 0), B = cmk<V>(0, 0);
+    const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
+    const V *twp;
+    V *buf = setup_smem<T, TWS>(a, twp, g);
+    const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2;
+    const T alpha = a.alpha.x, beta = a.beta;
+    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+        const int unit = base + g;
+        const bool valid = unit < a.units;
+        const int b = valid ? unit / pairs : 0, j1 = valid ? 2 * (unit - b * pairs) : 0;
+        const bool has2 = valid && j1 + 1 < n;
+        const V *Wb = reinterpret_cast<const V *>(a.in) + (size_t)b * h * n;
+        for (int k = lt; k < h; k += a.tpt) {
+            V A = cmk<V>(0, 0), B = cmk<V>(0, 0);
+            if (valid) {
+                A = Wb[(size_t)k * n + j1];
+                if (has2) B = Wb[(size_t)k * n + j1 + 1];
+            }
+            buf[pidx<T>(k)] = cmk<V>(A.x - B.y, A.y + B.x);
+            if (k > 0 && k < M - k) buf[pidx<T>(M - k)] = cmk<V>(A.x + B.y, B.x - A.y);
+        }
+        __syncthreads();
+        fft_smem<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt);
         if (valid) {
-            A = Wb[(size_t)k * n + j1];
-            if (has2) B = Wb[(size_t)k * n + j1 + 1];
+            const size_t ro = (size_t)b * n * n + (size_t)j1 * n;
+            T *oa = reinterpret_cast<T *>(a.out) + ro;
+            const T *ua = reinterpret_cast<const T *>(a.u) + ro;
+            for (int e = lt; e < n; e += a.tpt) {
+                V z = buf[pidx<T>(e)];
+                T ra = alpha * z.x, rb = alpha * z.y;
+                if (beta != (T)0) {
+                    ra += beta * ua[e];
+                    if (has2) rb += beta * ua[n + e];
+                }
+                oa[e] = ra;
+                if (has2) oa[n + e] = rb;
+            }
         }
-        buf[pidx<T>(k)] = cmk<V>(A.x - B.y, A.y + B.x);
-        if (k > 0 && k < M - k) buf[pidx<T>(M - k)] = cmk<V>(A.x + B.y, B.x - A.y);
-    }
-    __syncthreads();
-    fft_smem<T, E, true>(buf, P, tw, lt, tpt);
-    if (!valid) return;
-    const size_t bo = (size_t)blockIdx.y * n * n;
-    T *oa = out + bo + (size_t)j1 * n, *ob = oa + n;
-    const T *ua = u + bo + (size_t)j1 * n, *ub = ua + n;
-    for (int e = lt; e < n; e += tpt) {
-        V z = buf[pidx<T>(e)];
-        T ra = alpha * z.x, rb = alpha * z.y;
-        if (beta != (T)0) {
-            ra += beta * ua[e];
-            if (has2) rb += beta * ub[e];
-        }
-        oa[e] = ra;
-        if (has2) ob[e] = rb;
+        __syncthreads();
     }
 }
 
 // ============================================================================ C2C pipeline
-template <typename T, int E, bool IN_REAL>
-__global__ void WSC_LB(T, E)
-k_c2c_rows_fwd(const void *__restrict__ uin, const T *__restrict__ mask, typename cvec<T>::t *__restrict__ W,
-               int n, const FFTDesc *__restrict__ P, const typename cvec<T>::t *__restrict__ tw, int tpt)
+template <typename T, int E, bool TWS, bool IN_REAL>
+__global__ void WSC_LB(T, E) k_c2c_rows_fwd(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = __ldg(&P->L);
-    const int g = threadIdx.x / tpt, lt = threadIdx.x - g * tpt;
-    const int G = blockDim.x / tpt;
-    V *buf = reinterpret_cast<V *>(smem_raw) + (size_t)g * padded_len<T>(M);
-    const int j1 = blockIdx.x * G + g;
-    const bool valid = j1 < n;
-    const size_t ro = (size_t)blockIdx.y * n * n + (size_t)j1 * n;
-    const T *mr = mask ? mask + (size_t)j1 * n : nullptr;
-    for (int e = lt; e < M; e += tpt) {
-        V z = cmk<V>(0, 0);
-        if (valid && e < n) {
-            if (IN_REAL) z.x = reinterpret_cast<const T *>(uin)[ro + e];
-            else z = reinterpret_cast<const V *>(uin)[ro + e];
-            if (mask) z = cscale(z, mr[e]);
-        }
-        buf[pidx<T>(e)] = z;
-    }
-    __syncthreads();
-    fft_smem<T, E, false>(buf, P, tw, lt, tpt);
-    if (!valid) return;
-    V *Wb = W + (size_t)blockIdx.y * M * n;
-    for (int k = lt; k < M; k += tpt) Wb[(size_t)k * n + j1] = buf[pidx<T>(k)];
-}
-
-// Column pass; ghat real (CG = false) or complex (CG = true), quadrant [k2'][k1'].
-template <typename T, int E, bool CG>
-__global__ void WSC_LB(T, E)
-k_c2c_cols(typename cvec<T>::t *__restrict__ W, const void *__restrict__ ghat, int n, int h,
-           const FFTDesc *__restrict__ P, const typename cvec<T>::t *__restrict__ tw, int tpt)
-{
-    typedef typename cvec<T>::t V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = __ldg(&P->L);
-    const int g = threadIdx.x / tpt, lt = threadIdx.x - g * tpt;
-    const int G = blockDim.x / tpt;
-    V *buf = reinterpret_cast<V *>(smem_raw) + (size_t)g * padded_len<T>(M);
-    const int k2 = blockIdx.y * G + g;
-    const bool valid = k2 < M;
-    V *col = W + (size_t)blockIdx.x * M * n + (size_t)k2 * n;
-    for (int e = lt; e < M; e += tpt) buf[pidx<T>(e)] = (valid && e < n) ? col[e] : cmk<V>(0, 0);
-    __syncthreads();
-    fft_smem<T, E, false>(buf, P, tw, lt, tpt);
-    if (valid) {
-        const int k2q = k2 <= M / 2 ? k2 : M - k2;
-        for (int e = lt; e < M; e += tpt) {
-            int k1 = e <= M / 2 ? e : M - e;
-            V z = buf[pidx<T>(e)];
-            if (CG) z = cmul(z, __ldg(reinterpret_cast<const V *>(ghat) + (size_t)k2q * h + k1));
-            else z = cscale(z, __ldg(reinterpret_cast<const T *>(ghat) + (size_t)k2q * h + k1));
+    const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
+    const V *twp;
+    V *buf = setup_smem<T, TWS>(a, twp, g);
+    const int n = a.n, M = a.M;
+    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+        const int unit = base + g;
+        const bool valid = unit < a.units;
+        const int b = valid ? unit / n : 0, j1 = valid ? unit - b * n : 0;
+        const size_t ro = (size_t)b * n * n + (size_t)j1 * n;
+        const T *mr = a.mask ? a.mask + (size_t)j1 * n : nullptr;
+        for (int e = lt; e < M; e += a.tpt) {
+            V z = cmk<V>(0, 0);
+            if (valid && e < n) {
+                if (IN_REAL) z.x = reinterpret_cast<const T *>(a.in)[ro + e];
+                else z = reinterpret_cast<const V *>(a.in)[ro + e];
+                if (mr) z = cscale(z, mr[e]);
+            }
             buf[pidx<T>(e)] = z;
         }
+        __syncthreads();
+        fft_smem<T, E, false, TWS>(buf, a.P, twp, lt, a.tpt);
+        if (valid) {
+            V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * M * n;
+            for (int k = lt; k < M; k += a.tpt) Wb[(size_t)k * n + j1] = buf[pidx<T>(k)];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    fft_smem<T, E, true>(buf, P, tw, lt, tpt);
-    if (valid)
-        for (int e = lt; e < n; e += tpt) col[e] = buf[pidx<T>(e)];
 }
 
-template <typename T, int E, bool IN_REAL>
-__global__ void WSC_LB(T, E)
-k_c2c_rows_inv(const typename cvec<T>::t *__restrict__ W, const void *__restrict__ uin,
-               typename cvec<T>::t *__restrict__ out, int n, const FFTDesc *__restrict__ P,
-               const typename cvec<T>::t *__restrict__ tw, int tpt, typename cvec<T>::t alpha, T beta)
+// pass 2, complex pipeline: all M columns; ghat real (CG = false) or complex (CG = true).
+template <typename T, int E, bool TWS, bool CG>
+__global__ void WSC_LB(T, E) k_c2c_cols(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = __ldg(&P->L);
-    const int g = threadIdx.x / tpt, lt = threadIdx.x - g * tpt;
-    const int G = blockDim.x / tpt;
-    V *buf = reinterpret_cast<V *>(smem_raw) + (size_t)g * padded_len<T>(M);
-    const int j1 = blockIdx.x * G + g;
-    const bool valid = j1 < n;
-    const V *Wb = W + (size_t)blockIdx.y * M * n;
-    for (int k = lt; k < M; k += tpt) buf[pidx<T>(k)] = valid ? Wb[(size_t)k * n + j1] : cmk<V>(0, 0);
-    __syncthreads();
-    fft_smem<T, E, true>(buf, P, tw, lt, tpt);
-    if (!valid) return;
-    const size_t ro = (size_t)blockIdx.y * n * n + (size_t)j1 * n;
-    for (int e = lt; e < n; e += tpt) {
-        V z = cmul(buf[pidx<T>(e)], alpha);
-        if (beta != (T)0) {
-            if (IN_REAL) z.x += beta * reinterpret_cast<const T *>(uin)[ro + e];
-            else {
-                V x = reinterpret_cast<const V *>(uin)[ro + e];
-                z.x += beta * x.x;
-                z.y += beta * x.y;
-            }
+    const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
+    const V *twp;
+    V *buf = setup_smem<T, TWS>(a, twp, g);
+    const int n = a.n, M = a.M, h = a.h;
+    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+        const int unit = base + g;
+        const bool valid = unit < a.units;
+        const int k2 = valid ? unit / a.batch : 0, b = valid ? unit - k2 * a.batch : 0;
+        V *col = reinterpret_cast<V *>(a.out) + (size_t)b * M * n + (size_t)k2 * n;
+        for (int e = lt; e < M; e += a.tpt) buf[pidx<T>(e)] = (valid && e < n) ? col[e] : cmk<V>(0, 0);
+        __syncthreads();
+        fft_smem<T, E, false, TWS>(buf, a.P, twp, lt, a.tpt);
+        const int k2q = k2 <= M / 2 ? k2 : M - k2;
+        for (int e = lt; e < M; e += a.tpt) {
+            const int k1 = e <= M / 2 ? e : M - e;
+            V z = buf[pidx<T>(e)];
+            if (CG) z = cmul(z, __ldg(reinterpret_cast<const V *>(a.ghat) + (size_t)k2q * h + k1));
+            else z = cscale(z, __ldg(reinterpret_cast<const T *>(a.ghat) + (size_t)k2q * h + k1));
+            buf[pidx<T>(e)] = z;
         }
-        out[ro + e] = z;
+        __syncthreads();
+        fft_smem<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt);
+        if (valid)
+            for (int e = lt; e < n; e += a.tpt) col[e] = buf[pidx<T>(e)];
+        __syncthreads();
     }
 }
 
+template <typename T, int E, bool TWS, bool IN_REAL>
+__global__ void WSC_LB(T, E) k_c2c_rows_inv(const PassArgs<T> a)
+{
+    typedef typename cvec<T>::t V;
+    const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
+    const V *twp;
+    V *buf = setup_smem<T, TWS>(a, twp, g);
+    const int n = a.n, M = a.M;
+    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+        const int unit = base + g;
+        const bool valid = unit < a.units;
+        const int b = valid ? unit / n : 0, j1 = valid ? unit - b * n : 0;
+        const V *Wb = reinterpret_cast<const V *>(a.in) + (size_t)b * M * n;
+        for (int k = lt; k < M; k += a.tpt) buf[pidx<T>(k)] = valid ? Wb[(size_t)k * n + j1] : cmk<V>(0, 0);
+        __syncthreads();
+        fft_smem<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt);
+        if (valid) {
+            const size_t ro = (size_t)b * n * n + (size_t)j1 * n;
+            V *o = reinterpret_cast<V *>(a.out) + ro;
+            for (int e = lt; e < n; e += a.tpt) {
+                V z = cmul(buf[pidx<T>(e)], a.alpha);
+                if (a.beta != (T)0) {
+                    if (IN_REAL) z.x += a.beta * reinterpret_cast<const T *>(a.u)[ro + e];
+                    else {
+                        V x = reinterpret_cast<const V *>(a.u)[ro + e];
+                        z.x += a.beta * x.x;
+                        z.y += a.beta * x.y;
+                    }
+                }
+                o[e] = z;
+            }
+        }
+        __syncthreads();
+    }
+}
 
-template <typename T, int E> conv_status set_attrs(int smem)
+// ============================================================================ host glue
+template <typename T, int E, bool TWS> conv_status set_attrs(int smem)
 {
 #define WSC_ATTR(k) WSC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))
-    WSC_ATTR((k_r2r_rows_fwd<T, E>));
-    WSC_ATTR((k_r2r_cols<T, E>));
-    WSC_ATTR((k_r2r_rows_inv<T, E>));
-    WSC_ATTR((k_c2c_rows_fwd<T, E, true>));
-    WSC_ATTR((k_c2c_rows_fwd<T, E, false>));
-    WSC_ATTR((k_c2c_cols<T, E, true>));
-    WSC_ATTR((k_c2c_cols<T, E, false>));
-    WSC_ATTR((k_c2c_rows_inv<T, E, true>));
-    WSC_ATTR((k_c2c_rows_inv<T, E, false>));
+    WSC_ATTR((k_r2r_rows_fwd<T, E, TWS>));
+    WSC_ATTR((k_r2r_cols<T, E, TWS>));
+    WSC_ATTR((k_r2r_rows_inv<T, E, TWS>));
+    WSC_ATTR((k_c2c_rows_fwd<T, E, TWS, true>));
+    WSC_ATTR((k_c2c_rows_fwd<T, E, TWS, false>));
+    WSC_ATTR((k_c2c_cols<T, E, TWS, true>));
+    WSC_ATTR((k_c2c_cols<T, E, TWS, false>));
+    WSC_ATTR((k_c2c_rows_inv<T, E, TWS, true>));
+    WSC_ATTR((k_c2c_rows_inv<T, E, TWS, false>));
 #undef WSC_ATTR
     return CONV_OK;
 }
 
-template <typename T, int E>
+// CTAs of one pass kernel that fit on an SM at this launch shape.
+template <typename T, int E, bool TWS> int blocks_per_sm(int threads, size_t smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_r2r_cols<T, E, TWS>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+template <typename T, int E, bool TWS>
 conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
-                       double are, double aim, double beta, void *ws, cudaStream_t st)
+                         double are, double aim, double beta, void *ws, cudaStream_t st)
 {
     typedef typename cvec<T>::t V;
     const int n = p->n, M = p->M, h = p->h;
     const double sc = 1.0 / ((double)M * (double)M);
-    const V *tw = reinterpret_cast<const V *>(p->tw);
-    V *W = reinterpret_cast<V *>(ws);
-    const T *mk = reinterpret_cast<const T *>(mask);
-    const void *gh = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
+    PassArgs<T> a;
+    a.mask = reinterpret_cast<const T *>(mask);
+    a.ghat = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
+    a.u = u;
+    a.tw = reinterpret_cast<const V *>(p->tw);
+    a.P = p->fft_dev;
+    a.n = n;
+    a.h = h;
+    a.M = M;
+    a.batch = batch;
+    a.alpha = cmk<V>((T)(are * sc), (T)(aim * sc));
+    a.beta = (T)beta;
     const LaunchShape &R = p->rows, &C = p->cols;
-    const FFTDesc *fd = p->fft_dev;
+    auto grid = [&](const LaunchShape &S, int units) {
+        long long need = (units + S.groups - 1) / S.groups;
+        return (unsigned)std::min<long long>(need, (long long)S.max_ctas);
+    };
     cudaEvent_t *ev = timing_slot(p);
     if (ev) cudaEventRecord(ev[0], st);
     if (p->io == CONV_IO_R2R) {
-        int units = (n + 1) / 2;
-        dim3 g1((units + R.groups - 1) / R.groups, batch);
-        k_r2r_rows_fwd<T, E><<<g1, R.tpt * R.groups, R.smem, st>>>(reinterpret_cast<const T *>(u), mk, W, n, h, fd, tw, R.tpt);
+        a.tpt = R.tpt;
+        a.in = u;
+        a.out = ws;
+        a.units = batch * ((n + 1) / 2);
+        k_r2r_rows_fwd<T, E, TWS><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[1], st);
-        dim3 g2(batch, (h + C.groups - 1) / C.groups);
-        k_r2r_cols<T, E><<<g2, C.tpt * C.groups, C.smem, st>>>(W, reinterpret_cast<const T *>(gh), n, h, fd, tw, C.tpt);
+        a.tpt = C.tpt;
+        a.in = ws;
+        a.units = batch * h;
+        k_r2r_cols<T, E, TWS><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[2], st);
-        k_r2r_rows_inv<T, E><<<g1, R.tpt * R.groups, R.smem, st>>>(W, reinterpret_cast<const T *>(u), reinterpret_cast<T *>(out), n, h, fd, tw, R.tpt, (T)(are * sc), (T)beta);
+        a.tpt = R.tpt;
+        a.out = out;
+        a.units = batch * ((n + 1) / 2);
+        k_r2r_rows_inv<T, E, TWS><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
     } else {
         const bool in_real = p->io == CONV_IO_R2C;
-        dim3 g1((n + R.groups - 1) / R.groups, batch);
+        a.tpt = R.tpt;
+        a.in = u;
+        a.out = ws;
+        a.units = batch * n;
         if (in_real)
-            k_c2c_rows_fwd<T, E, true><<<g1, R.tpt * R.groups, R.smem, st>>>(u, mk, W, n, fd, tw, R.tpt);
+            k_c2c_rows_fwd<T, E, TWS, true><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
         else
-            k_c2c_rows_fwd<T, E, false><<<g1, R.tpt * R.groups, R.smem, st>>>(u, mk, W, n, fd, tw, R.tpt);
+            k_c2c_rows_fwd<T, E, TWS, false><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[1], st);
-        dim3 g2(batch, (M + C.groups - 1) / C.groups);
+        a.tpt = C.tpt;
+        a.in = ws;
+        a.units = batch * M;
         if (p->complex_ghat)
-            k_c2c_cols<T, E, true><<<g2, C.tpt * C.groups, C.smem, st>>>(W, gh, n, h, fd, tw, C.tpt);
+            k_c2c_cols<T, E, TWS, true><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
         else
-            k_c2c_cols<T, E, false><<<g2, C.tpt * C.groups, C.smem, st>>>(W, gh, n, h, fd, tw, C.tpt);
+            k_c2c_cols<T, E, TWS, false><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[2], st);
-        V al = cmk<V>((T)(are * sc), (T)(aim * sc));
+        a.tpt = R.tpt;
+        a.out = out;
+        a.units = batch * n;
         if (in_real)
-            k_c2c_rows_inv<T, E, true><<<g1, R.tpt * R.groups, R.smem, st>>>(W, u, reinterpret_cast<V *>(out), n, fd, tw, R.tpt, al, (T)beta);
+            k_c2c_rows_inv<T, E, TWS, true><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
         else
-            k_c2c_rows_inv<T, E, false><<<g1, R.tpt * R.groups, R.smem, st>>>(W, u, reinterpret_cast<V *>(out), n, fd, tw, R.tpt, al, (T)beta);
+            k_c2c_rows_inv<T, E, TWS, false><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
     }
     if (ev) cudaEventRecord(ev[3], st);
     WSC_CUDA(cudaGetLastError());
     return CONV_OK;
 }
-
 
 }  // namespace wsc

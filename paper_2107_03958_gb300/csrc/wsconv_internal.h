@@ -28,16 +28,18 @@ conv_status cuda_fail(cudaError_t e, const char *what);
 // guarded stages): keeps the E values in registers.
 template <typename T, int E> struct maxt { static const int v = (E == 0 || (int)(2 * sizeof(T) * E) > 160) ? 512 : 1024; };
 
-template <typename T, int E>
+template <typename T, int E, bool TWS>
 conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
                          double are, double aim, double beta, void *ws, cudaStream_t st);
-template <typename T, int E> conv_status set_attrs(int smem);
+template <typename T, int E, bool TWS> conv_status set_attrs(int smem);
+template <typename T, int E, bool TWS> int blocks_per_sm(int threads, size_t smem);
 
 // Launch shape of one pass family (rows or columns).
 struct LaunchShape {
-    int tpt;      // threads per transform
-    int groups;   // transforms per CTA
-    size_t smem;  // dynamic shared memory bytes
+    int tpt;       // threads per transform
+    int groups;    // transforms per CTA
+    size_t smem;   // dynamic shared memory bytes
+    int max_ctas;  // persistent grid size (CTAs resident at once)
 };
 
 }  // namespace wsc
@@ -52,6 +54,7 @@ struct conv_plan_s {
     bool complex_ghat;
     int device;
     int elems;  // complex elements per thread in the transform kernels
+    bool tws;   // twiddle table staged in shared memory
     wsc::FFTDesc fft;
     wsc::FFTDesc *fft_dev = nullptr;  // device copy read by the pass kernels
     // FP64 moment quadrant [k2][k1], k1, k2 in [0, h): real (h*h doubles) or complex (h*h double2)
