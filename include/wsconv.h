@@ -155,6 +155,23 @@ typedef struct {
 conv_status ls_solve(conv_plan_t plan, const double *m, const void *f, void *x, const ls_opts *opts,
                      ls_info *info, void *stream);
 
+/* Fourier-smoothed indicator mask for discontinuous densities (Sec. 2.4, eq. (tfs)):
+ *     mask_j = Re chi^n_Omega(x_j) * psi(x_j),  x_j = j/n,
+ *     chi^n_Omega(x) = sum_{k in F_n} chihat_b(k) e^{2 pi i k.x/b},
+ *     chihat_b(k) = (1/b^2) int_Omega e^{-2 pi i k.y/b} dy   (closed forms for a disk and a rectangle),
+ * i.e. eq. (tfs) read with the plan's period b and index set F_n.  psi(x) = w(x1) w(x2) is the
+ * smooth window: w = 1 on [delta, 1 - delta], ramping to 0 at the edges of D through the
+ * half-window varkappa(t) = exp(2 e^{-1/t}/(t - 1)) of eq. (halfwindow1); delta <= 0 omits psi.
+ * The approximation of A u is then A_n(u~ . mask) with u~ a smooth extension of u (pass the mask
+ * to conv_apply).
+ *   shape: 0 = disk, geom = {c1, c2, r}; 1 = rectangle [x0, x1] x [y0, y1], geom = {x0, x1, y0, y1}
+ *          (HOST array).
+ *   mask:  device, n x n, the plan's real type.
+ * Computed in FP64 by one pruned M x M inverse transform; allocates temporary device buffers and
+ * synchronises `stream` (geometry-time operation). */
+conv_status conv_fs_mask(conv_plan_t plan, int shape, const double *geom, double delta, void *mask,
+                         void *stream);
+
 /* Per-pass device timing (benchmark instrumentation; no counterpart in the paper).  While enabled,
  * every apply on this plan records CUDA events around its three kernel launches on the apply's
  * stream (no synchronisation).  conv_timing_read waits for the recorded events, returns the summed

@@ -118,6 +118,16 @@ class ConvPlan:
 
     __call__ = apply
 
+    def fs_mask(self, shape, geom, delta=0.15, stream=None):
+        """Fourier-smoothed indicator chi^n psi on the n x n grid (Sec. 2.4, eq. (tfs)).
+        shape 'disk': geom = (c1, c2, r); 'rect': geom = (x0, x1, y0, y1)."""
+        g = np.ascontiguousarray(geom, dtype=np.float64)
+        mask = torch.empty((self.n, self.n), dtype=self.real_dtype, device="cuda")
+        N.check(self._lib.conv_fs_mask(self._h, 0 if shape == "disk" else 1,
+                                       g.ctypes.data_as(ctypes.c_void_p), float(delta),
+                                       ctypes.c_void_p(mask.data_ptr()), _stream_ptr(stream)))
+        return mask
+
     def timing(self, enable):
         """Record per-pass CUDA events on every apply (benchmark instrumentation)."""
         N.check(self._lib.conv_timing_enable(self._h, int(bool(enable))))

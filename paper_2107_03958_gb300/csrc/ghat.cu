@@ -15,7 +15,9 @@
 //   Helmholtz g = scale (i/4) H0^(1)(kappa |x|): the closed forms of Sec. 2.2, with the k = 0 value
 //            taken with -2/(kappa pi) (the s -> 0 limit of the k != 0 line; the printed sign is
 //            wrong), and direct quadrature when |s - kappa| < 0.05 kappa, where the k != 0 line is a
-//            near 0/0 quotient (its numerator vanishes at s = kappa) and loses digits.
+//            near 0/0 quotient (its numerator vanishes at s = kappa) and loses digits.  H0 and H1
+//            at the single argument kappa a, and H0 at the quadrature nodes, are tabulated once on
+//            the host (the C library's j0/y0/j1/y1); the device evaluates J0, J1 at z = s a per k.
 #include <cmath>
 #include <vector>
 
@@ -63,28 +65,24 @@ __device__ double pow_moment_quad(double gamma, double s, double a)
 }
 
 // 2 pi (i/4) int_0^a H0(kappa rho) J0(s rho) rho d rho = i pi a^2 int_0^1 H0(kappa a t^2) J0(s a t^2) t^3 dt
-__device__ double2 helm_moment_quad(double kappa, double s, double a)
+// by composite Gauss-Legendre.  The nodes' H0(kappa a t^2) do not depend on s; the host tabulates
+// them once per plan (tab: per node t, weight, Re H0, Im H0), so only J0 is evaluated here.
+__device__ double2 helm_moment_quad(const double *__restrict__ tab, int nodes, double s, double a)
 {
-    int P = (int)ceil((kappa + s) * a / 3.0);
-    if (P < 32) P = 32;
-    const double hw = 0.5 / P;
     double sr = 0.0, si = 0.0;
-    for (int p = 0; p < P; ++p) {
-        double mid = (p + 0.5) / P;
-        for (int i = 0; i < GL_NODES; ++i) {
-            double t = mid + hw * c_glx[i], t2 = t * t;
-            double w = c_glw[i] * j0(s * a * t2) * t2 * t;
-            sr += w * j0(kappa * a * t2);
-            si += w * y0(kappa * a * t2);
-        }
+    for (int i = 0; i < nodes; ++i) {
+        const double t = tab[4 * i], t2 = t * t;
+        const double w = tab[4 * i + 1] * j0(s * a * t2) * t2 * t;
+        sr += w * tab[4 * i + 2];
+        si += w * tab[4 * i + 3];
     }
-    // i pi a^2 (sr + i si) hw
-    double c = M_PI * a * a * hw;
+    const double c = M_PI * a * a;
     return make_double2(-c * si, c * sr);
 }
 
+// hka = (J0, Y0, J1, Y1)(kappa a), tabulated on the host.
 __global__ void k_ghat(int family, double gamma, double kappa, double scale, double b, double a,
-                       int h, double *out)
+                       int h, double *out, double4 hka, const double *__restrict__ htab, int hnodes)
 {
     const long long N = (long long)h * h;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
@@ -114,13 +112,13 @@ __global__ void k_ghat(int family, double gamma, double kappa, double scale, dou
             if (km == 0.0) {
                 // (pi/(2 kappa)) (i a J1(ka) - a Y1(ka) - 2/(kappa pi))
                 double c = M_PI / (2.0 * kappa);
-                r = make_double2(c * (-a * y1(ka) - 2.0 / (kappa * M_PI)), c * a * j1(ka));
+                r = make_double2(c * (-a * hka.w - 2.0 / (kappa * M_PI)), c * a * hka.z);
             } else if (fabs(s - kappa) < HELM_RES_REL * kappa) {
-                r = helm_moment_quad(kappa, s, a);
+                r = helm_moment_quad(htab, hnodes, s, a);
             } else {
                 // (i pi/2) (z J1(z) H0(ka) - ka J0(z) H1(ka) - 2i/pi) / (s^2 - kappa^2)
                 double J0z = j0(z), J1z = j1(z);
-                double H0r = j0(ka), H0i = y0(ka), H1r = j1(ka), H1i = y1(ka);
+                double H0r = hka.x, H0i = hka.y, H1r = hka.z, H1i = hka.w;
                 double nr = z * J1z * H0r - ka * J0z * H1r;
                 double ni = z * J1z * H0i - ka * J0z * H1i - 2.0 / M_PI;
                 double d = 0.5 * M_PI / (s * s - kappa * kappa);
@@ -176,9 +174,41 @@ conv_status build_ghat(conv_plan_s *p)
         return fail(CONV_ENOMEM, "cudaMalloc of the moment table failed");
     }
     const double scale = p->kern.scale == 0.0 ? 1.0 : p->kern.scale;
+    // Helmholtz: H0, H1 at kappa a and the quadrature table for the resonance band
+    double4 hka = make_double4(0, 0, 0, 0);
+    double *htab = nullptr;
+    int hnodes = 0;
+    if (p->kern.family == CONV_K_HELMHOLTZ) {
+        const double kappa = p->kern.kappa, a = p->a, ka = kappa * a;
+        hka = make_double4(::j0(ka), ::y0(ka), ::j1(ka), ::y1(ka));
+        // panels of t-width 1/P with (kappa + s) a / P <= 3 for s up to the band's top
+        const int P = std::max(32, (int)std::ceil((2.0 + HELM_RES_REL) * kappa * a / 3.0));
+        std::vector<double> tab(4 * (size_t)P * GL_NODES);
+        const double hw = 0.5 / P;
+        for (int q = 0; q < P; ++q)
+            for (int i = 0; i < GL_NODES; ++i) {
+                const double t = (q + 0.5) / P + hw * gx[i], arg = ka * t * t;
+                double *e = &tab[4 * ((size_t)q * GL_NODES + i)];
+                e[0] = t;
+                e[1] = hw * gw[i];
+                e[2] = ::j0(arg);
+                e[3] = ::y0(arg);
+            }
+        hnodes = P * GL_NODES;
+        if (cudaMalloc(&htab, tab.size() * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CONV_ENOMEM, "cudaMalloc of the Helmholtz quadrature table failed");
+        }
+        WSC_CUDA(cudaMemcpy(htab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
     int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
     k_ghat<<<blocks, 256>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, p->h,
-                            p->ghat64);
+                            p->ghat64, hka, htab, hnodes);
+    if (htab) {
+        cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(htab);
+        if (e != cudaSuccess) return cuda_fail(e, "moment table kernel");
+    }
     WSC_CUDA(cudaGetLastError());
     if (p->prec == CONV_P_FP32) {
         if (cudaMalloc(&p->ghat32, (size_t)N * comps * sizeof(float)) != cudaSuccess) {

@@ -135,6 +135,9 @@ static int generic_tpt(const FFTDesc &P)
     return (need + 31) / 32 * 32;
 }
 
+int generic_threads(const FFTDesc &P) { return generic_tpt(P); }
+bool factorize_any(int L, FFTDesc &d) { return factorize(L, 0, d); }
+
 static conv_status set_all_attrs(int smem)
 {
     conv_status rc = CONV_OK;

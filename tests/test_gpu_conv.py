@@ -57,7 +57,10 @@ def test_ghat_table_matches_oracle(name, n):
             ref[k2, k1] = O.ghat_radial(kind, math.hypot(k1, k2), plan.b, plan.a, **okw)
     if kind != "helm":
         ref = ref.real
-    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # Helmholtz: outside the quadrature band the closed form divides by s^2 - kappa^2, so entries
+    # a few percent from resonance carry ~|kappa^2/(s^2-kappa^2)| ulps on either side.
+    tol = 1e-12 if kind == "helm" else 1e-13
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
 
 
 def test_helmholtz_ghat_near_resonance():
@@ -191,3 +194,27 @@ def test_full_size_kernel_sweep(prec):
     for i in (0, 9):
         ref = O.conv(u[i], plan.M, g).real
         assert _relerr(ref, out[i].cpu().numpy()) <= TOL[prec]
+
+
+# ------------------------------------------------------------------ Fourier smoothing (Sec. 2.4)
+@pytest.mark.parametrize("shape,geom", [("disk", (0.5, 0.5, 0.3)), ("rect", (0.25, 0.75, 0.25, 0.75)),
+                                        ("rect", (0.3, 0.7, 0.3, 0.7)), ("disk", (0.47, 0.55, 0.21))])
+@pytest.mark.parametrize("n", [32, 128])
+def test_fs_mask_matches_oracle(shape, geom, n):
+    plan = ConvPlan("log", n=n, period=3, precision="fp64", io="r2r", scale=-INV2PI)
+    got = plan.fs_mask(shape, geom, 0.15).cpu().numpy()
+    ref = O.fs_mask(n, 3.0, shape, geom, 0.15)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fourier_smoothed_convolution(prec):
+    """Disk(0.3) indicator times a smooth bump: A_n(u~ chi^n psi) on the GPU equals the oracle's."""
+    n = 256
+    plan = ConvPlan("pow", n=n, period=3, precision=prec, io="r2r", gamma=-1.0)
+    ut = inputs.smooth_extension(n)
+    mask = plan.fs_mask("disk", (0.5, 0.5, 0.3), 0.15)
+    out = plan.apply(torch.tensor(ut, dtype=plan.real_dtype, device="cuda"), mask=mask).cpu().numpy()
+    om = O.fs_mask(n, 3.0, "disk", (0.5, 0.5, 0.3), 0.15)
+    ref = O.conv(ut * om, plan.M, O.ghat_full("pow", plan.M, 3.0, plan.a, gamma=-1.0)).real
+    assert _relerr(ref, out) <= TOL[prec]
