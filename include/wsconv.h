@@ -92,6 +92,24 @@ conv_status conv_workspace_size(conv_plan_t plan, int batch, size_t *bytes);
 conv_status conv_apply(conv_plan_t plan, const void *u, const void *mask, void *out, int batch,
                        void *workspace, void *stream);
 
+/* conv_apply without any allocation (the paper has no counterpart; this is a deployment aid).
+ * For callers that cannot call cudaMalloc when they run the convolution: code under a device
+ * memory budget that forbids new allocations, real-time loops where an allocation may block, or
+ * host frameworks that own all device memory and pass this library only inputs and outputs.
+ * The plan must exist already (conv_plan allocates its tables once); this call uses neither the
+ * plan's workspace nor a caller's, but a fixed 32 MiB device array inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ *   Same arguments and result as conv_apply (workspace and stream aside).
+ *   Returns CONV_EINVAL, with a message giving both sizes, when the plan and batch need more than
+ *   32 MiB of workspace (conv_workspace_size), or when per-pass timing is enabled on the plan.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress); make
+ *   that first call before any stream capture.
+ *   All calls share the one array: calls that overlap on the GPU (other streams, other threads)
+ *   race and corrupt each other's results; serialise them.  Nothing in the array needs to start at
+ *   zero: each call writes every element it later reads. */
+conv_status conv_apply_noalloc(conv_plan_t plan, const void *u, const void *mask, void *out,
+                               int batch, void *stream);
+
 /* Generalised apply used by the Lippmann-Schwinger operator (Sec. 3.3, eq. (descretls)):
  *     out = beta * u + alpha * A_n(u . mask)
  * with complex alpha (alpha_re, alpha_im) and real beta; C2C/R2C plans only when beta != 0 needs a
