@@ -35,13 +35,17 @@ template <typename T> __host__ __device__ inline int padded_len(int L) { return 
 
 #define WSC_MAX_STAGES 24
 
-// Per-length stage table, passed by value as a kernel parameter.
+// Per-length stage table (device memory).  Twiddle table: for each stage s a block of 3 Ns entries,
+// [w^k | w^{2k} | w^{4k}], k < Ns, w = exp(-2 pi i / (Ns R)), so that consecutive threads (consecutive
+// k) read consecutive entries.
 struct FFTDesc {
     int L;
     int nst;
     int R[WSC_MAX_STAGES];
     int Ns[WSC_MAX_STAGES];
-    int tws[WSC_MAX_STAGES];                  // L / (Ns R): twiddle table stride
+    int tws[WSC_MAX_STAGES];                  // L / (Ns R)
+    int toff[WSC_MAX_STAGES];                 // offset of stage s's twiddle block in the table
+    int tw_len;                               // complex entries of the whole table
     unsigned long long mag[WSC_MAX_STAGES];  // ceil(2^40 / Ns): j / Ns == (j * mag) >> 40 for j < 2^24, Ns < 2^16
 };
 
@@ -127,8 +131,8 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x
 }
 
 // ---------------------------------------------------------------- twiddles
-// x[q] *= w^q, w = tw[t1] = exp(-/+ 2 pi i t1 / L), q = 1..R-1.  The powers 1, 2 and 4 are read
-// from the table (t1, 2 t1, 4 t1 < L since t1 < L/R); 3, 5, 6, 7 are products of two of them.
+// x[q] *= w^{qk}, q = 1..R-1, from the stage's block tab = [w^k | w^{2k} | w^{4k}] (k < Ns):
+// powers 1, 2, 4 are read; 3, 5, 6, 7 are products of two of them.
 template <typename T, bool TWS>
 __device__ __forceinline__ typename cvec<T>::t tw_load(const typename cvec<T>::t *__restrict__ tw, int t)
 {
@@ -137,21 +141,22 @@ __device__ __forceinline__ typename cvec<T>::t tw_load(const typename cvec<T>::t
 }
 
 template <typename T, int R, bool INV, bool TWS>
-__device__ __forceinline__ void apply_twiddles(typename cvec<T>::t *x, const typename cvec<T>::t *__restrict__ tw, int t1)
+__device__ __forceinline__ void apply_twiddles(typename cvec<T>::t *x, const typename cvec<T>::t *__restrict__ tab,
+                                               int Ns, int k)
 {
     typedef typename cvec<T>::t V;
-    V w1 = tw_load<T, TWS>(tw, t1);
+    V w1 = tw_load<T, TWS>(tab, k);
     if (INV) w1.y = -w1.y;
     x[1] = cmul(x[1], w1);
     if constexpr (R == 2) return;
-    V w2 = tw_load<T, TWS>(tw, 2 * t1);
+    V w2 = tw_load<T, TWS>(tab, Ns + k);
     if (INV) w2.y = -w2.y;
     x[2] = cmul(x[2], w2);
     if constexpr (R == 3) return;
     V w3 = cmul(w1, w2);
     x[3] = cmul(x[3], w3);
     if constexpr (R == 4) return;
-    V w4 = tw_load<T, TWS>(tw, 4 * t1);
+    V w4 = tw_load<T, TWS>(tab, 2 * Ns + k);
     if (INV) w4.y = -w4.y;
     x[4] = cmul(x[4], w4);
     if constexpr (R == 5) return;
@@ -171,7 +176,7 @@ __device__ __forceinline__ void stockham_stage(typename cvec<T>::t *buf, const F
     typedef typename cvec<T>::t V;
     constexpr int NB = E / R;
     const int nbf = NB * tpt;
-    const int Ns = __ldg(&P->Ns[s]), tws = __ldg(&P->tws[s]);
+    const int Ns = __ldg(&P->Ns[s]), toff = __ldg(&P->toff[s]);
     const unsigned long long mg = __ldg(&P->mag[s]);
     V v[NB][R];
 #pragma unroll
@@ -186,7 +191,7 @@ __device__ __forceinline__ void stockham_stage(typename cvec<T>::t *buf, const F
         const int j = lt + b * tpt;
         const int jq = (int)(((unsigned long long)j * mg) >> 40);
         const int k = j - jq * Ns;
-        if (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw, k * tws);
+        if (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw + toff, Ns, k);
         dftR<R, INV>(v[b]);
         const int base = jq * Ns * R + k;
 #pragma unroll
@@ -208,7 +213,7 @@ __device__ __forceinline__ void stockham_stage_guarded(typename cvec<T>::t *buf,
     typedef typename cvec<T>::t V;
     constexpr int NB = WSC_GMAXE / R;
     const int nbf = __ldg(&P->L) / R;
-    const int Ns = __ldg(&P->Ns[s]), tws = __ldg(&P->tws[s]);
+    const int Ns = __ldg(&P->Ns[s]), toff = __ldg(&P->toff[s]);
     const unsigned long long mg = __ldg(&P->mag[s]);
     V v[NB][R];
 #pragma unroll
@@ -226,7 +231,7 @@ __device__ __forceinline__ void stockham_stage_guarded(typename cvec<T>::t *buf,
         if (j < nbf) {
             const int jq = (int)(((unsigned long long)j * mg) >> 40);
             const int k = j - jq * Ns;
-            if (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw, k * tws);
+            if (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw + toff, Ns, k);
             dftR<R, INV>(v[b]);
             const int base = jq * Ns * R + k;
 #pragma unroll

@@ -94,6 +94,7 @@ __global__ void k_fs_finish(const double2 *__restrict__ chi, T *__restrict__ mas
 
 int generic_threads(const FFTDesc &P);
 bool factorize_any(int L, FFTDesc &d);
+void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im);
 
 }  // namespace wsc
 
@@ -115,15 +116,11 @@ extern "C" conv_status conv_fs_mask(conv_plan_t p, int shape, const double *geom
     WSC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     if (smem > (size_t)smem_optin || tpt > 512)
         return fail(CONV_EUNSUPPORTED, "FP64 transform of length M does not fit one CTA");
-    std::vector<double2> twh(M);
-    const long double PI_L = 3.141592653589793238462643383279502884L;
-    for (int t = 0; t < M; ++t) {
-        long double ang = 2.0L * PI_L * (long double)t / (long double)M;
-        twh[t] = make_double2((double)cosl(ang), (double)-sinl(ang));
-    }
+    std::vector<double> twh;
+    stage_twiddles(d, twh);
     double2 *tw = nullptr, *W = nullptr, *chi = nullptr;
     FFTDesc *dd = nullptr;
-    bool ok = cudaMalloc(&tw, M * sizeof(double2)) == cudaSuccess &&
+    bool ok = cudaMalloc(&tw, twh.size() * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&W, (size_t)M * n * sizeof(double2)) == cudaSuccess &&
               cudaMalloc(&chi, (size_t)n * n * sizeof(double2)) == cudaSuccess &&
               cudaMalloc(&dd, sizeof(FFTDesc)) == cudaSuccess;
@@ -133,7 +130,7 @@ extern "C" conv_status conv_fs_mask(conv_plan_t p, int shape, const double *geom
         rc = fail(CONV_ENOMEM, "FS mask buffers");
     }
     if (rc == CONV_OK) {
-        cudaMemcpyAsync(tw, twh.data(), M * sizeof(double2), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(double), cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(dd, &d, sizeof(FFTDesc), cudaMemcpyHostToDevice, st);
         cudaFuncSetAttribute(k_fs_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_c2c_rows_inv<double, 0, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -147,6 +144,7 @@ extern "C" conv_status conv_fs_mask(conv_plan_t p, int shape, const double *geom
         a.ghat = nullptr;
         a.u = nullptr;
         a.tw = tw;
+        a.tw_len = d.tw_len;
         a.P = dd;
         a.n = n;
         a.h = p->h;

@@ -114,14 +114,36 @@ static bool factorize(int L, int E, FFTDesc &d)
     d.L = L;
     d.nst = (int)R.size();
     long long Ns = 1;
+    int off = 0;
     for (int s = 0; s < d.nst; ++s) {
         d.R[s] = R[s];
         d.Ns[s] = (int)Ns;
         d.tws[s] = (int)(L / (Ns * R[s]));
+        d.toff[s] = off;
+        off += 3 * (int)Ns;
         d.mag[s] = ((1ULL << 40) + (unsigned long long)Ns - 1) / (unsigned long long)Ns;
         Ns *= R[s];
     }
+    d.tw_len = off;
     return true;
+}
+
+// Per-stage twiddle blocks [w^k | w^{2k} | w^{4k}], w = exp(-2 pi i / (Ns R)), in long double.
+void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im)
+{
+    const long double PI_L = 3.141592653589793238462643383279502884L;
+    re_im.assign(2 * (size_t)d.tw_len, 0.0);
+    for (int s = 0; s < d.nst; ++s) {
+        const long long Ns = d.Ns[s], NR = Ns * d.R[s];
+        for (int m = 0; m < 3; ++m)
+            for (long long k = 0; k < Ns; ++k) {
+                const long long e = ((1LL << m) * k) % NR;
+                const long double ang = 2.0L * PI_L * (long double)e / (long double)NR;
+                const size_t i = (size_t)d.toff[s] + (size_t)m * Ns + (size_t)k;
+                re_im[2 * i] = (double)cosl(ang);
+                re_im[2 * i + 1] = (double)-sinl(ang);
+            }
+    }
 }
 
 // Threads per transform for the guarded path: every stage fits GMAXE/R butterflies per thread.
@@ -168,7 +190,6 @@ conv_status select_transform(conv_plan_s *p)
     const int M = p->M;
     const size_t esz = p->prec == CONV_P_FP64 ? 16 : 8;
     const size_t per = (size_t)(p->prec == CONV_P_FP64 ? padded_len<double>(M) : padded_len<float>(M)) * esz;
-    const size_t twb = (size_t)M * esz;
     if (per > (size_t)smem_optin)
         return fail(CONV_EUNSUPPORTED, "transform length M=" + std::to_string(M) +
                                            " exceeds one CTA's shared memory at this precision");
@@ -193,6 +214,7 @@ conv_status select_transform(conv_plan_s *p)
         }
         if (tpt > maxT) continue;
         // twiddles in shared memory when the table and at least one transform buffer fit
+        const size_t twb = (size_t)d.tw_len * esz;
         bool tws = E > 0 && twb + per <= (size_t)smem_optin;
         if (force_t == 0) tws = false;
         const size_t avail = smem_optin - (tws ? twb : 0);

@@ -19,7 +19,8 @@ template <typename T> struct PassArgs {
     void *out;             // passes 1, 2: the workspace; pass 3: the result
     const void *ghat;      // pass 2: moment quadrant [k2][k1] (T or complex V)
     const void *u;         // pass 3: u for the beta term
-    const V *tw;           // twiddles exp(-2 pi i t / M), global
+    const V *tw;           // per-stage twiddle blocks (FFTDesc), global
+    int tw_len;            // entries of the twiddle table
     const FFTDesc *P;
     int n, h, M, tpt;
     int units;             // work items over the whole batch
@@ -37,10 +38,10 @@ __device__ __forceinline__ typename cvec<T>::t *setup_smem(const PassArgs<T> &a,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *base = reinterpret_cast<V *>(smem_raw);
     if (TWS) {
-        for (int t = threadIdx.x; t < a.M; t += blockDim.x) base[t] = __ldg(&a.tw[t]);
+        for (int t = threadIdx.x; t < a.tw_len; t += blockDim.x) base[t] = __ldg(&a.tw[t]);
         __syncthreads();
         twp = base;
-        base += a.M;
+        base += a.tw_len;
     } else {
         twp = a.tw;
     }
@@ -314,6 +315,7 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
     a.ghat = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
     a.u = u;
     a.tw = reinterpret_cast<const V *>(p->tw);
+    a.tw_len = p->fft.tw_len;
     a.P = p->fft_dev;
     a.n = n;
     a.h = h;

@@ -29,34 +29,24 @@ size_t spectrum_elems(const conv_plan_s *p)
     return (size_t)(p->io == CONV_IO_R2R ? p->h : p->M) * p->n;
 }
 
+void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im);
+
+// Per-stage twiddle blocks of the plan's radix sequence, in the plan precision.
 static conv_status upload_twiddles(conv_plan_s *p)
 {
-    const int L = p->M;
-    const long double PI_L = 3.141592653589793238462643383279502884L;
-    if (p->prec == CONV_P_FP64) {
-        std::vector<double> h(2 * (size_t)L);
-        for (int t = 0; t < L; ++t) {
-            long double ang = 2.0L * PI_L * (long double)t / (long double)L;
-            h[2 * t] = (double)cosl(ang);
-            h[2 * t + 1] = (double)-sinl(ang);
-        }
-        if (cudaMalloc(&p->tw, h.size() * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(CONV_ENOMEM, "cudaMalloc of the twiddle table failed");
-        }
-        WSC_CUDA(cudaMemcpy(p->tw, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<double> h;
+    stage_twiddles(p->fft, h);
+    const bool f64 = p->prec == CONV_P_FP64;
+    const size_t bytes = h.size() * (f64 ? sizeof(double) : sizeof(float));
+    if (cudaMalloc(&p->tw, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CONV_ENOMEM, "cudaMalloc of the twiddle table failed");
+    }
+    if (f64) {
+        WSC_CUDA(cudaMemcpy(p->tw, h.data(), bytes, cudaMemcpyHostToDevice));
     } else {
-        std::vector<float> h(2 * (size_t)L);
-        for (int t = 0; t < L; ++t) {
-            long double ang = 2.0L * PI_L * (long double)t / (long double)L;
-            h[2 * t] = (float)cosl(ang);
-            h[2 * t + 1] = (float)-sinl(ang);
-        }
-        if (cudaMalloc(&p->tw, h.size() * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(CONV_ENOMEM, "cudaMalloc of the twiddle table failed");
-        }
-        WSC_CUDA(cudaMemcpy(p->tw, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+        std::vector<float> f(h.begin(), h.end());
+        WSC_CUDA(cudaMemcpy(p->tw, f.data(), bytes, cudaMemcpyHostToDevice));
     }
     return CONV_OK;
 }
