@@ -157,12 +157,40 @@ static int generic_tpt(const FFTDesc &P)
     return (need + 31) / 32 * 32;
 }
 
+// Fused-transform variants: (precision, E, first radix, last radix).
+#define WSC_DISPATCH_FUSED(prec, E, tws, CALL)                                                          \
+    do {                                                                                                \
+        if ((prec) == CONV_P_FP32) {                                                                    \
+            if (tws) { typedef float T_; constexpr int E_ = 24, RF_ = 8, RL_ = 3; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 24, RF_ = 8, RL_ = 3; constexpr bool W_ = false; CALL; }    \
+        } else if ((E) == 12) {                                                                         \
+            if (tws) { typedef double T_; constexpr int E_ = 12, RF_ = 4, RL_ = 3; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 12, RF_ = 4, RL_ = 3; constexpr bool W_ = false; CALL; }    \
+        } else {                                                                                        \
+            if (tws) { typedef double T_; constexpr int E_ = 24, RF_ = 8, RL_ = 3; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 24, RF_ = 8, RL_ = 3; constexpr bool W_ = false; CALL; }    \
+        }                                                                                               \
+    } while (0)
+
+static bool fused_eligible(conv_precision prec, int E, const FFTDesc &d)
+{
+    if (d.nst < 2) return false;
+    const int RF = d.R[0], RL = d.R[d.nst - 1];
+    if (prec == CONV_P_FP32) return E == 24 && RF == 8 && RL == 3;
+    return (E == 12 && RF == 4 && RL == 3) || (E == 24 && RF == 8 && RL == 3);
+}
+
 int generic_threads(const FFTDesc &P) { return generic_tpt(P); }
 bool factorize_any(int L, FFTDesc &d) { return factorize(L, 0, d); }
 
 static conv_status set_all_attrs(int smem)
 {
     conv_status rc = CONV_OK;
+    for (int tws = 0; tws < 2 && rc == CONV_OK; ++tws) {
+        WSC_DISPATCH_FUSED(CONV_P_FP32, 24, tws, rc = (set_attrs_fused<T_, E_, RF_, RL_, W_>(smem)));
+        if (rc == CONV_OK) WSC_DISPATCH_FUSED(CONV_P_FP64, 12, tws, rc = (set_attrs_fused<T_, E_, RF_, RL_, W_>(smem)));
+        if (rc == CONV_OK) WSC_DISPATCH_FUSED(CONV_P_FP64, 24, tws, rc = (set_attrs_fused<T_, E_, RF_, RL_, W_>(smem)));
+    }
     for (int prec = 0; prec < 2 && rc == CONV_OK; ++prec)
         for (int tws = 0; tws < 2 && rc == CONV_OK; ++tws)
             for (int E : {8, 12, 16, 24, 0}) {
@@ -199,6 +227,8 @@ conv_status select_transform(conv_plan_s *p)
     const char *env_e = getenv("WSCONV_ELEMS"), *env_g = getenv("WSCONV_GROUPS"), *env_t = getenv("WSCONV_TWS");
     const int force_e = env_e ? atoi(env_e) : -1, force_g = env_g ? atoi(env_g) : 0;
     const int force_t = env_t ? atoi(env_t) : -1;
+    const char *env_f = getenv("WSCONV_FUSED");
+    const int force_f = env_f ? atoi(env_f) : -1;
     for (int i = 0; i < ncand; ++i) {
         const int E = cand[i];
         if (force_e >= 0 && E != force_e) continue;
@@ -228,8 +258,12 @@ conv_status select_transform(conv_plan_s *p)
         p->rows.tpt = p->cols.tpt = tpt;
         p->rows.groups = p->cols.groups = G;
         p->rows.smem = p->cols.smem = (tws ? twb : 0) + per * G;
+        p->fused = fused_eligible(p->prec, E, d) && force_f != 0;
         int bps = 1;
-        WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, p->rows.smem)));
+        if (p->fused)
+            WSC_DISPATCH_FUSED(p->prec, E, tws, bps = (blocks_per_sm_fused<T_, E_, RF_, RL_, W_>(tpt * G, p->rows.smem)));
+        else
+            WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, p->rows.smem)));
         p->rows.max_ctas = p->cols.max_ctas = bps * sms;
         return CONV_OK;
     }
@@ -241,8 +275,12 @@ conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, voi
                             double alpha_re, double alpha_im, double beta, void *ws, cudaStream_t st)
 {
     conv_status rc = CONV_OK;
-    WSC_DISPATCH(p->prec, p->elems, p->tws,
-                 rc = (run_pipeline<T_, E_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
+    if (p->fused)
+        WSC_DISPATCH_FUSED(p->prec, p->elems, p->tws,
+                           rc = (run_fused<T_, E_, RF_, RL_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
+    else
+        WSC_DISPATCH(p->prec, p->elems, p->tws,
+                     rc = (run_pipeline<T_, E_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
     return rc;
 }
 

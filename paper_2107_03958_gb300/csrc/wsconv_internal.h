@@ -33,6 +33,11 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
                          double are, double aim, double beta, void *ws, cudaStream_t st);
 template <typename T, int E, bool TWS> conv_status set_attrs(int smem);
 template <typename T, int E, bool TWS> int blocks_per_sm(int threads, size_t smem);
+template <typename T, int E, int RF, int RL, bool TWS>
+conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
+                      double aim, double beta, void *ws, cudaStream_t st);
+template <typename T, int E, int RF, int RL, bool TWS> conv_status set_attrs_fused(int smem);
+template <typename T, int E, int RF, int RL, bool TWS> int blocks_per_sm_fused(int threads, size_t smem);
 
 // Launch shape of one pass family (rows or columns).
 struct LaunchShape {
@@ -55,6 +60,7 @@ struct conv_plan_s {
     int device;
     int elems;  // complex elements per thread in the transform kernels
     bool tws;   // twiddle table staged in shared memory
+    bool fused; // passes on the fused transform (global-memory first/last stages)
     wsc::FFTDesc fft;
     wsc::FFTDesc *fft_dev = nullptr;  // device copy read by the pass kernels
     // FP64 moment quadrant [k2][k1], k1, k2 in [0, h): real (h*h doubles) or complex (h*h double2)
