@@ -349,6 +349,66 @@ def profile_case(args):
                       "radices": list(info.radices)[:info.nstages]}))
 
 
+def serving_leg(count, seed=5):
+    """Request mix (Poisson arrivals, mean 200/s): half convolutions, half Lippmann-Schwinger
+    solves; n from {128, 256, 512, 1024, 2048} with weights .3/.3/.2/.15/.05; kernels from the
+    five-kernel sweep; kappa ~ U[5, 60]; FP32 convolutions, mixed-precision LS (FP64 refinement to
+    1e-10).  Submitted by a producer thread at the drawn arrival times; 150 GB budget."""
+    import threading
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import Server
+    reqs = inputs.serving_requests(count, rate=200.0, seed=seed)
+    bufs = []
+    for r in reqs:
+        n = r["n"]
+        if r["kind"] == "ls":
+            m = torch.tensor(inputs.lippmann_contrast(n, "bump"), device="cuda")
+            f = torch.tensor(inputs.plane_wave(n, r["kappa"]), device="cuda")
+            bufs.append((m, f, torch.zeros_like(f)))
+        else:
+            u = torch.tensor(inputs.bump_sums(n, 1, seed=r["seed"])[0], dtype=torch.float32, device="cuda")
+            cplx = r["kernel"] == "helmholtz"
+            out = torch.empty((n, n), dtype=torch.complex64 if cplx else torch.float32, device="cuda")
+            bufs.append((u, out))
+    srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def producer():
+        for i, r in enumerate(reqs):
+            delay = r["t_arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            if r["kind"] == "ls":
+                m, f, x = bufs[i]
+                tickets[i] = srv.submit_ls(m, f, x, r["kappa"], precision="fp32")
+            else:
+                u, out = bufs[i]
+                kw = dict(r["params"])
+                io = "r2c" if r["kernel"] == "helmholtz" else "r2r"
+                tickets[i] = srv.submit_conv(u, out, kernel=r["kernel"], precision="fp32", io=io, **kw)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    res = [srv.wait(t, timeout_s=600) for t in tickets]
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    ok = [r for r in res if r["status"] == "CONV_OK"]
+    lat = sorted(r["latency_s"] for r in ok)
+    lat_ls = sorted(r["latency_s"] for r, q in zip(res, reqs) if q["kind"] == "ls" and r["status"] == "CONV_OK")
+    pct = lambda a, p: 1e3 * a[min(len(a) - 1, max(0, int(math.ceil(p * len(a))) - 1))] if a else None
+    return {"requests": count, "completed_ok": len(ok), "wall_s": wall,
+            "requests_per_s": len(ok) / wall,
+            "ls_solves_per_s": len(lat_ls) / wall, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
+            "ls_p50_ms": pct(lat_ls, 0.5), "ls_p99_ms": pct(lat_ls, 0.99),
+            "ls_max_rel_residual": max((r["rel_residual"] for r, q in zip(res, reqs) if q["kind"] == "ls"), default=None),
+            "batches": stats["batches"], "batched_requests": stats["batched_requests"],
+            "plans_built": stats["plans_built"], "mix": "50% conv / 50% LS, Poisson 200/s"}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -435,6 +495,7 @@ def main():
         extras["fp32_n%d" % n2] = {"value": ws * 5 * args.batch * args.steps / (l2_ms * 1e-3),
                                    "unit": "conv/s", "ms_per_step": l2_ms / args.steps}
         extras["ls"] = ls_leg(512, 40.0, 5, stream)
+        extras["serving"] = serving_leg(80)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "conv/s", "n_gpus": ws, "steps": args.steps,

@@ -199,6 +199,61 @@ conv_status conv_timing_enable(conv_plan_t plan, int enable);
 conv_status conv_timing_read(conv_plan_t plan, double ms_out[3], long long *applies);
 
 /* ------------------------------------------------------------------------------------------
+ * Serving (no counterpart in the paper): a request loop with continuous batching around
+ * conv_apply (Sec. 2.1) and ls_solve (Sec. 3.3).  Requests may be submitted at any time from any
+ * thread.  A dispatcher admits them first-fit against a device-memory budget (plan tables,
+ * workspaces and batching buffers, Krylov bases), keeps plans resident (evicting idle ones
+ * oldest-first when the budget requires), batches waiting convolutions that share a plan into one
+ * launch on that plan's stream, and runs Lippmann-Schwinger solves on worker threads with their
+ * own streams, so the work of different requests overlaps on the GPU.  Every result equals the one
+ * the same request gets alone (same kernels, fixed-order reductions).
+ * The caller owns every request buffer (device memory) until srv_wait returns for that ticket. */
+typedef struct srv_s *srv_t;
+typedef enum { SRV_CONV = 0, SRV_LS = 1 } srv_kind;
+
+typedef struct {
+    int kind;                      /* SRV_CONV or SRV_LS */
+    conv_kernel kernel;            /* SRV_LS: a Helmholtz kernel */
+    int n, period_num, period_den;
+    int precision;                 /* conv: plan precision; LS: CONV_P_FP64, or CONV_P_FP32 = FP32
+                                      matvecs inside FP64 iterative refinement */
+    int io;                        /* conv: conv_io (ignored for LS) */
+    const void *in;                /* conv: u (n x n, plan types); LS: f (complex128 n x n) */
+    const void *mask;              /* conv: optional n x n mask (plan real type) */
+    const double *m;               /* LS: contrast (FP64 n x n) */
+    void *out;                     /* conv: A_n(u . mask); LS: solution (complex128), zero start */
+    double tol;                    /* LS: relative residual target (<= 0: 1e-10) */
+    int restart, max_iters;        /* LS: (<= 0: 50, 2000) */
+} srv_request;
+
+typedef struct {
+    int status;                    /* conv_status of the request */
+    double t_submit, t_start, t_done;  /* seconds, one monotonic host clock */
+    int batched_with;              /* requests in the launch that carried this one */
+    int iters;                     /* LS: matvecs */
+    double rel_residual;           /* LS: final true relative residual */
+} srv_result;
+
+typedef struct {
+    long long submitted, completed, failed, batches, batched_requests, plans_built, plans_evicted;
+    size_t bytes_in_use;
+    int plans_cached;
+} srv_stats;
+
+/* mem_budget_bytes: device bytes the server may hold; max_inflight: admitted requests at once;
+ * conv_batch_max: convolutions per batched launch; ls_workers: concurrent LS solves. */
+conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch_max, int ls_workers,
+                       srv_t *server);
+/* Non-blocking; returns a ticket.  CONV_EINVAL for malformed requests. */
+conv_status srv_submit(srv_t server, const srv_request *request, long long *ticket);
+/* Blocks until the request finished (timeout_s <= 0: no limit); CONV_ETIMEOUT if the limit
+ * passed first.  On CONV_OK the ticket is released and *result filled. */
+conv_status srv_wait(srv_t server, long long ticket, double timeout_s, srv_result *result);
+conv_status srv_get_stats(srv_t server, srv_stats *stats);
+/* Stops admitting, finishes what is on the GPU, frees every cached plan. */
+void srv_destroy(srv_t server);
+
+/* ------------------------------------------------------------------------------------------
  * Roofline denominators measured on the running GPU (no counterpart in the paper):
  *   copy:  bytes read + written per second by a grid-stride float4 copy of `bytes` bytes;
  *   fma:   FP64 and FP32 fused multiply-add throughput (flops/s, an FMA counts 2).

@@ -38,6 +38,28 @@ class LsInfo(ctypes.Structure):
                 ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double)]
 
 
+class SrvRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("kernel", ConvKernel), ("n", ctypes.c_int),
+                ("period_num", ctypes.c_int), ("period_den", ctypes.c_int),
+                ("precision", ctypes.c_int), ("io", ctypes.c_int), ("inp", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("m", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int)]
+
+
+class SrvResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("batched_with", ctypes.c_int), ("iters", ctypes.c_int),
+                ("rel_residual", ctypes.c_double)]
+
+
+class SrvStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("batches", ctypes.c_longlong),
+                ("batched_requests", ctypes.c_longlong), ("plans_built", ctypes.c_longlong),
+                ("plans_evicted", ctypes.c_longlong), ("bytes_in_use", ctypes.c_size_t),
+                ("plans_cached", ctypes.c_int)]
+
+
 # every exported symbol of include/wsconv.h with its prototype
 PROTOTYPES = {
     "conv_plan": (ctypes.c_int, [ctypes.POINTER(ConvKernel), ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -63,6 +85,14 @@ PROTOTYPES = {
     "conv_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "conv_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_longlong)]),
+    "srv_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "srv_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SrvRequest),
+                                  ctypes.POINTER(ctypes.c_longlong)]),
+    "srv_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
+                                ctypes.POINTER(SrvResult)]),
+    "srv_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SrvStats)]),
+    "srv_destroy": (None, [ctypes.c_void_p]),
     "conv_measure_peaks": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]),

@@ -172,6 +172,71 @@ def ls_solve(plan, m, f, x=None, restart=50, max_iters=2000, tol=1e-10, refine=F
     return x, info
 
 
+class Server:
+    """Continuous-batching request loop (C++ runtime in the library; see srv_* in wsconv.h).
+
+    submit_conv / submit_ls return tickets; wait(ticket) returns the result record.  The tensors of
+    a request must stay alive until its wait returns (the server keeps references until then)."""
+
+    def __init__(self, mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4):
+        self._lib = N.load()
+        h = ctypes.c_void_p()
+        N.check(self._lib.srv_create(int(mem_budget_bytes), int(max_inflight), int(conv_batch_max),
+                                     int(ls_workers), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def _submit(self, req, keep):
+        t = ctypes.c_longlong()
+        N.check(self._lib.srv_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_conv(self, u, out, kernel="log", period=3, precision="fp32", io="r2r", mask=None,
+                    gamma=0.0, kappa=0.0, scale=1.0):
+        frac = Fraction(period).limit_denominator(64)
+        r = N.SrvRequest(0, N.ConvKernel(FAMILY[kernel], float(gamma), float(kappa), float(scale)),
+                         int(u.shape[-1]), frac.numerator, frac.denominator, PRECISION[precision],
+                         IO[io], u.data_ptr(), mask.data_ptr() if mask is not None else None, None,
+                         out.data_ptr(), 0.0, 0, 0)
+        return self._submit(r, (u, out, mask))
+
+    def submit_ls(self, m, f, x, kappa, period=3, precision="fp64", tol=1e-10, restart=50,
+                  max_iters=2000):
+        frac = Fraction(period).limit_denominator(64)
+        r = N.SrvRequest(1, N.ConvKernel(2, 0.0, float(kappa), 1.0), int(f.shape[-1]),
+                         frac.numerator, frac.denominator, PRECISION[precision], IO["c2c"],
+                         f.data_ptr(), None, m.data_ptr(), x.data_ptr(), float(tol), int(restart),
+                         int(max_iters))
+        return self._submit(r, (m, f, x))
+
+    def wait(self, ticket, timeout_s=0.0):
+        res = N.SrvResult()
+        N.check(self._lib.srv_wait(self._h, int(ticket), float(timeout_s), ctypes.byref(res)))
+        self._keep.pop(ticket, None)
+        return {"status": N.STATUS.get(res.status, res.status), "t_submit": res.t_submit,
+                "t_start": res.t_start, "t_done": res.t_done, "batched_with": res.batched_with,
+                "iters": res.iters, "rel_residual": res.rel_residual,
+                "latency_s": res.t_done - res.t_submit}
+
+    def stats(self):
+        st = N.SrvStats()
+        N.check(self._lib.srv_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in N.SrvStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.srv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def measure_peaks(nbytes=1 << 30):
     """Measured HBM copy GB/s and FP64/FP32 FMA TFLOP/s on the current GPU."""
     lib = N.load()

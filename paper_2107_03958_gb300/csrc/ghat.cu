@@ -164,8 +164,9 @@ conv_status build_ghat(conv_plan_s *p)
 {
     double gx[GL_NODES], gw[GL_NODES];
     gauss_legendre(GL_NODES, gx, gw);
-    WSC_CUDA(cudaMemcpyToSymbol(c_glx, gx, sizeof(gx)));
-    WSC_CUDA(cudaMemcpyToSymbol(c_glw, gw, sizeof(gw)));
+    cudaStream_t st = p->setup_stream;
+    WSC_CUDA(cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, st));
+    WSC_CUDA(cudaMemcpyToSymbolAsync(c_glw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, st));
     const long long N = (long long)p->h * p->h;
     const int comps = p->complex_ghat ? 2 : 1;
     p->ghat_bytes = (size_t)N * comps * sizeof(double);
@@ -199,13 +200,13 @@ conv_status build_ghat(conv_plan_s *p)
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the Helmholtz quadrature table failed");
         }
-        WSC_CUDA(cudaMemcpy(htab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+        WSC_CUDA(cudaMemcpyAsync(htab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
-    k_ghat<<<blocks, 256>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, p->h,
+    k_ghat<<<blocks, 256, 0, st>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, p->h,
                             p->ghat64, hka, htab, hnodes);
     if (htab) {
-        cudaError_t e = cudaDeviceSynchronize();
+        cudaError_t e = cudaStreamSynchronize(st);
         cudaFree(htab);
         if (e != cudaSuccess) return cuda_fail(e, "moment table kernel");
     }
@@ -215,10 +216,10 @@ conv_status build_ghat(conv_plan_s *p)
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the FP32 moment table failed");
         }
-        k_to_f32<<<blocks, 256>>>(p->ghat64, reinterpret_cast<float *>(p->ghat32), N * comps);
+        k_to_f32<<<blocks, 256, 0, st>>>(p->ghat64, reinterpret_cast<float *>(p->ghat32), N * comps);
         WSC_CUDA(cudaGetLastError());
     }
-    WSC_CUDA(cudaDeviceSynchronize());
+    WSC_CUDA(cudaStreamSynchronize(st));
     return CONV_OK;
 }
 

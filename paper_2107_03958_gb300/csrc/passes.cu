@@ -265,6 +265,19 @@ conv_status select_transform(conv_plan_s *p)
         else
             WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, p->rows.smem)));
         p->rows.max_ctas = p->cols.max_ctas = bps * sms;
+        // fused pass 3 reads twiddles from global memory: its own shape, without the table
+        p->inv = p->rows;
+        if (p->fused && tws) {
+            int Gi = std::max(1, maxT / tpt);
+            Gi = std::min<int>(Gi, (int)(smem_optin / per));
+            Gi = std::min(Gi, 8);
+            if (force_g > 0 && force_g <= Gi) Gi = force_g;
+            p->inv.groups = Gi;
+            p->inv.smem = per * Gi;
+            int bi = 1;
+            WSC_DISPATCH_FUSED(p->prec, E, false, bi = (blocks_per_sm_fused<T_, E_, RF_, RL_, W_>(tpt * Gi, p->inv.smem)));
+            p->inv.max_ctas = bi * sms;
+        }
         return CONV_OK;
     }
     return fail(CONV_EUNSUPPORTED, "M = " + std::to_string(M) +

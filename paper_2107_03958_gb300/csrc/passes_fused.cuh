@@ -263,7 +263,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
     a.batch = batch;
     a.alpha = cmk<V>((T)(are * sc), (T)(aim * sc));
     a.beta = (T)beta;
-    const LaunchShape &R = p->rows, &C = p->cols;
+    const LaunchShape &R = p->rows, &C = p->cols, &I = p->inv;
     auto grid = [&](const LaunchShape &S, int units) {
         long long need = (units + S.groups - 1) / S.groups;
         return (unsigned)std::min<long long>(need, (long long)S.max_ctas);
@@ -282,10 +282,10 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.units = batch * h;
         kf_r2r_cols<T, E, RF, RL, TWS><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[2], st);
-        a.tpt = R.tpt;
+        a.tpt = I.tpt;
         a.out = out;
         a.units = batch * ((n + 1) / 2);
-        kf_r2r_rows_inv<T, E, RF, RL, TWS><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+        kf_r2r_rows_inv<T, E, RF, RL, false><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
     } else {
         const bool in_real = p->io == CONV_IO_R2C;
         a.tpt = R.tpt;
@@ -305,13 +305,13 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         else
             kf_c2c_cols<T, E, RF, RL, TWS, false><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[2], st);
-        a.tpt = R.tpt;
+        a.tpt = I.tpt;
         a.out = out;
         a.units = batch * n;
         if (in_real)
-            kf_c2c_rows_inv<T, E, RF, RL, TWS, true><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+            kf_c2c_rows_inv<T, E, RF, RL, false, true><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
         else
-            kf_c2c_rows_inv<T, E, RF, RL, TWS, false><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+            kf_c2c_rows_inv<T, E, RF, RL, false, false><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
     }
     if (ev) cudaEventRecord(ev[3], st);
     WSC_CUDA(cudaGetLastError());

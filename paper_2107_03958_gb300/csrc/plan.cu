@@ -43,10 +43,12 @@ static conv_status upload_twiddles(conv_plan_s *p)
         return fail(CONV_ENOMEM, "cudaMalloc of the twiddle table failed");
     }
     if (f64) {
-        WSC_CUDA(cudaMemcpy(p->tw, h.data(), bytes, cudaMemcpyHostToDevice));
+        WSC_CUDA(cudaMemcpyAsync(p->tw, h.data(), bytes, cudaMemcpyHostToDevice, p->setup_stream));
+        WSC_CUDA(cudaStreamSynchronize(p->setup_stream));
     } else {
         std::vector<float> f(h.begin(), h.end());
-        WSC_CUDA(cudaMemcpy(p->tw, f.data(), bytes, cudaMemcpyHostToDevice));
+        WSC_CUDA(cudaMemcpyAsync(p->tw, f.data(), bytes, cudaMemcpyHostToDevice, p->setup_stream));
+        WSC_CUDA(cudaStreamSynchronize(p->setup_stream));
     }
     return CONV_OK;
 }
@@ -85,6 +87,7 @@ void conv_destroy(conv_plan_t p)
     if (p->ghat32) cudaFree(p->ghat32);
     if (p->tw) cudaFree(p->tw);
     if (p->fft_dev) cudaFree(p->fft_dev);
+    if (p->setup_stream) cudaStreamDestroy(p->setup_stream);
     if (p->ws) cudaFree(p->ws);
     if (p->fp64_twin) conv_destroy(p->fp64_twin);
     for (auto &v : {&p->tev_used, &p->tev_free})
@@ -157,12 +160,20 @@ conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den,
         delete p;
         return fail(CONV_EUNSUPPORTED, "transform length M = n b must be at least 4");
     }
+    // plan-time device work runs on a private non-blocking stream, so building a plan never waits
+    // for (or stalls) work other threads have in flight on the device
+    if (cudaStreamCreateWithFlags(&p->setup_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(CONV_ECUDA, "stream creation failed");
+    }
     conv_status rc = select_transform(p);
     if (rc == CONV_OK) {
         if (cudaMalloc(&p->fft_dev, sizeof(FFTDesc)) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(CONV_ENOMEM, "cudaMalloc of the stage table failed");
-        } else if (cudaMemcpy(p->fft_dev, &p->fft, sizeof(FFTDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+        } else if (cudaMemcpyAsync(p->fft_dev, &p->fft, sizeof(FFTDesc), cudaMemcpyHostToDevice, p->setup_stream) !=
+                   cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "stage table upload");
         }
     }
@@ -174,6 +185,10 @@ conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den,
             cudaGetLastError();
             rc = fail(CONV_ENOMEM, "cudaMalloc of the workspace failed");
         }
+    }
+    if (rc == CONV_OK) {
+        cudaError_t e = cudaStreamSynchronize(p->setup_stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "plan setup");
     }
     if (rc != CONV_OK) {
         conv_destroy(p);

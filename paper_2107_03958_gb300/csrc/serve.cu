@@ -1,0 +1,483 @@
+// serve.cu -- continuous-batching request loop over conv_apply and ls_solve (no counterpart in the
+// paper; this is the serving layer around the Sec. 2.1 convolution and the Sec. 3.3 solver).
+//
+// Requests arrive at any time (srv_submit).  A dispatcher thread admits them first-fit against a
+// device-memory budget (plan tables, workspaces, Krylov bases), keeps plans resident in a cache, and
+//   - convolution requests with the same plan key that are waiting together are gathered into one
+//     batched launch (their inputs copied into the plan's staging buffer, results scattered back),
+//     on that plan's own stream, so different plans' batches overlap on the GPU;
+//   - Lippmann-Schwinger requests run on worker threads, each solve on its own stream, overlapping
+//     with everything else.
+// A completion thread polls the batches' events; srv_wait blocks on a request's completion.
+// Results do not depend on what else is in flight: each density of a batch is transformed by the
+// same kernels with the same arithmetic as alone, and GMRES uses fixed-order reductions.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "wsconv_internal.h"
+
+namespace wsc {
+
+static double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct PlanKey {
+    int family;
+    double gamma, kappa, scale;
+    int n, pnum, pden, prec, io;
+    bool operator<(const PlanKey &o) const
+    {
+        return std::tie(family, gamma, kappa, scale, n, pnum, pden, prec, io) <
+               std::tie(o.family, o.gamma, o.kappa, o.scale, o.n, o.pnum, o.pden, o.prec, o.io);
+    }
+};
+
+struct CachedPlan {
+    conv_plan_t plan = nullptr;
+    cudaStream_t stream = nullptr;
+    void *stage_in = nullptr, *stage_out = nullptr;  // batching staging buffers (conv plans)
+    size_t bytes = 0;
+    int users = 0;       // admitted requests currently holding the plan
+    double last_use = 0;
+    std::mutex run_mu;   // LS plans: one solve at a time per plan (shared workspace)
+};
+
+struct Req {
+    long long ticket;
+    srv_request r;
+    srv_result res;
+    size_t need = 0;     // bytes reserved while admitted (beyond the plan)
+    bool done = false;
+    std::shared_ptr<CachedPlan> cp;
+};
+
+struct Batch {
+    std::vector<std::shared_ptr<Req>> reqs;
+    std::shared_ptr<CachedPlan> cp;
+    cudaEvent_t ev = nullptr;
+};
+
+}  // namespace wsc
+
+struct srv_s {
+    size_t budget = 0, in_use = 0;
+    int max_inflight = 64, batch_max = 16, ls_workers = 4;
+    std::mutex mu;
+    std::condition_variable cv_dispatch, cv_done, cv_ls;
+    std::deque<std::shared_ptr<wsc::Req>> pending;
+    std::map<long long, std::shared_ptr<wsc::Req>> all;
+    std::map<wsc::PlanKey, std::shared_ptr<wsc::CachedPlan>> plans;
+    std::deque<wsc::Batch> inflight;
+    std::deque<std::shared_ptr<wsc::Req>> ls_queue;
+    int inflight_reqs = 0;
+    long long next_ticket = 1;
+    bool stop = false;
+    int device = 0;
+    std::thread dispatcher, completer;
+    std::vector<std::thread> workers;
+    srv_stats stats{};
+};
+
+namespace wsc {
+
+static size_t elem_bytes_of(int prec) { return prec == CONV_P_FP64 ? 8 : 4; }
+
+static PlanKey key_of(const srv_request &r)
+{
+    PlanKey k;
+    k.family = r.kernel.family;
+    k.gamma = r.kernel.gamma;
+    k.kappa = r.kernel.kappa;
+    k.scale = r.kernel.scale;
+    k.n = r.n;
+    k.pnum = r.period_num;
+    k.pden = r.period_den;
+    k.prec = r.kind == SRV_LS ? r.precision : r.precision;
+    k.io = r.kind == SRV_LS ? CONV_IO_C2C + 100 : r.io;  // LS plans are cached apart from conv plans
+    return k;
+}
+
+// Device bytes of a plan (moment table, twiddles, workspace) plus, for conv plans, the staging
+// buffers of one batch; estimated from the sizes before the plan exists.
+static size_t plan_bytes_estimate(const srv_request &r, int batch_max)
+{
+    const long long n = r.n, M = n * r.period_num / r.period_den, h = M / 2 + 1;
+    const size_t cz = 2 * elem_bytes_of(r.precision);
+    const bool c2c = r.kind == SRV_LS || r.io != CONV_IO_R2R;
+    size_t ghat = (size_t)h * h * 8 * (r.kernel.family == CONV_K_HELMHOLTZ ? 2 : 1);
+    if (r.precision == CONV_P_FP32) ghat += ghat / 2;
+    const int B = r.kind == SRV_LS ? 1 : batch_max;
+    size_t ws = (size_t)(c2c ? M : h) * n * cz * B;
+    size_t stage = 0;
+    if (r.kind == SRV_CONV) {
+        const size_t in_b = (size_t)n * n * (r.io == CONV_IO_C2C ? cz : cz / 2);
+        const size_t out_b = (size_t)n * n * (r.io == CONV_IO_R2R ? cz / 2 : cz);
+        stage = (in_b + out_b) * batch_max;
+    }
+    size_t twin = 0;
+    if (r.kind == SRV_LS && r.precision == CONV_P_FP32) twin = (size_t)h * h * 16 + (size_t)M * n * 16;
+    return ghat + ws + stage + twin + (size_t)M * cz * 4;
+}
+
+// Per-request bytes beyond the plan: the LS solver's Krylov basis and vectors.
+static size_t request_bytes(const srv_request &r)
+{
+    if (r.kind != SRV_LS) return 0;
+    const size_t N = (size_t)r.n * r.n;
+    const int restart = r.restart > 0 ? r.restart : 50;
+    return N * 16 * (restart + 5) + N * 8 * 4;
+}
+
+static void finish(srv_t s, const std::shared_ptr<Req> &q, int status, double t_done)
+{
+    q->res.status = status;
+    q->res.t_done = t_done;
+    q->done = true;
+    s->in_use -= q->need;
+    if (q->cp) {
+        q->cp->users--;
+        q->cp->last_use = t_done;
+    }
+    s->inflight_reqs--;
+    s->stats.completed++;
+    if (status != CONV_OK) s->stats.failed++;
+}
+
+// Evict idle cached plans (oldest first) until `need` more bytes fit.  Caller holds s->mu.
+static bool make_room(srv_t s, size_t need)
+{
+    while (s->in_use + need > s->budget) {
+        auto victim = s->plans.end();
+        for (auto it = s->plans.begin(); it != s->plans.end(); ++it)
+            if (it->second->users == 0 && (victim == s->plans.end() || it->second->last_use < victim->second->last_use))
+                victim = it;
+        if (victim == s->plans.end()) return false;
+        auto cp = victim->second;
+        s->plans.erase(victim);
+        s->in_use -= cp->bytes;
+        cudaStreamSynchronize(cp->stream);
+        conv_destroy(cp->plan);
+        cudaStreamDestroy(cp->stream);
+        cudaFree(cp->stage_in);
+        cudaFree(cp->stage_out);
+        s->stats.plans_evicted++;
+    }
+    return true;
+}
+
+static std::shared_ptr<CachedPlan> get_plan(srv_t s, const srv_request &r, int &status)
+{
+    PlanKey k = key_of(r);
+    auto it = s->plans.find(k);
+    if (it != s->plans.end()) return it->second;
+    auto cp = std::make_shared<CachedPlan>();
+    const conv_io io = r.kind == SRV_LS ? CONV_IO_C2C : (conv_io)r.io;
+    status = conv_plan(&r.kernel, r.period_num, r.period_den, r.n, 0.0, (conv_precision)r.precision, io,
+                       r.kind == SRV_LS ? 1 : s->batch_max, &cp->plan);
+    if (status != CONV_OK) return nullptr;
+    cudaStreamCreateWithFlags(&cp->stream, cudaStreamNonBlocking);
+    conv_plan_info inf;
+    conv_get_info(cp->plan, &inf);
+    cp->bytes = inf.ghat_bytes + inf.workspace_bytes + (inf.precision == CONV_P_FP32 ? inf.ghat_bytes / 2 : 0);
+    if (r.kind == SRV_CONV) {
+        const size_t cz = 2 * elem_bytes_of(r.precision);
+        const size_t in_b = (size_t)r.n * r.n * (io == CONV_IO_C2C ? cz : cz / 2);
+        const size_t out_b = (size_t)r.n * r.n * (io == CONV_IO_R2R ? cz / 2 : cz);
+        if (cudaMalloc(&cp->stage_in, in_b * s->batch_max) != cudaSuccess ||
+            cudaMalloc(&cp->stage_out, out_b * s->batch_max) != cudaSuccess) {
+            cudaGetLastError();
+            conv_destroy(cp->plan);
+            status = fail(CONV_ENOMEM, "serving staging buffers");
+            return nullptr;
+        }
+        cp->bytes += (in_b + out_b) * s->batch_max;
+    }
+    s->in_use += cp->bytes;
+    s->plans[k] = cp;
+    s->stats.plans_built++;
+    return cp;
+}
+
+static size_t in_bytes(const srv_request &r)
+{
+    const size_t e = elem_bytes_of(r.precision);
+    return (size_t)r.n * r.n * (r.io == CONV_IO_C2C ? 2 * e : e);
+}
+static size_t out_bytes(const srv_request &r)
+{
+    const size_t e = elem_bytes_of(r.precision);
+    return (size_t)r.n * r.n * (r.io == CONV_IO_R2R ? e : 2 * e);
+}
+
+// Launch one batch of same-plan convolution requests on the plan's stream.  Caller holds s->mu.
+static void launch_batch(srv_t s, Batch &bt)
+{
+    auto &cp = bt.cp;
+    const srv_request &r0 = bt.reqs[0]->r;
+    const double t0 = now_s();
+    const int B = (int)bt.reqs.size();
+    conv_status st;
+    if (B == 1) {
+        st = conv_apply(cp->plan, r0.in, r0.mask, r0.out, 1, nullptr, cp->stream);
+    } else {
+        const size_t ib = in_bytes(r0), ob = out_bytes(r0);
+        for (int i = 0; i < B; ++i)
+            cudaMemcpyAsync((char *)cp->stage_in + i * ib, bt.reqs[i]->r.in, ib, cudaMemcpyDeviceToDevice, cp->stream);
+        st = conv_apply(cp->plan, cp->stage_in, r0.mask, cp->stage_out, B, nullptr, cp->stream);
+        for (int i = 0; i < B; ++i)
+            cudaMemcpyAsync(bt.reqs[i]->r.out, (char *)cp->stage_out + i * ob, ob, cudaMemcpyDeviceToDevice, cp->stream);
+    }
+    cudaEventCreateWithFlags(&bt.ev, cudaEventDisableTiming);
+    cudaEventRecord(bt.ev, cp->stream);
+    for (auto &q : bt.reqs) {
+        q->res.t_start = t0;
+        q->res.batched_with = B;
+        q->res.status = st;
+    }
+    s->stats.batches++;
+    s->stats.batched_requests += B;
+}
+
+static void dispatcher_loop(srv_t s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        // admission: first fit in arrival order
+        std::vector<std::shared_ptr<Req>> admitted;
+        for (auto it = s->pending.begin(); it != s->pending.end();) {
+            auto q = *it;
+            if (s->inflight_reqs >= s->max_inflight) break;
+            PlanKey k = key_of(q->r);
+            const bool have = s->plans.count(k) != 0;
+            const size_t need = request_bytes(q->r) + (have ? 0 : plan_bytes_estimate(q->r, s->batch_max));
+            if (need > s->budget) {  // can never fit
+                it = s->pending.erase(it);
+                s->inflight_reqs++;
+                q->need = 0;
+                finish(s, q, fail(CONV_ENOMEM, "request exceeds the serving memory budget"), now_s());
+                s->cv_done.notify_all();
+                continue;
+            }
+            if (s->in_use + need > s->budget && !make_room(s, need)) {
+                ++it;
+                continue;
+            }
+            int status = CONV_OK;
+            auto cp = get_plan(s, q->r, status);
+            it = s->pending.erase(it);
+            s->inflight_reqs++;
+            if (!cp) {
+                q->need = 0;
+                finish(s, q, status, now_s());
+                s->cv_done.notify_all();
+                continue;
+            }
+            q->cp = cp;
+            cp->users++;
+            q->need = request_bytes(q->r);
+            s->in_use += q->need;
+            admitted.push_back(q);
+        }
+        // group admitted convolutions by plan; hand LS solves to the workers
+        std::map<CachedPlan *, Batch> groups;
+        for (auto &q : admitted) {
+            if (q->r.kind == SRV_LS) {
+                s->ls_queue.push_back(q);
+                s->cv_ls.notify_one();
+                continue;
+            }
+            Batch &bt = groups[q->cp.get()];
+            bt.cp = q->cp;
+            // masks are per batch: start a new batch when the mask differs or the batch is full
+            if (!bt.reqs.empty() && (bt.reqs[0]->r.mask != q->r.mask || (int)bt.reqs.size() >= s->batch_max)) {
+                launch_batch(s, bt);
+                s->inflight.push_back(bt);
+                bt = Batch();
+                bt.cp = q->cp;
+            }
+            bt.reqs.push_back(q);
+        }
+        for (auto &g : groups)
+            if (!g.second.reqs.empty()) {
+                launch_batch(s, g.second);
+                s->inflight.push_back(g.second);
+            }
+        s->cv_dispatch.wait_for(lk, std::chrono::microseconds(200));
+    }
+}
+
+static void completer_loop(srv_t s)
+{
+    cudaSetDevice(s->device);
+    while (true) {
+        std::vector<Batch> done;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->stop && s->inflight.empty()) break;
+            for (auto it = s->inflight.begin(); it != s->inflight.end();) {
+                if (cudaEventQuery(it->ev) == cudaSuccess) {
+                    done.push_back(*it);
+                    it = s->inflight.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            const double t = now_s();
+            for (auto &bt : done) {
+                cudaEventDestroy(bt.ev);
+                for (auto &q : bt.reqs) finish(s, q, q->res.status, t);
+            }
+            if (!done.empty()) {
+                s->cv_done.notify_all();
+                s->cv_dispatch.notify_one();
+            }
+        }
+        if (done.empty()) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+static void ls_worker(srv_t s)
+{
+    cudaSetDevice(s->device);
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    while (true) {
+        std::shared_ptr<Req> q;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_ls.wait(lk, [&] { return s->stop || !s->ls_queue.empty(); });
+            if (s->ls_queue.empty()) break;
+            q = s->ls_queue.front();
+            s->ls_queue.pop_front();
+        }
+        ls_opts o = {q->r.restart > 0 ? q->r.restart : 50, q->r.max_iters > 0 ? q->r.max_iters : 2000,
+                     q->r.tol > 0 ? q->r.tol : 1e-10, q->r.precision == CONV_P_FP32 ? 1 : 0, 1e-5, 1};
+        ls_info info{};
+        conv_status rc;
+        {
+            std::lock_guard<std::mutex> plk(q->cp->run_mu);
+            q->res.t_start = now_s();
+            rc = ls_solve(q->cp->plan, q->r.m, q->r.in, q->r.out, &o, &info, st);
+        }
+        std::lock_guard<std::mutex> lk(s->mu);
+        q->res.iters = info.iters;
+        q->res.rel_residual = info.rel_residual;
+        q->res.batched_with = 1;
+        finish(s, q, rc, now_s());
+        s->cv_done.notify_all();
+        s->cv_dispatch.notify_one();
+    }
+    cudaStreamDestroy(st);
+}
+
+}  // namespace wsc
+
+using namespace wsc;
+
+extern "C" {
+
+conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch_max, int ls_workers, srv_t *out)
+{
+    if (!out || mem_budget_bytes == 0 || max_inflight < 1 || conv_batch_max < 1 || ls_workers < 1)
+        return fail(CONV_EINVAL, "bad serving parameters");
+    srv_s *s = new srv_s();
+    s->budget = mem_budget_bytes;
+    s->max_inflight = max_inflight;
+    s->batch_max = conv_batch_max;
+    s->ls_workers = ls_workers;
+    cudaGetDevice(&s->device);
+    s->dispatcher = std::thread(dispatcher_loop, s);
+    s->completer = std::thread(completer_loop, s);
+    for (int i = 0; i < ls_workers; ++i) s->workers.emplace_back(ls_worker, s);
+    *out = s;
+    return CONV_OK;
+}
+
+conv_status srv_submit(srv_t s, const srv_request *r, long long *ticket)
+{
+    if (!s || !r || !ticket) return fail(CONV_EINVAL, "bad argument");
+    if (r->kind != SRV_CONV && r->kind != SRV_LS) return fail(CONV_EINVAL, "unknown request kind");
+    if (!r->in || !r->out || (r->kind == SRV_LS && !r->m)) return fail(CONV_EINVAL, "missing request buffers");
+    if (r->kind == SRV_LS && r->kernel.family != CONV_K_HELMHOLTZ)
+        return fail(CONV_EINVAL, "Lippmann-Schwinger requests need the Helmholtz kernel");
+    auto q = std::make_shared<Req>();
+    q->r = *r;
+    std::memset(&q->res, 0, sizeof(q->res));
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return fail(CONV_EINVAL, "server is shutting down");
+        q->ticket = s->next_ticket++;
+        q->res.t_submit = now_s();
+        s->pending.push_back(q);
+        s->all[q->ticket] = q;
+        s->stats.submitted++;
+        *ticket = q->ticket;
+    }
+    s->cv_dispatch.notify_one();
+    return CONV_OK;
+}
+
+conv_status srv_wait(srv_t s, long long ticket, double timeout_s, srv_result *res)
+{
+    if (!s) return fail(CONV_EINVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return fail(CONV_EINVAL, "unknown ticket");
+    auto q = it->second;
+    auto pred = [&] { return q->done; };
+    if (timeout_s > 0) {
+        if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+            return fail(CONV_ETIMEOUT, "request not finished within the timeout");
+    } else {
+        s->cv_done.wait(lk, pred);
+    }
+    if (res) *res = q->res;
+    s->all.erase(ticket);
+    return CONV_OK;
+}
+
+conv_status srv_get_stats(srv_t s, srv_stats *out)
+{
+    if (!s || !out) return fail(CONV_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    out->bytes_in_use = s->in_use;
+    out->plans_cached = (int)s->plans.size();
+    return CONV_OK;
+}
+
+void srv_destroy(srv_t s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_dispatch.notify_all();
+    s->cv_ls.notify_all();
+    s->dispatcher.join();
+    for (auto &w : s->workers) w.join();
+    s->completer.join();
+    for (auto &kv : s->plans) {
+        cudaStreamSynchronize(kv.second->stream);
+        conv_destroy(kv.second->plan);
+        cudaStreamDestroy(kv.second->stream);
+        cudaFree(kv.second->stage_in);
+        cudaFree(kv.second->stage_out);
+    }
+    delete s;
+}
+
+}  // extern "C"

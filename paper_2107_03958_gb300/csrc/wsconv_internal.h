@@ -58,6 +58,7 @@ struct conv_plan_s {
     int batch_max;
     bool complex_ghat;
     int device;
+    cudaStream_t setup_stream = nullptr;  // private stream for plan-time device work
     int elems;  // complex elements per thread in the transform kernels
     bool tws;   // twiddle table staged in shared memory
     bool fused; // passes on the fused transform (global-memory first/last stages)
@@ -72,7 +73,7 @@ struct conv_plan_s {
     void *tw = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
-    wsc::LaunchShape rows, cols;
+    wsc::LaunchShape rows, cols, inv;  // inv: fused pass 3 (twiddles always from global memory)
     // FP64 companion plan used as the outer operator of mixed-precision refinement (owned)
     conv_plan_s *fp64_twin = nullptr;
     // per-pass timing instrumentation

