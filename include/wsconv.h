@@ -79,7 +79,23 @@ conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den,
                       double trunc_a, conv_precision precision, conv_io io, int batch_max,
                       conv_plan_t *plan);
 
-/* Bytes of workspace conv_apply needs for `batch` densities (the n x (M/2+1) or n x M spectra). */
+/* Plan flags for conv_plan_ex. */
+enum {
+    /* Compact embedding: the passes run on the 2n-periodic lattice instead of the period-b one.
+     * A_n u is the quadrature of eq. (quad), (A_n u)_i = sum_j w(i - j) u_j, whose weights
+     * w(d) (eq. (quad_wts), |d1|, |d2| <= n - 1) are built once from the moments ghat (period b,
+     * Sec. 2.2) by an FP64 M x M inverse DFT; placed on the period-2n lattice they make A_n u a
+     * cyclic convolution of length L = 2n, so the passes transform 2n points per line with the
+     * L x L DFT of w as multiplier.  Same A_n u up to rounding, fewer points (2n vs n b per line). */
+    CONV_PLAN_COMPACT = 1
+};
+
+conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_den, int n,
+                         double trunc_a, conv_precision precision, conv_io io, int batch_max,
+                         int flags, conv_plan_t *plan);
+
+/* Bytes of workspace conv_apply needs for `batch` densities (the n x (L/2+1) or n x L spectra,
+ * L the transform length). */
 conv_status conv_workspace_size(conv_plan_t plan, int batch, size_t *bytes);
 
 /* out = A_n(u . mask) for `batch` densities (Sec. 2.1, eq. (An)).
@@ -126,6 +142,8 @@ typedef struct {
     int radices[16];
     size_t ghat_bytes, workspace_bytes;
     int threads_rows, groups_rows, threads_cols, groups_cols;
+    int transform_len;   /* points per line in the passes: M = n b, or 2n when compact */
+    int compact;         /* CONV_PLAN_COMPACT was set */
 } conv_plan_info;
 
 conv_status conv_get_info(conv_plan_t plan, conv_plan_info *info);

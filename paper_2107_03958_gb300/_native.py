@@ -24,7 +24,8 @@ class ConvPlanInfo(ctypes.Structure):
                 ("radices", ctypes.c_int * 16), ("ghat_bytes", ctypes.c_size_t),
                 ("workspace_bytes", ctypes.c_size_t), ("threads_rows", ctypes.c_int),
                 ("groups_rows", ctypes.c_int), ("threads_cols", ctypes.c_int),
-                ("groups_cols", ctypes.c_int)]
+                ("groups_cols", ctypes.c_int), ("transform_len", ctypes.c_int),
+                ("compact", ctypes.c_int)]
 
 
 class LsOpts(ctypes.Structure):
@@ -65,6 +66,9 @@ PROTOTYPES = {
     "conv_plan": (ctypes.c_int, [ctypes.POINTER(ConvKernel), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "conv_plan_ex": (ctypes.c_int, [ctypes.POINTER(ConvKernel), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "conv_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "conv_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),

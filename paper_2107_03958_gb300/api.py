@@ -31,7 +31,7 @@ class ConvPlan:
     """A plan for A_n on an n x n grid with period b (Sec. 2.1, eq. (An))."""
 
     def __init__(self, kernel="log", n=64, period=3, trunc_a=0.0, precision="fp64", io="r2r",
-                 batch_max=1, gamma=0.0, kappa=0.0, scale=1.0, device=None):
+                 batch_max=1, gamma=0.0, kappa=0.0, scale=1.0, device=None, compact=False):
         self._lib = N.load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -41,12 +41,13 @@ class ConvPlan:
         self.period = (frac.numerator, frac.denominator)
         k = N.ConvKernel(FAMILY[kernel], float(gamma), float(kappa), float(scale))
         h = ctypes.c_void_p()
-        N.check(self._lib.conv_plan(ctypes.byref(k), frac.numerator, frac.denominator, int(n),
-                                    float(trunc_a), PRECISION[precision], IO[io], int(batch_max),
-                                    ctypes.byref(h)))
+        N.check(self._lib.conv_plan_ex(ctypes.byref(k), frac.numerator, frac.denominator, int(n),
+                                       float(trunc_a), PRECISION[precision], IO[io], int(batch_max),
+                                       1 if compact else 0, ctypes.byref(h)))
         self._h = h
         self.info = self._info()
         self.M, self.a = self.info.M, self.info.a
+        self.compact = bool(compact)
         self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
         self.cplx_dtype = torch.complex128 if precision == "fp64" else torch.complex64
         self.batch_max = int(batch_max)

@@ -3,8 +3,7 @@
 // shared-memory store), so a pass never spends separate shared-memory sweeps on loading, zero-filling,
 // multiplying or storing its data.
 //
-// Radix sequences handled here: (R_first, ..., R_last) with R_first and R_last fixed at compile
-// time; the interior stages dispatch on the radix.  Sources/destinations:
+// Every stage dispatches on its radix (8, 4, 2 or 3; it must divide E).  Sources/destinations:
 //   FromSmem / ToSmem          the transform buffer
 //   a functor  V src(int i)    stage-0 input element i (global loads, zero beyond the data)
 //   a functor  void dst(int i, V v)   last-stage output element i (global stores)
@@ -98,22 +97,44 @@ __device__ __forceinline__ void fstage_mid(typename cvec<T>::t *buf, const FFTDe
     }
 }
 
-// Whole transform, first radix RF, last radix RL, at least two stages.  All threads of the CTA
-// call it.  If src is FromSmem the buffer must hold the input; if dst writes global memory, the
-// caller must meet a barrier before the buffer is written again.
-template <typename T, int E, int RF, int RL, bool INV, bool TWS, class Src, class Dst>
+// Edge stage (first or last) with the radix read from the descriptor.
+template <typename T, int E, bool INV, bool TWS, class Src, class Dst>
+__device__ __forceinline__ void fstage_edge(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P, int s,
+                                            const typename cvec<T>::t *__restrict__ tw, int lt, int tpt,
+                                            const Src &src, const Dst &dst)
+{
+    switch (__ldg(&P->R[s])) {
+    case 8:
+        if constexpr (E % 8 == 0) fstage<T, E, 8, INV, TWS>(buf, P, s, tw, lt, tpt, src, dst);
+        break;
+    case 4:
+        if constexpr (E % 4 == 0) fstage<T, E, 4, INV, TWS>(buf, P, s, tw, lt, tpt, src, dst);
+        break;
+    case 2:
+        if constexpr (E % 2 == 0) fstage<T, E, 2, INV, TWS>(buf, P, s, tw, lt, tpt, src, dst);
+        break;
+    default:
+        if constexpr (E % 3 == 0) fstage<T, E, 3, INV, TWS>(buf, P, s, tw, lt, tpt, src, dst);
+        break;
+    }
+}
+
+// Whole transform, at least two stages.  All threads of the CTA call it.  If src is FromSmem the
+// buffer must hold the input; if dst writes global memory, the caller must meet a barrier before
+// the buffer is written again.
+template <typename T, int E, bool INV, bool TWS, class Src, class Dst>
 __device__ __forceinline__ void fft_fused(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
                                           const typename cvec<T>::t *__restrict__ tw, int lt, int tpt,
                                           const Src &src, const Dst &dst)
 {
     const int nst = __ldg(&P->nst);
-    fstage<T, E, RF, INV, TWS>(buf, P, 0, tw, lt, tpt, src, ToSmem{});
+    fstage_edge<T, E, INV, TWS>(buf, P, 0, tw, lt, tpt, src, ToSmem{});
     for (int s = 1; s < nst - 1; ++s) {
         int lt_ = lt;
         asm volatile("" : "+r"(lt_));
         fstage_mid<T, E, INV, TWS>(buf, P, s, tw, lt_, tpt);
     }
-    fstage<T, E, RL, INV, TWS>(buf, P, nst - 1, tw, lt, tpt, FromSmem{}, dst);
+    fstage_edge<T, E, INV, TWS>(buf, P, nst - 1, tw, lt, tpt, FromSmem{}, dst);
 }
 
 }  // namespace wsc

@@ -1,24 +1,46 @@
-// fsmask.cu -- Fourier-smoothed indicator of Sec. 2.4 (eq. (tfs)), built on the GPU in FP64.
+// fsmask.cu -- plan-time FP64 line transforms: the Fourier-smoothed indicator of Sec. 2.4 and the
+// compact-embedding multiplier.
 //
-//   mask_j = Re chi^n_Omega(x_j) * psi(x_j),  x_j = j/n,
-//   chi^n_Omega(x) = sum_{k in F_n} chihat_b(k) e^{2 pi i k.x/b},  chihat_b(k) = (1/b^2) int_Omega e^{-2 pi i k.y/b} dy,
+// k_lines transforms `nlines` lines of length L in FP64, each generated on the fly (an analytic
+// coefficient table, a moment-table lookup, a mirrored weight table, or a strided read), and
+// stores the first `keep` outputs of each line with arbitrary strides.  Chained, two such launches
+// give a pruned 2-D transform.
 //
-// read with period b and the index set F_n of eq. (An) (the printed e^{2 pi i k.x} with k in F_n
-// mixes period 1 and nb modes; the period-b reading makes chi^n the trigonometric interpolant the
-// scheme itself uses).  Its samples are one M x M inverse DFT of chihat_b cropped to n x n:
-// a column kernel generates chihat_b(., k2) analytically, inverse-transforms it along k1 and keeps
-// rows j1 < n; the complex row pass then transforms along k2 and keeps j2 < n.
+// (1) Fourier smoothing (Sec. 2.4, eq. (tfs) read with period b and the index set F_n of eq. (An)):
+//   mask_j = Re chi^n_Omega(x_j) * psi(x_j),  chi^n_Omega(x) = sum_{k in F_n} chihat_b(k) e^{2 pi i k.x/b},
+//   chihat_b(k) = (1/b^2) int_Omega e^{-2 pi i k.y/b} dy,
 //   disk  (c1, c2, r):   chihat_b = e^{-2 pi i k.c/b} r J1(2 pi |k| r/b) / (b |k|),  k = 0: pi r^2/b^2
 //   rect  (x0, x1, y0, y1): product over the axes of (e^{-2 pi i k s0/b} - e^{-2 pi i k s1/b})/(2 pi i k),
-//                         k = 0: (s1 - s0)/b
-// psi(x) = w(x1) w(x2), w = 1 on [delta, 1 - delta], w(t) = varkappa((delta - t)/delta) below delta and
-// mirrored above 1 - delta, with the half-window varkappa(t) = exp(2 e^{-1/t}/(t - 1)) of eq. (halfwindow1).
+//                           k = 0: (s1 - s0)/b
+//   psi(x) = w(x1) w(x2), w = 1 on [delta, 1 - delta], w(t) = varkappa((delta - t)/delta) below delta
+//   and mirrored above 1 - delta, with varkappa(t) = exp(2 e^{-1/t}/(t - 1)) of eq. (halfwindow1).
+//   Its samples are one M x M inverse DFT of chihat_b cropped to n x n.
+//
+// (2) Compact embedding.  A_n u is the quadrature of eq. (quad): (A_n u)_i = sum_j w(i - j) u_j with
+//   w(d) = (1/M^2) sum_{k in F_n} ghat(k) e^{2 pi i k.d/M}, |d1|, |d2| <= n - 1 (eq. (quad_wts)).  Placing
+//   w on the 2n-periodic lattice (w(d) at d mod 2n, zero at the unused index n) turns the same sum into
+//   a cyclic convolution of period L = 2n, so A_n u = crop_n(ifft2_L(G2 . fft2_L(pad_L u))) with
+//   G2 = fft2_L(w), exactly (up to rounding).  G2 is built here from the moment table: an M x M inverse
+//   DFT cropped to the n x n quadrant of w (w is even in each index), then an L x L forward DFT whose
+//   (n+1) x (n+1) quadrant is kept (G2 is even as well).
 #include <cmath>
 #include <vector>
 
 #include "passes.cuh"
 
 namespace wsc {
+
+struct LineGen {
+    int mode;             // 0 disk chihat, 1 rect chihat, 2 real quadrant, 3 complex quadrant,
+                          // 4 mirrored n x n table on the L-periodic lattice, 5 strided read
+    int L;                // line length
+    double b, g[4];       // modes 0, 1
+    const double *quad;   // modes 2, 3: quadrant [k2][k1] of a table of period L, h = L/2 + 1 per row
+    int h;
+    const double2 *src;   // modes 4, 5
+    int n;                // mode 4: table side
+    long long sl, se;     // mode 5: src[line * sl + e * se]
+};
 
 __device__ double2 chihat(int shape, const double *g, double b, int M, int q1, int q2)
 {
@@ -49,20 +71,46 @@ __device__ double2 chihat(int shape, const double *g, double b, int M, int q1, i
     return make_double2(f[0].x * f[1].x - f[0].y * f[1].y, f[0].x * f[1].y + f[0].y * f[1].x);
 }
 
-// Column k2 of chihat_b, inverse DFT along k1 (unnormalised, e^{+}), rows j1 < n into W[k2][j1].
-__global__ void __launch_bounds__(512, 1) k_fs_cols(double2 *__restrict__ W, const FFTDesc *__restrict__ P,
-                                                    const double2 *__restrict__ tw, int n, int M, int tpt,
-                                                    int shape, double g0, double g1, double g2, double g3, double b)
+__device__ __forceinline__ double2 line_value(const LineGen &G, int line, int e)
+{
+    switch (G.mode) {
+    case 0:
+    case 1: return chihat(G.mode, G.g, G.b, G.L, e, line);
+    case 2:
+    case 3: {
+        const int k1 = e <= G.L / 2 ? e : G.L - e, k2 = line <= G.L / 2 ? line : G.L - line;
+        const size_t i = (size_t)k2 * G.h + k1;
+        return G.mode == 2 ? make_double2(G.quad[i], 0.0) : make_double2(G.quad[2 * i], G.quad[2 * i + 1]);
+    }
+    case 4: {
+        // w(d1, d2) with d = e for e < n, L - e for e > n, nothing at e = n
+        const int d1 = line < G.n ? line : (line > G.L - G.n ? G.L - line : -1);
+        const int d2 = e < G.n ? e : (e > G.L - G.n ? G.L - e : -1);
+        if (d1 < 0 || d2 < 0) return make_double2(0.0, 0.0);
+        return G.src[(size_t)d1 * G.n + d2];
+    }
+    default: return G.src[line * G.sl + e * G.se];
+    }
+}
+
+// out[line * ol + e * oe] = scale * DFT_L(line)[e] for e < keep (INV: e^{+}, unnormalised).
+template <bool INV>
+__global__ void __launch_bounds__(512, 1) k_lines(LineGen G, double2 *__restrict__ out, int nlines, int keep,
+                                                  long long ol, long long oe, double scale,
+                                                  const FFTDesc *__restrict__ P, const double2 *__restrict__ tw,
+                                                  int tpt)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *buf = reinterpret_cast<double2 *>(smem_raw);
-    const double geom[4] = {g0, g1, g2, g3};
     const int lt = threadIdx.x;
-    for (int k2 = blockIdx.x; k2 < M; k2 += gridDim.x) {
-        for (int e = lt; e < M; e += tpt) buf[pidx<double>(e)] = chihat(shape, geom, b, M, e, k2);
+    for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
+        for (int e = lt; e < G.L; e += tpt) buf[pidx<double>(e)] = line_value(G, line, e);
         __syncthreads();
-        fft_smem<double, 0, true, false>(buf, P, tw, lt, tpt);
-        for (int e = lt; e < n; e += tpt) W[(size_t)k2 * n + e] = buf[pidx<double>(e)];
+        fft_smem<double, 0, INV, false>(buf, P, tw, lt, tpt);
+        for (int e = lt; e < keep; e += tpt) {
+            const double2 v = buf[pidx<double>(e)];
+            out[line * ol + e * oe] = make_double2(scale * v.x, scale * v.y);
+        }
         __syncthreads();
     }
 }
@@ -92,9 +140,131 @@ __global__ void k_fs_finish(const double2 *__restrict__ chi, T *__restrict__ mas
     }
 }
 
+// quadrant [k2][k1] of G2 (real or complex) from the complex transform output
+__global__ void k_take_quadrant(const double2 *__restrict__ in, double *__restrict__ out, long long N, int cplx)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (cplx) {
+            out[2 * i] = in[i].x;
+            out[2 * i + 1] = in[i].y;
+        } else {
+            out[i] = in[i].x;
+        }
+    }
+}
+
 int generic_threads(const FFTDesc &P);
 bool factorize_any(int L, FFTDesc &d);
 void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im);
+
+// Device-side FFT set-up of one line length (descriptor, twiddles, launch shape).
+struct LineFFT {
+    FFTDesc d;
+    FFTDesc *dd = nullptr;
+    double2 *tw = nullptr;
+    int tpt = 0;
+    size_t smem = 0;
+    std::vector<double> twh;
+    ~LineFFT()
+    {
+        cudaFree(dd);
+        cudaFree(tw);
+    }
+    conv_status init(int L, cudaStream_t st)
+    {
+        if (!factorize_any(L, d)) return fail(CONV_EUNSUPPORTED, "line length not 2^a 3^b 5^c");
+        tpt = generic_threads(d);
+        smem = (size_t)padded_len<double>(L) * sizeof(double2);
+        int optin = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (smem > (size_t)optin || tpt > 512) return fail(CONV_EUNSUPPORTED, "FP64 line transform does not fit one CTA");
+        stage_twiddles(d, twh);
+        if (cudaMalloc(&dd, sizeof(FFTDesc)) != cudaSuccess || cudaMalloc(&tw, twh.size() * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CONV_ENOMEM, "line transform tables");
+        }
+        WSC_CUDA(cudaMemcpyAsync(dd, &d, sizeof(FFTDesc), cudaMemcpyHostToDevice, st));
+        WSC_CUDA(cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        WSC_CUDA(cudaFuncSetAttribute(k_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        WSC_CUDA(cudaFuncSetAttribute(k_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        return CONV_OK;
+    }
+    template <bool INV>
+    void run(const LineGen &G, double2 *out, int nlines, int keep, long long ol, long long oe, double scale,
+             int sms, cudaStream_t st) const
+    {
+        k_lines<INV><<<std::min(nlines, sms * 2), tpt, smem, st>>>(G, out, nlines, keep, ol, oe, scale, dd, tw, tpt);
+    }
+};
+
+static int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Compact-embedding multiplier G2 (quadrant [k2][k1], k1, k2 <= n, FP64, real or complex) from the
+// period-M moment quadrant ghat (h = M/2 + 1 per row).  Synchronises `st`.
+conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, double *g2_out, cudaStream_t st)
+{
+    const int L = 2 * n, h = M / 2 + 1, sms = sm_count();
+    LineFFT fm, fl;
+    conv_status rc = fm.init(M, st);
+    if (rc == CONV_OK) rc = fl.init(L, st);
+    if (rc != CONV_OK) return rc;
+    double2 *t1 = nullptr, *w = nullptr, *t2 = nullptr, *g2 = nullptr;
+    const size_t n1 = (size_t)n + 1;
+    bool ok = cudaMalloc(&t1, (size_t)M * n * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&w, (size_t)n * n * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&t2, n1 * L * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&g2, n1 * n1 * sizeof(double2)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(t1);
+        cudaFree(w);
+        cudaFree(t2);
+        cudaFree(g2);
+        return fail(CONV_ENOMEM, "compact-embedding buffers");
+    }
+    LineGen G{};
+    // w = (1/M^2) IDFT_M x M (ghat) on [0, n)^2: columns k2 (lines) along k1, keep d1 < n -> t1[k2][d1]
+    G.mode = cplx ? 3 : 2;
+    G.L = M;
+    G.quad = ghat;
+    G.h = h;
+    fm.run<true>(G, t1, M, n, n, 1, 1.0, sms, st);
+    // rows d1: along k2, keep d2 < n -> w[d1][d2]
+    G.mode = 5;
+    G.src = t1;
+    G.sl = 1;
+    G.se = n;
+    fm.run<true>(G, w, n, n, n, 1, 1.0 / ((double)M * (double)M), sms, st);
+    // G2 = DFT_L x L (w on the L-periodic lattice): rows e1 along e2, keep k2 <= n -> t2[k2][e1]
+    G.mode = 4;
+    G.L = L;
+    G.src = w;
+    G.n = n;
+    fl.run<false>(G, t2, L, n + 1, 1, L, 1.0, sms, st);
+    // columns k2 along e1, keep k1 <= n -> g2[k2][k1]
+    G.mode = 5;
+    G.src = t2;
+    G.sl = L;
+    G.se = 1;
+    fl.run<false>(G, g2, n + 1, n + 1, n + 1, 1, 1.0, sms, st);
+    const long long NQ = (long long)n1 * n1;
+    k_take_quadrant<<<(int)std::min<long long>((NQ + 255) / 256, sms * 8LL), 256, 0, st>>>(g2, g2_out, NQ, cplx ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(t1);
+    cudaFree(w);
+    cudaFree(t2);
+    cudaFree(g2);
+    if (e != cudaSuccess) return cuda_fail(e, "compact-embedding table");
+    return CONV_OK;
+}
 
 }  // namespace wsc
 
@@ -106,67 +276,39 @@ extern "C" conv_status conv_fs_mask(conv_plan_t p, int shape, const double *geom
     if (!p || !geom || !mask) return fail(CONV_EINVAL, "bad argument");
     if (shape != 0 && shape != 1) return fail(CONV_EINVAL, "shape must be 0 (disk) or 1 (rectangle)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int n = p->n, M = p->M;
-    FFTDesc d;
-    if (!factorize_any(M, d)) return fail(CONV_EUNSUPPORTED, "transform length not 2^a 3^b 5^c");
-    const int tpt = generic_threads(d);
-    const size_t smem = (size_t)padded_len<double>(M) * sizeof(double2);
-    int smem_optin = 0, sms = 0;
-    WSC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-    WSC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-    if (smem > (size_t)smem_optin || tpt > 512)
-        return fail(CONV_EUNSUPPORTED, "FP64 transform of length M does not fit one CTA");
-    std::vector<double> twh;
-    stage_twiddles(d, twh);
-    double2 *tw = nullptr, *W = nullptr, *chi = nullptr;
-    FFTDesc *dd = nullptr;
-    bool ok = cudaMalloc(&tw, twh.size() * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&W, (size_t)M * n * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&chi, (size_t)n * n * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&dd, sizeof(FFTDesc)) == cudaSuccess;
-    conv_status rc = CONV_OK;
-    if (!ok) {
+    const int n = p->n, M = p->Mb, sms = sm_count();
+    LineFFT f;
+    conv_status rc = f.init(M, st);
+    if (rc != CONV_OK) return rc;
+    double2 *W = nullptr, *chi = nullptr;
+    if (cudaMalloc(&W, (size_t)M * n * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&chi, (size_t)n * n * sizeof(double2)) != cudaSuccess) {
         cudaGetLastError();
-        rc = fail(CONV_ENOMEM, "FS mask buffers");
+        cudaFree(W);
+        return fail(CONV_ENOMEM, "FS mask buffers");
     }
-    if (rc == CONV_OK) {
-        cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(dd, &d, sizeof(FFTDesc), cudaMemcpyHostToDevice, st);
-        cudaFuncSetAttribute(k_fs_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_c2c_rows_inv<double, 0, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        k_fs_cols<<<std::min(M, sms), tpt, smem, st>>>(W, dd, tw, n, M, tpt, shape, geom[0], geom[1], geom[2],
-                                                     shape == 1 ? geom[3] : 0.0, p->b);
-        PassArgs<double> a;
-        a.in = W;
-        a.mask = nullptr;
-        a.out = chi;
-        a.ghat = nullptr;
-        a.u = nullptr;
-        a.tw = tw;
-        a.tw_len = d.tw_len;
-        a.P = dd;
-        a.n = n;
-        a.h = p->h;
-        a.M = M;
-        a.tpt = tpt;
-        a.units = n;
-        a.batch = 1;
-        a.alpha = make_double2(1.0, 0.0);
-        a.beta = 0.0;
-        k_c2c_rows_inv<double, 0, false, false><<<std::min(n, sms), tpt, smem, st>>>(a);
-        int blocks = (int)std::min<long long>(((long long)n * n + 255) / 256, (long long)sms * 8);
-        if (p->prec == CONV_P_FP64)
-            k_fs_finish<double><<<blocks, 256, 0, st>>>(chi, reinterpret_cast<double *>(mask), n, delta);
-        else
-            k_fs_finish<float><<<blocks, 256, 0, st>>>(chi, reinterpret_cast<float *>(mask), n, delta);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "conv_fs_mask");
-    }
-    cudaFree(tw);
+    LineGen G{};
+    G.mode = shape;
+    G.L = M;
+    G.b = p->b;
+    for (int i = 0; i < (shape == 0 ? 3 : 4); ++i) G.g[i] = geom[i];
+    // columns k2 (lines) of chihat along k1, keep j1 < n -> W[k2][j1]
+    f.run<true>(G, W, M, n, n, 1, 1.0, sms, st);
+    // rows j1: along k2, keep j2 < n -> chi[j1][j2]
+    G.mode = 5;
+    G.src = W;
+    G.sl = 1;
+    G.se = n;
+    f.run<true>(G, chi, n, n, n, 1, 1.0, sms, st);
+    const int blocks = (int)std::min<long long>(((long long)n * n + 255) / 256, (long long)sms * 8);
+    if (p->prec == CONV_P_FP64)
+        k_fs_finish<double><<<blocks, 256, 0, st>>>(chi, reinterpret_cast<double *>(mask), n, delta);
+    else
+        k_fs_finish<float><<<blocks, 256, 0, st>>>(chi, reinterpret_cast<float *>(mask), n, delta);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(W);
     cudaFree(chi);
-    cudaFree(dd);
-    return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "conv_fs_mask");
+    return CONV_OK;
 }

@@ -160,6 +160,8 @@ static void gauss_legendre(int n, double *x, double *w)
     }
 }
 
+conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, double *g2_out, cudaStream_t st);
+
 conv_status build_ghat(conv_plan_s *p)
 {
     double gx[GL_NODES], gw[GL_NODES];
@@ -167,10 +169,11 @@ conv_status build_ghat(conv_plan_s *p)
     cudaStream_t st = p->setup_stream;
     WSC_CUDA(cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, st));
     WSC_CUDA(cudaMemcpyToSymbolAsync(c_glw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, st));
-    const long long N = (long long)p->h * p->h;
+    const int hb = p->Mb / 2 + 1;
+    const long long N = (long long)hb * hb;
     const int comps = p->complex_ghat ? 2 : 1;
     p->ghat_bytes = (size_t)N * comps * sizeof(double);
-    if (cudaMalloc(&p->ghat64, p->ghat_bytes) != cudaSuccess) {
+    if (cudaMalloc(&p->ghat_paper, p->ghat_bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(CONV_ENOMEM, "cudaMalloc of the moment table failed");
     }
@@ -203,20 +206,36 @@ conv_status build_ghat(conv_plan_s *p)
         WSC_CUDA(cudaMemcpyAsync(htab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
-    k_ghat<<<blocks, 256, 0, st>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, p->h,
-                            p->ghat64, hka, htab, hnodes);
+    k_ghat<<<blocks, 256, 0, st>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, hb,
+                                   p->ghat_paper, hka, htab, hnodes);
     if (htab) {
         cudaError_t e = cudaStreamSynchronize(st);
         cudaFree(htab);
         if (e != cudaSuccess) return cuda_fail(e, "moment table kernel");
     }
     WSC_CUDA(cudaGetLastError());
-    if (p->prec == CONV_P_FP32) {
-        if (cudaMalloc(&p->ghat32, (size_t)N * comps * sizeof(float)) != cudaSuccess) {
+    // the passes' multiplier: the moments themselves, or the compact-embedding table built from them
+    if (p->compact) {
+        const size_t nq = (size_t)(p->n + 1) * (p->n + 1) * comps;
+        p->table_bytes = nq * sizeof(double);
+        if (cudaMalloc(&p->ghat64, p->table_bytes) != cudaSuccess) {
             cudaGetLastError();
-            return fail(CONV_ENOMEM, "cudaMalloc of the FP32 moment table failed");
+            return fail(CONV_ENOMEM, "cudaMalloc of the compact multiplier failed");
         }
-        k_to_f32<<<blocks, 256, 0, st>>>(p->ghat64, reinterpret_cast<float *>(p->ghat32), N * comps);
+        conv_status rc = build_compact_table(p->ghat_paper, p->complex_ghat, p->n, p->Mb, p->ghat64, st);
+        if (rc != CONV_OK) return rc;
+    } else {
+        p->ghat64 = p->ghat_paper;
+        p->table_bytes = p->ghat_bytes;
+    }
+    if (p->prec == CONV_P_FP32) {
+        const long long NT = (long long)(p->table_bytes / sizeof(double));
+        if (cudaMalloc(&p->ghat32, (size_t)NT * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CONV_ENOMEM, "cudaMalloc of the FP32 multiplier failed");
+        }
+        const int b2 = (int)std::min<long long>((NT + 255) / 256, 152LL * 16);
+        k_to_f32<<<b2, 256, 0, st>>>(p->ghat64, reinterpret_cast<float *>(p->ghat32), NT);
         WSC_CUDA(cudaGetLastError());
     }
     WSC_CUDA(cudaStreamSynchronize(st));

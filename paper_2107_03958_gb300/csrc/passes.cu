@@ -157,27 +157,34 @@ static int generic_tpt(const FFTDesc &P)
     return (need + 31) / 32 * 32;
 }
 
-// Fused-transform variants: (precision, E, first radix, last radix).
-#define WSC_DISPATCH_FUSED(prec, E, tws, CALL)                                                          \
-    do {                                                                                                \
-        if ((prec) == CONV_P_FP32) {                                                                    \
-            if (tws) { typedef float T_; constexpr int E_ = 24, RF_ = 8, RL_ = 3; constexpr bool W_ = true; CALL; } \
-            else { typedef float T_; constexpr int E_ = 24, RF_ = 8, RL_ = 3; constexpr bool W_ = false; CALL; }    \
-        } else if ((E) == 12) {                                                                         \
-            if (tws) { typedef double T_; constexpr int E_ = 12, RF_ = 4, RL_ = 3; constexpr bool W_ = true; CALL; } \
-            else { typedef double T_; constexpr int E_ = 12, RF_ = 4, RL_ = 3; constexpr bool W_ = false; CALL; }    \
-        } else {                                                                                        \
-            if (tws) { typedef double T_; constexpr int E_ = 24, RF_ = 8, RL_ = 3; constexpr bool W_ = true; CALL; } \
-            else { typedef double T_; constexpr int E_ = 24, RF_ = 8, RL_ = 3; constexpr bool W_ = false; CALL; }    \
-        }                                                                                               \
+// Fused-transform variants: (precision, E) with E in {24, 16} (FP32) or {12, 24, 8} (FP64).
+#define WSC_DISPATCH_FUSED(prec, E, tws, CALL)                                                             \
+    do {                                                                                                   \
+        if ((prec) == CONV_P_FP32) {                                                                       \
+            if ((E) == 16) {                                                                               \
+                if (tws) { typedef float T_; constexpr int E_ = 16; constexpr bool W_ = true; CALL; }      \
+                else { typedef float T_; constexpr int E_ = 16; constexpr bool W_ = false; CALL; }         \
+            } else {                                                                                       \
+                if (tws) { typedef float T_; constexpr int E_ = 24; constexpr bool W_ = true; CALL; }      \
+                else { typedef float T_; constexpr int E_ = 24; constexpr bool W_ = false; CALL; }         \
+            }                                                                                              \
+        } else if ((E) == 12) {                                                                            \
+            if (tws) { typedef double T_; constexpr int E_ = 12; constexpr bool W_ = true; CALL; }         \
+            else { typedef double T_; constexpr int E_ = 12; constexpr bool W_ = false; CALL; }            \
+        } else if ((E) == 8) {                                                                             \
+            if (tws) { typedef double T_; constexpr int E_ = 8; constexpr bool W_ = true; CALL; }          \
+            else { typedef double T_; constexpr int E_ = 8; constexpr bool W_ = false; CALL; }             \
+        } else {                                                                                           \
+            if (tws) { typedef double T_; constexpr int E_ = 24; constexpr bool W_ = true; CALL; }         \
+            else { typedef double T_; constexpr int E_ = 24; constexpr bool W_ = false; CALL; }            \
+        }                                                                                                  \
     } while (0)
 
 static bool fused_eligible(conv_precision prec, int E, const FFTDesc &d)
 {
     if (d.nst < 2) return false;
-    const int RF = d.R[0], RL = d.R[d.nst - 1];
-    if (prec == CONV_P_FP32) return E == 24 && RF == 8 && RL == 3;
-    return (E == 12 && RF == 4 && RL == 3) || (E == 24 && RF == 8 && RL == 3);
+    if (prec == CONV_P_FP32) return E == 24 || E == 16;
+    return E == 12 || E == 24 || E == 8;
 }
 
 int generic_threads(const FFTDesc &P) { return generic_tpt(P); }
@@ -187,9 +194,10 @@ static conv_status set_all_attrs(int smem)
 {
     conv_status rc = CONV_OK;
     for (int tws = 0; tws < 2 && rc == CONV_OK; ++tws) {
-        WSC_DISPATCH_FUSED(CONV_P_FP32, 24, tws, rc = (set_attrs_fused<T_, E_, RF_, RL_, W_>(smem)));
-        if (rc == CONV_OK) WSC_DISPATCH_FUSED(CONV_P_FP64, 12, tws, rc = (set_attrs_fused<T_, E_, RF_, RL_, W_>(smem)));
-        if (rc == CONV_OK) WSC_DISPATCH_FUSED(CONV_P_FP64, 24, tws, rc = (set_attrs_fused<T_, E_, RF_, RL_, W_>(smem)));
+        for (int E : {24, 16})
+            if (rc == CONV_OK) WSC_DISPATCH_FUSED(CONV_P_FP32, E, tws, rc = (set_attrs_fused<T_, E_, W_>(smem)));
+        for (int E : {12, 24, 8})
+            if (rc == CONV_OK) WSC_DISPATCH_FUSED(CONV_P_FP64, E, tws, rc = (set_attrs_fused<T_, E_, W_>(smem)));
     }
     for (int prec = 0; prec < 2 && rc == CONV_OK; ++prec)
         for (int tws = 0; tws < 2 && rc == CONV_OK; ++tws)
@@ -261,7 +269,7 @@ conv_status select_transform(conv_plan_s *p)
         p->fused = fused_eligible(p->prec, E, d) && force_f != 0;
         int bps = 1;
         if (p->fused)
-            WSC_DISPATCH_FUSED(p->prec, E, tws, bps = (blocks_per_sm_fused<T_, E_, RF_, RL_, W_>(tpt * G, p->rows.smem)));
+            WSC_DISPATCH_FUSED(p->prec, E, tws, bps = (blocks_per_sm_fused<T_, E_, W_>(tpt * G, p->rows.smem)));
         else
             WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, p->rows.smem)));
         p->rows.max_ctas = p->cols.max_ctas = bps * sms;
@@ -275,7 +283,7 @@ conv_status select_transform(conv_plan_s *p)
             p->inv.groups = Gi;
             p->inv.smem = per * Gi;
             int bi = 1;
-            WSC_DISPATCH_FUSED(p->prec, E, false, bi = (blocks_per_sm_fused<T_, E_, RF_, RL_, W_>(tpt * Gi, p->inv.smem)));
+            WSC_DISPATCH_FUSED(p->prec, E, false, bi = (blocks_per_sm_fused<T_, E_, W_>(tpt * Gi, p->inv.smem)));
             p->inv.max_ctas = bi * sms;
         }
         return CONV_OK;
@@ -290,7 +298,7 @@ conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, voi
     conv_status rc = CONV_OK;
     if (p->fused)
         WSC_DISPATCH_FUSED(p->prec, p->elems, p->tws,
-                           rc = (run_fused<T_, E_, RF_, RL_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
+                           rc = (run_fused<T_, E_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
     else
         WSC_DISPATCH(p->prec, p->elems, p->tws,
                      rc = (run_pipeline<T_, E_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));

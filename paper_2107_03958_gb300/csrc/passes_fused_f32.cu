@@ -2,10 +2,16 @@
 #include "passes_fused.cuh"
 
 namespace wsc {
-template conv_status run_fused<float, 24, 8, 3, true>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
-template conv_status set_attrs_fused<float, 24, 8, 3, true>(int);
-template int blocks_per_sm_fused<float, 24, 8, 3, true>(int, size_t);
-template conv_status run_fused<float, 24, 8, 3, false>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
-template conv_status set_attrs_fused<float, 24, 8, 3, false>(int);
-template int blocks_per_sm_fused<float, 24, 8, 3, false>(int, size_t);
+template conv_status run_fused<float, 24, true>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
+template conv_status set_attrs_fused<float, 24, true>(int);
+template int blocks_per_sm_fused<float, 24, true>(int, size_t);
+template conv_status run_fused<float, 24, false>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
+template conv_status set_attrs_fused<float, 24, false>(int);
+template int blocks_per_sm_fused<float, 24, false>(int, size_t);
+template conv_status run_fused<float, 16, true>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
+template conv_status set_attrs_fused<float, 16, true>(int);
+template int blocks_per_sm_fused<float, 16, true>(int, size_t);
+template conv_status run_fused<float, 16, false>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
+template conv_status set_attrs_fused<float, 16, false>(int);
+template int blocks_per_sm_fused<float, 16, false>(int, size_t);
 }  // namespace wsc

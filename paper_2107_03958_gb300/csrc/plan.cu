@@ -83,7 +83,8 @@ const char *conv_last_error(void) { return g_last_error.c_str(); }
 void conv_destroy(conv_plan_t p)
 {
     if (!p) return;
-    if (p->ghat64) cudaFree(p->ghat64);
+    if (p->ghat64 && p->ghat64 != p->ghat_paper) cudaFree(p->ghat64);
+    if (p->ghat_paper) cudaFree(p->ghat_paper);
     if (p->ghat32) cudaFree(p->ghat32);
     if (p->tw) cudaFree(p->tw);
     if (p->fft_dev) cudaFree(p->fft_dev);
@@ -99,6 +100,13 @@ void conv_destroy(conv_plan_t p)
 conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den, int n,
                       double trunc_a, conv_precision precision, conv_io io, int batch_max,
                       conv_plan_t *plan)
+{
+    return conv_plan_ex(kernel, period_num, period_den, n, trunc_a, precision, io, batch_max, 0, plan);
+}
+
+conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_den, int n,
+                         double trunc_a, conv_precision precision, conv_io io, int batch_max, int flags,
+                         conv_plan_t *plan)
 {
     g_last_error.clear();
     if (!plan) return fail(CONV_EINVAL, "plan output pointer is NULL");
@@ -138,13 +146,16 @@ conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den,
             return fail(CONV_EINVAL, "period b < 1 + sqrt 2 admits no default truncation radius; pass trunc_a");
         a = 0.5 * (std::sqrt(2.0) + b - 1.0);
     }
+    if (flags & ~CONV_PLAN_COMPACT) return fail(CONV_EINVAL, "unknown plan flags");
     conv_plan_s *p = new conv_plan_s();
     p->kern = *kernel;
     p->pnum = period_num;
     p->pden = period_den;
     p->n = n;
-    p->M = M;
-    p->h = M / 2 + 1;
+    p->Mb = M;
+    p->compact = (flags & CONV_PLAN_COMPACT) != 0;
+    p->M = p->compact ? 2 * n : M;
+    p->h = p->M / 2 + 1;
     p->b = b;
     p->a = a;
     p->prec = precision;
@@ -156,9 +167,9 @@ conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den,
         delete p;
         return fail(CONV_ECUDA, "no CUDA device");
     }
-    if (M < 4) {
+    if (p->M < 4) {
         delete p;
-        return fail(CONV_EUNSUPPORTED, "transform length M = n b must be at least 4");
+        return fail(CONV_EUNSUPPORTED, "transform length must be at least 4");
     }
     // plan-time device work runs on a private non-blocking stream, so building a plan never waits
     // for (or stalls) work other threads have in flight on the device
@@ -238,7 +249,9 @@ conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
     if (!p || !info) return fail(CONV_EINVAL, "bad argument");
     std::memset(info, 0, sizeof(*info));
     info->n = p->n;
-    info->M = p->M;
+    info->M = p->Mb;
+    info->transform_len = p->M;
+    info->compact = p->compact ? 1 : 0;
     info->period_num = p->pnum;
     info->period_den = p->pden;
     info->b = p->b;
@@ -249,7 +262,7 @@ conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
     info->batch_max = p->batch_max;
     info->nstages = p->fft.nst;
     for (int s = 0; s < p->fft.nst && s < 16; ++s) info->radices[s] = p->fft.R[s];
-    info->ghat_bytes = p->ghat_bytes;
+    info->ghat_bytes = p->ghat_bytes + (p->compact ? p->table_bytes : 0);
     info->workspace_bytes = p->ws_bytes;
     info->threads_rows = p->rows.tpt;
     info->groups_rows = p->rows.groups;
@@ -261,7 +274,7 @@ conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
 conv_status conv_ghat_to_host(conv_plan_t p, double *host_out)
 {
     if (!p || !host_out) return fail(CONV_EINVAL, "bad argument");
-    WSC_CUDA(cudaMemcpy(host_out, p->ghat64, p->ghat_bytes, cudaMemcpyDeviceToHost));
+    WSC_CUDA(cudaMemcpy(host_out, p->ghat_paper, p->ghat_bytes, cudaMemcpyDeviceToHost));
     return CONV_OK;
 }
 

@@ -33,11 +33,11 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
                          double are, double aim, double beta, void *ws, cudaStream_t st);
 template <typename T, int E, bool TWS> conv_status set_attrs(int smem);
 template <typename T, int E, bool TWS> int blocks_per_sm(int threads, size_t smem);
-template <typename T, int E, int RF, int RL, bool TWS>
+template <typename T, int E, bool TWS>
 conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
                       double aim, double beta, void *ws, cudaStream_t st);
-template <typename T, int E, int RF, int RL, bool TWS> conv_status set_attrs_fused(int smem);
-template <typename T, int E, int RF, int RL, bool TWS> int blocks_per_sm_fused(int threads, size_t smem);
+template <typename T, int E, bool TWS> conv_status set_attrs_fused(int smem);
+template <typename T, int E, bool TWS> int blocks_per_sm_fused(int threads, size_t smem);
 
 // Launch shape of one pass family (rows or columns).
 struct LaunchShape {
@@ -51,7 +51,10 @@ struct LaunchShape {
 
 struct conv_plan_s {
     conv_kernel kern;
-    int pnum, pden, n, M, h;  // h = M/2 + 1
+    int pnum, pden, n;
+    int Mb;                   // n b: the period-b grid of eq. (An), on which the moments live
+    int M, h;                 // transform length of the passes (Mb, or 2n for the compact embedding), h = M/2 + 1
+    bool compact = false;     // passes use the 2n-periodic embedding of the quadrature weights
     double b, a;
     conv_precision prec;
     conv_io io;
@@ -64,8 +67,12 @@ struct conv_plan_s {
     bool fused; // passes on the fused transform (global-memory first/last stages)
     wsc::FFTDesc fft;
     wsc::FFTDesc *fft_dev = nullptr;  // device copy read by the pass kernels
-    // FP64 moment quadrant [k2][k1], k1, k2 in [0, h): real (h*h doubles) or complex (h*h double2)
+    // FP64 moment quadrant [k2][k1], k1, k2 <= Mb/2: real or complex (ghat_bytes)
+    double *ghat_paper = nullptr;
+    // FP64 multiplier of the passes, quadrant [k2][k1], k1, k2 < h: the moments (aliases ghat_paper)
+    // or the compact-embedding table (table_bytes)
     double *ghat64 = nullptr;
+    size_t table_bytes = 0;
     // FP32 copy for FP32 plans (float or float2)
     void *ghat32 = nullptr;
     size_t ghat_bytes = 0;

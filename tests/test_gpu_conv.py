@@ -86,12 +86,14 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("compact", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("n,period,name,io", CASES)
-def test_conv_matches_oracle(n, period, name, io, prec):
+def test_conv_matches_oracle(n, period, name, io, prec, compact):
+    """Period-b passes and the compact (2n-periodic) embedding of the same quadrature weights."""
     kw = KERNELS[name]
     a = 0.0 if period == 3 else 0.45 * 2  # b = 2 needs an explicit radius
-    plan = ConvPlan(n=n, period=period, trunc_a=a, precision=prec, io=io, batch_max=3, **kw)
+    plan = ConvPlan(n=n, period=period, trunc_a=a, precision=prec, io=io, batch_max=3, compact=compact, **kw)
     rng = np.random.default_rng(n * 7 + period)
     B = 3
     u = rng.standard_normal((B, n, n))
@@ -181,13 +183,14 @@ def test_invalid_arguments_are_reported():
         plan.apply(u[0], out=u[0])  # aliasing
 
 
+@pytest.mark.parametrize("compact", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_full_size_kernel_sweep(prec):
+def test_full_size_kernel_sweep(prec, compact):
     """n = 4096, b = 3, batch 16 (the benchmark's launch configuration): densities 0 and 9 against
     the oracle's full FFT convolution."""
     n, B = 4096, 16
     kw = KERNELS["log"]
-    plan = ConvPlan(n=n, period=3, precision=prec, io="r2r", batch_max=B, **kw)
+    plan = ConvPlan(n=n, period=3, precision=prec, io="r2r", batch_max=B, compact=compact, **kw)
     u = inputs.bump_sums(n, B)
     out = plan.apply(torch.tensor(u, dtype=plan.real_dtype, device="cuda"))
     g = O.ghat_full("log", plan.M, plan.b, plan.a, scale=-INV2PI)

@@ -32,12 +32,13 @@ def _true_residual(g, M, kappa, m, f, x):
     return np.linalg.norm(r) / np.linalg.norm(f)
 
 
+@pytest.mark.parametrize("compact", [False, True])
 @pytest.mark.parametrize("n,kappa,contrast", [(32, 10.0, "bump"), (64, 10.0, "disk"), (64, 40.0, "bump")])
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
-def test_ls_solve_matches_oracle(n, kappa, contrast, mode):
+def test_ls_solve_matches_oracle(n, kappa, contrast, mode, compact):
     g, m, f, xref = _oracle(n, kappa, contrast)
     prec = "fp64" if mode == "fp64" else "fp32"
-    plan = ConvPlan("helmholtz", n=n, period=3, precision=prec, io="c2c", kappa=kappa)
+    plan = ConvPlan("helmholtz", n=n, period=3, precision=prec, io="c2c", kappa=kappa, compact=compact)
     x, info = ls_solve(plan, torch.tensor(m, device="cuda"), torch.tensor(f, device="cuda"),
                        tol=1e-10, restart=50, refine=(mode == "mixed"))
     assert info["status"] == "CONV_OK", info
