@@ -186,8 +186,9 @@ struct LineFFT {
         }
         WSC_CUDA(cudaMemcpyAsync(dd, &d, sizeof(FFTDesc), cudaMemcpyHostToDevice, st));
         WSC_CUDA(cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        WSC_CUDA(cudaFuncSetAttribute(k_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        WSC_CUDA(cudaFuncSetAttribute(k_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // the opt-in maximum, so line transforms of any length can follow each other
+        WSC_CUDA(cudaFuncSetAttribute(k_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        WSC_CUDA(cudaFuncSetAttribute(k_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         return CONV_OK;
     }
     template <bool INV>

@@ -13,6 +13,38 @@
 namespace wsc {
 
 // ============================================================================ R2R
+// The two spectra of a row pair sit side by side (W[k][j1], W[k][j1+1]); with n even the pair
+// starts on an even element, so FP32 moves it as one 16-byte access.
+template <typename T>
+__device__ __forceinline__ void load_pair(const typename cvec<T>::t *p, typename cvec<T>::t &A,
+                                          typename cvec<T>::t &B, bool has2, bool vec)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (vec && has2) {
+            const float4 q = *reinterpret_cast<const float4 *>(p);
+            A = make_float2(q.x, q.y);
+            B = make_float2(q.z, q.w);
+            return;
+        }
+    }
+    A = p[0];
+    B = has2 ? p[1] : cmk<typename cvec<T>::t>(0, 0);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(typename cvec<T>::t *p, typename cvec<T>::t A, typename cvec<T>::t B,
+                                           bool has2, bool vec)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (vec && has2) {
+            *reinterpret_cast<float4 *>(p) = make_float4(A.x, A.y, B.x, B.y);
+            return;
+        }
+    }
+    p[0] = A;
+    if (has2) p[1] = B;
+}
+
 template <typename T, int E, bool TWS>
 __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
 {
@@ -21,6 +53,7 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
     const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2;
+    const bool pair_vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0;
     for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
         const int unit = base + g;
         const bool valid = unit < a.units;
@@ -42,8 +75,9 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
             V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * h * n;
             for (int k = lt; k < h; k += a.tpt) {
                 V Zk = buf[pidx<T>(k)], Zm = buf[pidx<T>(k == 0 ? 0 : M - k)];
-                Wb[(size_t)k * n + j1] = cmk<V>((T)0.5 * (Zk.x + Zm.x), (T)0.5 * (Zk.y - Zm.y));
-                if (has2) Wb[(size_t)k * n + j1 + 1] = cmk<V>((T)0.5 * (Zk.y + Zm.y), (T)-0.5 * (Zk.x - Zm.x));
+                const V A = cmk<V>((T)0.5 * (Zk.x + Zm.x), (T)0.5 * (Zk.y - Zm.y));
+                const V B = cmk<V>((T)0.5 * (Zk.y + Zm.y), (T)-0.5 * (Zk.x - Zm.x));
+                store_pair<T>(Wb + (size_t)k * n + j1, A, B, has2, pair_vec);
             }
         }
         __syncthreads();
@@ -87,6 +121,7 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
     const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2;
+    const bool pair_vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
     const T alpha = a.alpha.x, beta = a.beta;
     for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
         const int unit = base + g;
@@ -99,8 +134,8 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
             if (!valid) return cmk<V>(0, 0);
             const bool lo = i <= M / 2;
             const size_t k = (size_t)(lo ? i : M - i);
-            const V A = Wb[k * n + j1];
-            const V B = has2 ? Wb[k * n + j1 + 1] : cmk<V>(0, 0);
+            V A, B;
+            load_pair<T>(Wb + k * n + j1, A, B, has2, pair_vec);
             return lo ? cmk<V>(A.x - B.y, A.y + B.x) : cmk<V>(A.x + B.y, B.x - A.y);
         };
         const size_t ro = (size_t)b * n * n + (size_t)j1 * n;
