@@ -66,14 +66,20 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(ws, value):
+def max_over_ranks(ws, value, device="cuda"):
+    """Slowest rank's time (the job's time for replicas that run concurrently)."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(ws, units_per_rank, ms_max):
+    """Whole-job rate of N replicas: all ranks' units over the slowest rank's time."""
+    return ws * units_per_rank / (ms_max * 1e-3)
 
 
 # ---------------------------------------------------------------- clocks
@@ -229,24 +235,27 @@ def workload_config(args):
                         "|x|^-1, |x|^-1.5, Helmholtz kappa=20}, n=%d, b=3" % args.n,
             "n": args.n, "period_b": 3, "batch": args.batch, "kernels": 5,
             "convolutions_per_step": 5 * args.batch, "precision": "fp32 (headline), fp64 reported",
+            "embedding": "compact: weights of eq. (quad_wts) from the period-3 moments, 2n-periodic "
+                         "transforms (period-3 transforms reported as fp32_period_b)",
             "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
 
 
 # ---------------------------------------------------------------- GPU legs
-def make_plans(n, batch, precision):
+def make_plans(n, batch, precision, compact):
     from paper_2107_03958_gb300.api import ConvPlan
     plans = []
     for kern, kw in SWEEP:
         io = "r2c" if kern == "helmholtz" else "r2r"
-        plans.append(ConvPlan(kern, n=n, period=3, precision=precision, io=io, batch_max=batch, **kw))
+        plans.append(ConvPlan(kern, n=n, period=3, precision=precision, io=io, batch_max=batch,
+                              compact=compact, **kw))
     return plans
 
 
-def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, host_io=False):
+def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, host_io=False, compact=True):
     """Time `steps` sweeps; returns dict with ms/step, pass timings of the real-kernel plans."""
     import torch
     from paper_2107_03958_gb300 import inputs
-    plans = make_plans(n, batch, precision)
+    plans = make_plans(n, batch, precision, compact)
     dt = torch.float64 if precision == "fp64" else torch.float32
     u_host = torch.from_numpy(inputs.bump_sums(n, batch)).to(dt)
     u = u_host.cuda()
@@ -292,10 +301,10 @@ def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, host_io=
 
 
 def r2r_bytes(plan, batch):
-    """Algorithmic HBM bytes of one column-pass launch (R2R): read and write the n x (M/2+1)
-    spectra of the batch, read the moment quadrant once."""
-    n, M = plan.n, plan.M
-    h = M // 2 + 1
+    """Algorithmic HBM bytes of one column-pass launch (R2R): read and write the n x (L/2+1)
+    spectra of the batch (L the transform length), read the multiplier quadrant once."""
+    n, L = plan.n, plan.info.transform_len
+    h = L // 2 + 1
     esz = 16 if plan.precision == "fp64" else 8
     return batch * 2 * h * n * esz + h * h * (esz // 2)
 
@@ -309,7 +318,7 @@ def ls_leg(n, kappa, repeats, stream):
     out = {}
     for mode in ("fp64", "mixed"):
         plan = ConvPlan("helmholtz", n=n, period=3, precision="fp64" if mode == "fp64" else "fp32",
-                        io="c2c", kappa=kappa)
+                        io="c2c", kappa=kappa, compact=True)
         ls_solve(plan, m, f, refine=(mode == "mixed"), stream=stream)  # warm-up
         lat, info = [], None
         for _ in range(repeats):
@@ -371,7 +380,7 @@ def serving_leg(count, seed=5):
             cplx = r["kernel"] == "helmholtz"
             out = torch.empty((n, n), dtype=torch.complex64 if cplx else torch.float32, device="cuda")
             bufs.append((u, out))
-    srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4)
+    srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4, compact=True)
     tickets = [None] * len(reqs)
     t0 = time.perf_counter()
 
@@ -445,7 +454,7 @@ def main():
     clk = clocks.stop()
     ms = max_over_ranks(ws, head["ms"])
     convs = 5 * args.batch * args.steps
-    value = ws * convs / (ms * 1e-3)
+    value = job_throughput(ws, convs, ms)
 
     # dominant kernel: the R2R column pass
     r2r = [(p, t) for p, t in zip(head["plans"], head["passes"]) if p.io == "r2r"]
@@ -459,9 +468,10 @@ def main():
     col_bytes = r2r_bytes(r2r[0][0], args.batch)
     achieved = col_bytes / (col_ms * 1e-3) / 1e9
     share = [t / sum(tot) for t in tot]
-    roofline = {"bound": "hbm", "kernel": "k_r2r_cols<float> (column pass)", "achieved": achieved,
+    roofline = {"bound": "hbm", "kernel": "kf_r2r_cols<float> (column pass, compact embedding, L = 2n)",
+                "achieved": achieved,
                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src,
-                "traffic": recorded_traffic("k_r2r_cols_fp32_n4096.txt"),
+                "traffic": recorded_traffic("kf_r2r_cols_fp32_compact_n4096.txt"),
                 "algorithmic_bytes_per_launch": col_bytes, "avg_launch_ms": col_ms,
                 "pass_share_r2r": {"rows_fwd": share[0], "cols": share[1], "rows_inv": share[2]},
                 "live_peaks": peaks}
@@ -480,7 +490,8 @@ def main():
         f64_ms = max_over_ranks(ws, f64["ms"])
         r64 = [(p, t) for p, t in zip(f64["plans"], f64["passes"]) if p.io == "r2r"]
         c64 = sum(t[0][1] for _, t in r64) / sum(t[1] for _, t in r64)
-        flops = 5 * (r64[0][0].M) * math.log2(r64[0][0].M) * 2 * (r64[0][0].M // 2 + 1) * args.batch
+        L64 = r64[0][0].info.transform_len
+        flops = 5 * L64 * math.log2(L64) * 2 * (L64 // 2 + 1) * args.batch
         extras["fp64"] = {"value": ws * 5 * args.batch * k64 / (f64_ms * 1e-3), "unit": "conv/s",
                           "ms_per_step": f64_ms / k64, "steps": k64,
                           "roofline_cols": {"bound": "alu", "achieved": flops / (c64 * 1e-3) / 1e12,
@@ -489,6 +500,18 @@ def main():
                                             "flops_model": "5 M log2 M per complex length-M FFT, 2 per column",
                                             "peak_source": "measured FP64 FMA microbenchmark"},
                           "hbm_frac_cols": r2r_bytes(r64[0][0], args.batch) / (c64 * 1e-3) / 1e9 / hbm}
+        kb = max(3, args.steps // 2)
+        pb = sweep_leg(args.n, args.batch, "fp32", kb, args.warmup, stream, timing=True, compact=False)
+        pb_ms = max_over_ranks(ws, pb["ms"])
+        rpb = [(p, t) for p, t in zip(pb["plans"], pb["passes"]) if p.io == "r2r"]
+        cpb = sum(t[0][1] for _, t in rpb) / sum(t[1] for _, t in rpb)
+        bpb = r2r_bytes(rpb[0][0], args.batch)
+        extras["fp32_period_b"] = {
+            "value": job_throughput(ws, 5 * args.batch * kb, pb_ms), "unit": "conv/s", "steps": kb,
+            "ms_per_step": pb_ms / kb, "transform_len": rpb[0][0].info.transform_len,
+            "roofline_cols": {"bound": "hbm", "achieved": bpb / (cpb * 1e-3) / 1e9, "peak": hbm,
+                              "unit": "GB/s", "frac": bpb / (cpb * 1e-3) / 1e9 / hbm,
+                              "algorithmic_bytes_per_launch": bpb, "avg_launch_ms": cpb}}
         n2 = args.n // 2
         l2 = sweep_leg(n2, args.batch, "fp32", args.steps, args.warmup, stream)
         l2_ms = max_over_ranks(ws, l2["ms"])

@@ -87,7 +87,11 @@ enum {
      * Sec. 2.2) by an FP64 M x M inverse DFT; placed on the period-2n lattice they make A_n u a
      * cyclic convolution of length L = 2n, so the passes transform 2n points per line with the
      * L x L DFT of w as multiplier.  Same A_n u up to rounding, fewer points (2n vs n b per line). */
-    CONV_PLAN_COMPACT = 1
+    CONV_PLAN_COMPACT = 1,
+    /* Autotune the launch configuration (elements per thread, twiddles in shared memory or not,
+     * fused or plain passes): time each on zero densities at batch_max and keep the fastest
+     * (results cached per shape for the process).  Allocates temporary buffers. */
+    CONV_PLAN_AUTOTUNE = 2
 };
 
 conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_den, int n,
@@ -144,6 +148,9 @@ typedef struct {
     int threads_rows, groups_rows, threads_cols, groups_cols;
     int transform_len;   /* points per line in the passes: M = n b, or 2n when compact */
     int compact;         /* CONV_PLAN_COMPACT was set */
+    int elems;           /* complex elements per thread in the transform kernels (0: generic) */
+    int smem_twiddles;   /* twiddle table staged in shared memory */
+    int fused;           /* fused passes (global-memory first/last stages) */
 } conv_plan_info;
 
 conv_status conv_get_info(conv_plan_t plan, conv_plan_info *info);
@@ -259,9 +266,10 @@ typedef struct {
 } srv_stats;
 
 /* mem_budget_bytes: device bytes the server may hold; max_inflight: admitted requests at once;
- * conv_batch_max: convolutions per batched launch; ls_workers: concurrent LS solves. */
+ * conv_batch_max: convolutions per batched launch; ls_workers: concurrent LS solves;
+ * plan_flags: conv_plan_ex flags for every plan the server builds (CONV_PLAN_COMPACT, ...). */
 conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch_max, int ls_workers,
-                       srv_t *server);
+                       int plan_flags, srv_t *server);
 /* Non-blocking; returns a ticket.  CONV_EINVAL for malformed requests. */
 conv_status srv_submit(srv_t server, const srv_request *request, long long *ticket);
 /* Blocks until the request finished (timeout_s <= 0: no limit); CONV_ETIMEOUT if the limit

@@ -25,7 +25,8 @@ class ConvPlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("threads_rows", ctypes.c_int),
                 ("groups_rows", ctypes.c_int), ("threads_cols", ctypes.c_int),
                 ("groups_cols", ctypes.c_int), ("transform_len", ctypes.c_int),
-                ("compact", ctypes.c_int)]
+                ("compact", ctypes.c_int), ("elems", ctypes.c_int), ("smem_twiddles", ctypes.c_int),
+                ("fused", ctypes.c_int)]
 
 
 class LsOpts(ctypes.Structure):
@@ -90,7 +91,7 @@ PROTOTYPES = {
     "conv_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_longlong)]),
     "srv_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                  ctypes.POINTER(ctypes.c_void_p)]),
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "srv_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SrvRequest),
                                   ctypes.POINTER(ctypes.c_longlong)]),
     "srv_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,

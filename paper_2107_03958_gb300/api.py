@@ -31,7 +31,8 @@ class ConvPlan:
     """A plan for A_n on an n x n grid with period b (Sec. 2.1, eq. (An))."""
 
     def __init__(self, kernel="log", n=64, period=3, trunc_a=0.0, precision="fp64", io="r2r",
-                 batch_max=1, gamma=0.0, kappa=0.0, scale=1.0, device=None, compact=False):
+                 batch_max=1, gamma=0.0, kappa=0.0, scale=1.0, device=None, compact=False,
+                 autotune=False):
         self._lib = N.load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -43,7 +44,7 @@ class ConvPlan:
         h = ctypes.c_void_p()
         N.check(self._lib.conv_plan_ex(ctypes.byref(k), frac.numerator, frac.denominator, int(n),
                                        float(trunc_a), PRECISION[precision], IO[io], int(batch_max),
-                                       1 if compact else 0, ctypes.byref(h)))
+                                       (1 if compact else 0) | (2 if autotune else 0), ctypes.byref(h)))
         self._h = h
         self.info = self._info()
         self.M, self.a = self.info.M, self.info.a
@@ -179,11 +180,13 @@ class Server:
     submit_conv / submit_ls return tickets; wait(ticket) returns the result record.  The tensors of
     a request must stay alive until its wait returns (the server keeps references until then)."""
 
-    def __init__(self, mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4):
+    def __init__(self, mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4,
+                 compact=False):
         self._lib = N.load()
         h = ctypes.c_void_p()
         N.check(self._lib.srv_create(int(mem_budget_bytes), int(max_inflight), int(conv_batch_max),
-                                     int(ls_workers), ctypes.byref(h)))
+                                     int(ls_workers), 1 if compact else 0, ctypes.byref(h)))
+        self.compact = bool(compact)
         self._h = h
         self._keep = {}
 

@@ -122,19 +122,23 @@ __device__ __forceinline__ void fstage_edge(typename cvec<T>::t *buf, const FFTD
 // Whole transform, at least two stages.  All threads of the CTA call it.  If src is FromSmem the
 // buffer must hold the input; if dst writes global memory, the caller must meet a barrier before
 // the buffer is written again.
-template <typename T, int E, bool INV, bool TWS, class Src, class Dst>
+// ED encodes the first and last radix at compile time as 16 R_first + R_last (0: read both from
+// the descriptor).
+template <typename T, int E, int ED, bool INV, bool TWS, class Src, class Dst>
 __device__ __forceinline__ void fft_fused(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
                                           const typename cvec<T>::t *__restrict__ tw, int lt, int tpt,
                                           const Src &src, const Dst &dst)
 {
     const int nst = __ldg(&P->nst);
-    fstage_edge<T, E, INV, TWS>(buf, P, 0, tw, lt, tpt, src, ToSmem{});
+    if constexpr (ED == 0) fstage_edge<T, E, INV, TWS>(buf, P, 0, tw, lt, tpt, src, ToSmem{});
+    else fstage<T, E, ED / 16, INV, TWS>(buf, P, 0, tw, lt, tpt, src, ToSmem{});
     for (int s = 1; s < nst - 1; ++s) {
         int lt_ = lt;
         asm volatile("" : "+r"(lt_));
         fstage_mid<T, E, INV, TWS>(buf, P, s, tw, lt_, tpt);
     }
-    fstage_edge<T, E, INV, TWS>(buf, P, nst - 1, tw, lt, tpt, FromSmem{}, dst);
+    if constexpr (ED == 0) fstage_edge<T, E, INV, TWS>(buf, P, nst - 1, tw, lt, tpt, FromSmem{}, dst);
+    else fstage<T, E, ED % 16, INV, TWS>(buf, P, nst - 1, tw, lt, tpt, FromSmem{}, dst);
 }
 
 }  // namespace wsc

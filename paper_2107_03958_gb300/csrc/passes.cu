@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <array>
 #include <cstdlib>
 #include <string>
 #include <vector>
@@ -157,34 +158,68 @@ static int generic_tpt(const FFTDesc &P)
     return (need + 31) / 32 * 32;
 }
 
-// Fused-transform variants: (precision, E) with E in {24, 16} (FP32) or {12, 24, 8} (FP64).
-#define WSC_DISPATCH_FUSED(prec, E, tws, CALL)                                                             \
-    do {                                                                                                   \
-        if ((prec) == CONV_P_FP32) {                                                                       \
-            if ((E) == 16) {                                                                               \
-                if (tws) { typedef float T_; constexpr int E_ = 16; constexpr bool W_ = true; CALL; }      \
-                else { typedef float T_; constexpr int E_ = 16; constexpr bool W_ = false; CALL; }         \
-            } else {                                                                                       \
-                if (tws) { typedef float T_; constexpr int E_ = 24; constexpr bool W_ = true; CALL; }      \
-                else { typedef float T_; constexpr int E_ = 24; constexpr bool W_ = false; CALL; }         \
-            }                                                                                              \
-        } else if ((E) == 12) {                                                                            \
-            if (tws) { typedef double T_; constexpr int E_ = 12; constexpr bool W_ = true; CALL; }         \
-            else { typedef double T_; constexpr int E_ = 12; constexpr bool W_ = false; CALL; }            \
-        } else if ((E) == 8) {                                                                             \
-            if (tws) { typedef double T_; constexpr int E_ = 8; constexpr bool W_ = true; CALL; }          \
-            else { typedef double T_; constexpr int E_ = 8; constexpr bool W_ = false; CALL; }             \
-        } else {                                                                                           \
-            if (tws) { typedef double T_; constexpr int E_ = 24; constexpr bool W_ = true; CALL; }         \
-            else { typedef double T_; constexpr int E_ = 24; constexpr bool W_ = false; CALL; }            \
-        }                                                                                                  \
+// Fused-transform variants: (precision, E, ED = 16 R_first + R_last).
+#define WSC_DISPATCH_FUSED(prec, E, ED, tws, CALL) \
+    do { \
+        if ((prec) == CONV_P_FP32 && (E) == 24 && (ED) == 131) { \
+            if (tws) { typedef float T_; constexpr int E_ = 24, ED_ = 131; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 24, ED_ = 131; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 136) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 136; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 136; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 130) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 130; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 130; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 132) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 132; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 132; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP64 && (E) == 12 && (ED) == 67) { \
+            if (tws) { typedef double T_; constexpr int E_ = 12, ED_ = 67; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 12, ED_ = 67; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP64 && (E) == 24 && (ED) == 131) { \
+            if (tws) { typedef double T_; constexpr int E_ = 24, ED_ = 131; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 24, ED_ = 131; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP64 && (E) == 8 && (ED) == 136) { \
+            if (tws) { typedef double T_; constexpr int E_ = 8, ED_ = 136; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 8, ED_ = 136; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP64 && (E) == 8 && (ED) == 130) { \
+            if (tws) { typedef double T_; constexpr int E_ = 8, ED_ = 130; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 8, ED_ = 130; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP64 && (E) == 8 && (ED) == 132) { \
+            if (tws) { typedef double T_; constexpr int E_ = 8, ED_ = 132; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 8, ED_ = 132; constexpr bool W_ = false; CALL; } \
+        } \
     } while (0)
 
-static bool fused_eligible(conv_precision prec, int E, const FFTDesc &d)
+static const int kFusedSets[][3] = {
+    {1, 24, 131},
+    {1, 16, 136},
+    {1, 16, 130},
+    {1, 16, 132},
+    {0, 12, 67},
+    {0, 24, 131},
+    {0, 8, 136},
+    {0, 8, 130},
+    {0, 8, 132},
+};
+
+// Fused passes exist for these (precision, E, first radix, last radix); everything else runs the
+// plain passes.
+static int fused_edges(conv_precision prec, int E, const FFTDesc &d)
 {
-    if (d.nst < 2) return false;
-    if (prec == CONV_P_FP32) return E == 24 || E == 16;
-    return E == 12 || E == 24 || E == 8;
+    if (d.nst < 2) return 0;
+    const int ed = 16 * d.R[0] + d.R[d.nst - 1];
+    for (const auto &f : kFusedSets)
+        if ((f[0] == 1) == (prec == CONV_P_FP32) && f[1] == E && f[2] == ed) return ed;
+    return 0;
 }
 
 int generic_threads(const FFTDesc &P) { return generic_tpt(P); }
@@ -194,10 +229,10 @@ static conv_status set_all_attrs(int smem)
 {
     conv_status rc = CONV_OK;
     for (int tws = 0; tws < 2 && rc == CONV_OK; ++tws) {
-        for (int E : {24, 16})
-            if (rc == CONV_OK) WSC_DISPATCH_FUSED(CONV_P_FP32, E, tws, rc = (set_attrs_fused<T_, E_, W_>(smem)));
-        for (int E : {12, 24, 8})
-            if (rc == CONV_OK) WSC_DISPATCH_FUSED(CONV_P_FP64, E, tws, rc = (set_attrs_fused<T_, E_, W_>(smem)));
+        for (const auto &f : kFusedSets)
+            if (rc == CONV_OK)
+                WSC_DISPATCH_FUSED(f[0] == 1 ? CONV_P_FP32 : CONV_P_FP64, f[1], f[2], tws,
+                                   rc = (set_attrs_fused<T_, E_, ED_, W_>(smem)));
     }
     for (int prec = 0; prec < 2 && rc == CONV_OK; ++prec)
         for (int tws = 0; tws < 2 && rc == CONV_OK; ++tws)
@@ -211,10 +246,69 @@ static conv_status set_all_attrs(int smem)
     return rc;
 }
 
-conv_status select_transform(conv_plan_s *p)
+// One launch configuration: E elements per thread, twiddles in shared memory (tws_pref: 1 when
+// they fit, 0 never), fused passes (fused_pref: 1 when eligible, 0 never), G transforms per CTA
+// (force_g > 0 caps it).  Returns false if the configuration does not exist for this plan.
+static bool configure(conv_plan_s *p, int E, int tws_pref, int fused_pref, int force_g, int smem_optin, int sms)
 {
-    int dev = p->device;
-    int smem_optin = 0, sms = 0;
+    const int M = p->M;
+    const size_t esz = p->prec == CONV_P_FP64 ? 16 : 8;
+    const size_t per = (size_t)(p->prec == CONV_P_FP64 ? padded_len<double>(M) : padded_len<float>(M)) * esz;
+    FFTDesc d;
+    if (!factorize(M, E, d)) return false;
+    const int maxT = max_threads(p->prec, E);
+    int tpt;
+    if (E > 0) {
+        if (M % E) return false;
+        tpt = M / E;
+    } else {
+        tpt = generic_tpt(d);
+    }
+    if (tpt > maxT) return false;
+    const size_t twb = (size_t)d.tw_len * esz;
+    const bool tws = tws_pref != 0 && E > 0 && twb + per <= (size_t)smem_optin;
+    if (tws_pref == 1 && !tws && E > 0 && twb + per > (size_t)smem_optin) {
+        // asked for shared-memory twiddles that do not fit: fall back silently
+    }
+    const size_t avail = smem_optin - (tws ? twb : 0);
+    int G = std::max(1, maxT / tpt);
+    G = std::min<int>(G, (int)(avail / per));
+    G = std::min(G, 8);
+    if (G < 1) return false;
+    if (force_g > 0 && force_g <= G) G = force_g;
+    p->elems = E;
+    p->tws = tws;
+    p->fft = d;
+    p->rows.tpt = p->cols.tpt = tpt;
+    p->rows.groups = p->cols.groups = G;
+    p->rows.smem = p->cols.smem = (tws ? twb : 0) + per * G;
+    p->ed = fused_pref != 0 ? fused_edges(p->prec, E, d) : 0;
+    p->fused = p->ed != 0;
+    int bps = 1;
+    if (p->fused)
+        WSC_DISPATCH_FUSED(p->prec, E, p->ed, tws, bps = (blocks_per_sm_fused<T_, E_, ED_, W_>(tpt * G, p->rows.smem)));
+    else
+        WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, p->rows.smem)));
+    p->rows.max_ctas = p->cols.max_ctas = bps * sms;
+    // fused pass 3 reads twiddles from global memory: its own shape, without the table
+    p->inv = p->rows;
+    if (p->fused && tws) {
+        int Gi = std::max(1, maxT / tpt);
+        Gi = std::min<int>(Gi, (int)(smem_optin / per));
+        Gi = std::min(Gi, 8);
+        if (force_g > 0 && force_g <= Gi) Gi = force_g;
+        p->inv.groups = Gi;
+        p->inv.smem = per * Gi;
+        int bi = 1;
+        WSC_DISPATCH_FUSED(p->prec, E, p->ed, false, bi = (blocks_per_sm_fused<T_, E_, ED_, W_>(tpt * Gi, p->inv.smem)));
+        p->inv.max_ctas = bi * sms;
+    }
+    return true;
+}
+
+static conv_status device_limits(conv_plan_s *p, int &smem_optin, int &sms)
+{
+    const int dev = p->device;
     WSC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     WSC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     static bool attrs_set[64] = {false};
@@ -227,69 +321,61 @@ conv_status select_transform(conv_plan_s *p)
     const size_t esz = p->prec == CONV_P_FP64 ? 16 : 8;
     const size_t per = (size_t)(p->prec == CONV_P_FP64 ? padded_len<double>(M) : padded_len<float>(M)) * esz;
     if (per > (size_t)smem_optin)
-        return fail(CONV_EUNSUPPORTED, "transform length M=" + std::to_string(M) +
+        return fail(CONV_EUNSUPPORTED, "transform length " + std::to_string(M) +
                                            " exceeds one CTA's shared memory at this precision");
+    return CONV_OK;
+}
+
+// Default configuration: the first candidate E that exists, shared-memory twiddles and fused
+// passes whenever possible.  Environment overrides for experiments: WSCONV_ELEMS, WSCONV_GROUPS,
+// WSCONV_TWS (0/1), WSCONV_FUSED (0/1).
+conv_status select_transform(conv_plan_s *p)
+{
+    int smem_optin = 0, sms = 0;
+    conv_status rc = device_limits(p, smem_optin, sms);
+    if (rc != CONV_OK) return rc;
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
     const int ncand = p->prec == CONV_P_FP64 ? 4 : 3;
-    // optional overrides for tuning experiments: WSCONV_ELEMS, WSCONV_GROUPS, WSCONV_TWS (0/1)
     const char *env_e = getenv("WSCONV_ELEMS"), *env_g = getenv("WSCONV_GROUPS"), *env_t = getenv("WSCONV_TWS");
-    const int force_e = env_e ? atoi(env_e) : -1, force_g = env_g ? atoi(env_g) : 0;
-    const int force_t = env_t ? atoi(env_t) : -1;
     const char *env_f = getenv("WSCONV_FUSED");
-    const int force_f = env_f ? atoi(env_f) : -1;
+    const int force_e = env_e ? atoi(env_e) : -1, force_g = env_g ? atoi(env_g) : 0;
+    const int tws_pref = env_t ? atoi(env_t) : 1, fused_pref = env_f ? atoi(env_f) : 1;
     for (int i = 0; i < ncand; ++i) {
-        const int E = cand[i];
-        if (force_e >= 0 && E != force_e) continue;
-        FFTDesc d;
-        if (!factorize(M, E, d)) continue;
-        const int maxT = max_threads(p->prec, E);
-        int tpt;
-        if (E > 0) {
-            if (M % E) continue;
-            tpt = M / E;
-        } else {
-            tpt = generic_tpt(d);
-        }
-        if (tpt > maxT) continue;
-        // twiddles in shared memory when the table and at least one transform buffer fit
-        const size_t twb = (size_t)d.tw_len * esz;
-        bool tws = E > 0 && twb + per <= (size_t)smem_optin;
-        if (force_t == 0) tws = false;
-        const size_t avail = smem_optin - (tws ? twb : 0);
-        int G = std::max(1, maxT / tpt);
-        G = std::min<int>(G, (int)(avail / per));
-        G = std::min(G, 8);
-        if (force_g > 0 && force_g <= G) G = force_g;
-        p->elems = E;
-        p->tws = tws;
-        p->fft = d;
-        p->rows.tpt = p->cols.tpt = tpt;
-        p->rows.groups = p->cols.groups = G;
-        p->rows.smem = p->cols.smem = (tws ? twb : 0) + per * G;
-        p->fused = fused_eligible(p->prec, E, d) && force_f != 0;
-        int bps = 1;
-        if (p->fused)
-            WSC_DISPATCH_FUSED(p->prec, E, tws, bps = (blocks_per_sm_fused<T_, E_, W_>(tpt * G, p->rows.smem)));
-        else
-            WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, p->rows.smem)));
-        p->rows.max_ctas = p->cols.max_ctas = bps * sms;
-        // fused pass 3 reads twiddles from global memory: its own shape, without the table
-        p->inv = p->rows;
-        if (p->fused && tws) {
-            int Gi = std::max(1, maxT / tpt);
-            Gi = std::min<int>(Gi, (int)(smem_optin / per));
-            Gi = std::min(Gi, 8);
-            if (force_g > 0 && force_g <= Gi) Gi = force_g;
-            p->inv.groups = Gi;
-            p->inv.smem = per * Gi;
-            int bi = 1;
-            WSC_DISPATCH_FUSED(p->prec, E, false, bi = (blocks_per_sm_fused<T_, E_, W_>(tpt * Gi, p->inv.smem)));
-            p->inv.max_ctas = bi * sms;
-        }
-        return CONV_OK;
+        if (force_e >= 0 && cand[i] != force_e) continue;
+        if (configure(p, cand[i], tws_pref, fused_pref, force_g, smem_optin, sms)) return CONV_OK;
     }
-    return fail(CONV_EUNSUPPORTED, "M = " + std::to_string(M) +
+    return fail(CONV_EUNSUPPORTED, "transform length " + std::to_string(p->M) +
                                        " is not 2^a 3^b 5^c or needs more threads than one CTA has");
+}
+
+// All configurations the autotuner may time: (E, twiddles in shared memory, fused).
+std::vector<std::array<int, 3>> transform_candidates(conv_plan_s *p)
+{
+    std::vector<std::array<int, 3>> out;
+    int smem_optin = 0, sms = 0;
+    if (device_limits(p, smem_optin, sms) != CONV_OK) return out;
+    const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
+    const int ncand = p->prec == CONV_P_FP64 ? 4 : 3;
+    conv_plan_s probe = *p;
+    probe.tev_used.clear();
+    probe.tev_free.clear();
+    for (int i = 0; i < ncand; ++i)
+        for (int tws = 1; tws >= 0; --tws)
+            for (int fu = 1; fu >= 0; --fu) {
+                if (!configure(&probe, cand[i], tws, fu, 0, smem_optin, sms)) continue;
+                if ((int)probe.tws != tws || (int)probe.fused != fu) continue;  // not distinct
+                out.push_back({cand[i], tws, fu});
+            }
+    return out;
+}
+
+conv_status apply_candidate(conv_plan_s *p, const std::array<int, 3> &c)
+{
+    int smem_optin = 0, sms = 0;
+    conv_status rc = device_limits(p, smem_optin, sms);
+    if (rc != CONV_OK) return rc;
+    if (!configure(p, c[0], c[1], c[2], 0, smem_optin, sms)) return fail(CONV_EINVAL, "candidate does not apply");
+    return CONV_OK;
 }
 
 conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
@@ -297,8 +383,8 @@ conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, voi
 {
     conv_status rc = CONV_OK;
     if (p->fused)
-        WSC_DISPATCH_FUSED(p->prec, p->elems, p->tws,
-                           rc = (run_fused<T_, E_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
+        WSC_DISPATCH_FUSED(p->prec, p->elems, p->ed, p->tws,
+                           rc = (run_fused<T_, E_, ED_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
     else
         WSC_DISPATCH(p->prec, p->elems, p->tws,
                      rc = (run_pipeline<T_, E_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));

@@ -45,7 +45,7 @@ __device__ __forceinline__ void store_pair(typename cvec<T>::t *p, typename cvec
     if (has2) p[1] = B;
 }
 
-template <typename T, int E, bool TWS>
+template <typename T, int E, int ED, bool TWS>
 __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
@@ -70,7 +70,7 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
             }
             return cmk<V>(x, y);
         };
-        fft_fused<T, E, false, TWS>(buf, a.P, twp, lt, a.tpt, src, ToSmem{});
+        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, ToSmem{});
         if (valid) {
             V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * h * n;
             for (int k = lt; k < h; k += a.tpt) {
@@ -84,7 +84,7 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
     }
 }
 
-template <typename T, int E, bool TWS>
+template <typename T, int E, int ED, bool TWS>
 __global__ void WSC_LB(T, E) kf_r2r_cols(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
@@ -104,16 +104,16 @@ __global__ void WSC_LB(T, E) kf_r2r_cols(const PassArgs<T> a)
             const int k1 = o <= M / 2 ? o : M - o;
             x = cscale(x, __ldg(&gc[k1]));
         });
-        fft_fused<T, E, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul);
+        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul);
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_fused<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
 
-template <typename T, int E, bool TWS>
+template <typename T, int E, int ED, bool TWS>
 __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
@@ -151,13 +151,13 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
             oa[o] = ra;
             if (has2) oa[n + o] = rb;
         };
-        fft_fused<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
+        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
         __syncthreads();
     }
 }
 
 // ============================================================================ C2C
-template <typename T, int E, bool TWS, bool IN_REAL>
+template <typename T, int E, int ED, bool TWS, bool IN_REAL>
 __global__ void WSC_LB(T, E) kf_c2c_rows_fwd(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
@@ -182,12 +182,12 @@ __global__ void WSC_LB(T, E) kf_c2c_rows_fwd(const PassArgs<T> a)
         auto dst = [&](int o, V z) {
             if (valid) Wb[(size_t)o * n + j1] = z;
         };
-        fft_fused<T, E, false, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
+        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
         __syncthreads();
     }
 }
 
-template <typename T, int E, bool TWS, bool CG>
+template <typename T, int E, int ED, bool TWS, bool CG>
 __global__ void WSC_LB(T, E) kf_c2c_cols(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
@@ -207,16 +207,16 @@ __global__ void WSC_LB(T, E) kf_c2c_cols(const PassArgs<T> a)
             if (CG) x = cmul(x, __ldg(reinterpret_cast<const V *>(a.ghat) + (size_t)k2q * h + k1));
             else x = cscale(x, __ldg(reinterpret_cast<const T *>(a.ghat) + (size_t)k2q * h + k1));
         });
-        fft_fused<T, E, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul);
+        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul);
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_fused<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
 
-template <typename T, int E, bool TWS, bool IN_REAL>
+template <typename T, int E, int ED, bool TWS, bool IN_REAL>
 __global__ void WSC_LB(T, E) kf_c2c_rows_inv(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
@@ -245,32 +245,32 @@ __global__ void WSC_LB(T, E) kf_c2c_rows_inv(const PassArgs<T> a)
             }
             o_[o] = z;
         };
-        fft_fused<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
+        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
         __syncthreads();
     }
 }
 
 // ============================================================================ host glue
-template <typename T, int E, bool TWS> conv_status set_attrs_fused(int smem)
+template <typename T, int E, int ED, bool TWS> conv_status set_attrs_fused(int smem)
 {
 #define WSC_ATTR(k) WSC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))
-    WSC_ATTR((kf_r2r_rows_fwd<T, E, TWS>));
-    WSC_ATTR((kf_r2r_cols<T, E, TWS>));
-    WSC_ATTR((kf_r2r_rows_inv<T, E, TWS>));
-    WSC_ATTR((kf_c2c_rows_fwd<T, E, TWS, true>));
-    WSC_ATTR((kf_c2c_rows_fwd<T, E, TWS, false>));
-    WSC_ATTR((kf_c2c_cols<T, E, TWS, true>));
-    WSC_ATTR((kf_c2c_cols<T, E, TWS, false>));
-    WSC_ATTR((kf_c2c_rows_inv<T, E, TWS, true>));
-    WSC_ATTR((kf_c2c_rows_inv<T, E, TWS, false>));
+    WSC_ATTR((kf_r2r_rows_fwd<T, E, ED, TWS>));
+    WSC_ATTR((kf_r2r_cols<T, E, ED, TWS>));
+    WSC_ATTR((kf_r2r_rows_inv<T, E, ED, TWS>));
+    WSC_ATTR((kf_c2c_rows_fwd<T, E, ED, TWS, true>));
+    WSC_ATTR((kf_c2c_rows_fwd<T, E, ED, TWS, false>));
+    WSC_ATTR((kf_c2c_cols<T, E, ED, TWS, true>));
+    WSC_ATTR((kf_c2c_cols<T, E, ED, TWS, false>));
+    WSC_ATTR((kf_c2c_rows_inv<T, E, ED, TWS, true>));
+    WSC_ATTR((kf_c2c_rows_inv<T, E, ED, TWS, false>));
 #undef WSC_ATTR
     return CONV_OK;
 }
 
-template <typename T, int E, bool TWS> int blocks_per_sm_fused(int threads, size_t smem)
+template <typename T, int E, int ED, bool TWS> int blocks_per_sm_fused(int threads, size_t smem)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kf_r2r_cols<T, E, TWS>, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kf_r2r_cols<T, E, ED, TWS>, threads, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -278,7 +278,7 @@ template <typename T, int E, bool TWS> int blocks_per_sm_fused(int threads, size
     return nb > 0 ? nb : 1;
 }
 
-template <typename T, int E, bool TWS>
+template <typename T, int E, int ED, bool TWS>
 conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
                       double aim, double beta, void *ws, cudaStream_t st)
 {
@@ -310,17 +310,17 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.in = u;
         a.out = ws;
         a.units = batch * ((n + 1) / 2);
-        kf_r2r_rows_fwd<T, E, TWS><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+        kf_r2r_rows_fwd<T, E, ED, TWS><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[1], st);
         a.tpt = C.tpt;
         a.in = ws;
         a.units = batch * h;
-        kf_r2r_cols<T, E, TWS><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
+        kf_r2r_cols<T, E, ED, TWS><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[2], st);
         a.tpt = I.tpt;
         a.out = out;
         a.units = batch * ((n + 1) / 2);
-        kf_r2r_rows_inv<T, E, false><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
+        kf_r2r_rows_inv<T, E, ED, false><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
     } else {
         const bool in_real = p->io == CONV_IO_R2C;
         a.tpt = R.tpt;
@@ -328,25 +328,25 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.out = ws;
         a.units = batch * n;
         if (in_real)
-            kf_c2c_rows_fwd<T, E, TWS, true><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+            kf_c2c_rows_fwd<T, E, ED, TWS, true><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
         else
-            kf_c2c_rows_fwd<T, E, TWS, false><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+            kf_c2c_rows_fwd<T, E, ED, TWS, false><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[1], st);
         a.tpt = C.tpt;
         a.in = ws;
         a.units = batch * M;
         if (p->complex_ghat)
-            kf_c2c_cols<T, E, TWS, true><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
+            kf_c2c_cols<T, E, ED, TWS, true><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
         else
-            kf_c2c_cols<T, E, TWS, false><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
+            kf_c2c_cols<T, E, ED, TWS, false><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
         if (ev) cudaEventRecord(ev[2], st);
         a.tpt = I.tpt;
         a.out = out;
         a.units = batch * n;
         if (in_real)
-            kf_c2c_rows_inv<T, E, false, true><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
+            kf_c2c_rows_inv<T, E, ED, false, true><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
         else
-            kf_c2c_rows_inv<T, E, false, false><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
+            kf_c2c_rows_inv<T, E, ED, false, false><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
     }
     if (ev) cudaEventRecord(ev[3], st);
     WSC_CUDA(cudaGetLastError());

@@ -1,6 +1,9 @@
 // plan.cu -- conv_plan / conv_apply and the rest of the C ABI's host side (Sec. 2.1, eq. (io), (An)).
+#include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -51,6 +54,90 @@ static conv_status upload_twiddles(conv_plan_s *p)
         WSC_CUDA(cudaStreamSynchronize(p->setup_stream));
     }
     return CONV_OK;
+}
+
+std::vector<std::array<int, 3>> transform_candidates(conv_plan_s *p);
+conv_status apply_candidate(conv_plan_s *p, const std::array<int, 3> &c);
+
+// Re-upload the stage table and twiddles after the launch configuration changed.
+static conv_status reupload(conv_plan_s *p)
+{
+    if (p->tw) cudaFree(p->tw);
+    p->tw = nullptr;
+    conv_status rc = upload_twiddles(p);
+    if (rc != CONV_OK) return rc;
+    WSC_CUDA(cudaMemcpyAsync(p->fft_dev, &p->fft, sizeof(FFTDesc), cudaMemcpyHostToDevice, p->setup_stream));
+    WSC_CUDA(cudaStreamSynchronize(p->setup_stream));
+    return CONV_OK;
+}
+
+// Autotuner: time every launch configuration (per-thread count, shared-memory twiddles, fused
+// passes) on zero densities at the plan's batch size and keep the fastest.  Choices are cached per
+// (transform length, n, precision, io, batch, compact) for the process.
+static conv_status autotune(conv_plan_s *p)
+{
+    static std::mutex mu;
+    static std::map<std::array<int, 6>, std::array<int, 3>> cache;
+    const std::array<int, 6> key = {p->M, p->n, (int)p->prec, (int)p->io, p->batch_max, p->compact ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            conv_status rc = apply_candidate(p, it->second);
+            return rc == CONV_OK ? reupload(p) : rc;
+        }
+    }
+    auto cands = transform_candidates(p);
+    if (cands.size() <= 1) return CONV_OK;
+    const int B = p->batch_max;
+    const size_t rsz = p->prec == CONV_P_FP64 ? 8 : 4;
+    const size_t in_b = (size_t)B * p->n * p->n * rsz * (p->io == CONV_IO_C2C ? 2 : 1);
+    const size_t out_b = (size_t)B * p->n * p->n * rsz * (p->io == CONV_IO_R2R ? 1 : 2);
+    void *u = nullptr, *out = nullptr;
+    if (cudaMalloc(&u, in_b) != cudaSuccess || cudaMalloc(&out, out_b) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(u);
+        return fail(CONV_ENOMEM, "autotuner buffers");
+    }
+    cudaMemsetAsync(u, 0, in_b, p->setup_stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::array<int, 3> pick = cands[0];
+    conv_status rc = CONV_OK;
+    for (const auto &c : cands) {
+        rc = apply_candidate(p, c);
+        if (rc == CONV_OK) rc = reupload(p);
+        if (rc != CONV_OK) break;
+        for (int w = 0; w < 2; ++w) launch_pipeline(p, u, nullptr, out, B, 1.0, 0.0, 0.0, p->ws, p->setup_stream);
+        cudaEventRecord(e0, p->setup_stream);
+        for (int r = 0; r < 3; ++r) launch_pipeline(p, u, nullptr, out, B, 1.0, 0.0, 0.0, p->ws, p->setup_stream);
+        cudaEventRecord(e1, p->setup_stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotuner run");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(u);
+    cudaFree(out);
+    if (rc != CONV_OK) return rc;
+    rc = apply_candidate(p, pick);
+    if (rc == CONV_OK) rc = reupload(p);
+    if (rc == CONV_OK) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = pick;
+    }
+    return rc;
 }
 
 cudaEvent_t *timing_slot(conv_plan_s *p)
@@ -146,7 +233,7 @@ conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_d
             return fail(CONV_EINVAL, "period b < 1 + sqrt 2 admits no default truncation radius; pass trunc_a");
         a = 0.5 * (std::sqrt(2.0) + b - 1.0);
     }
-    if (flags & ~CONV_PLAN_COMPACT) return fail(CONV_EINVAL, "unknown plan flags");
+    if (flags & ~(CONV_PLAN_COMPACT | CONV_PLAN_AUTOTUNE)) return fail(CONV_EINVAL, "unknown plan flags");
     conv_plan_s *p = new conv_plan_s();
     p->kern = *kernel;
     p->pnum = period_num;
@@ -201,6 +288,7 @@ conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_d
         cudaError_t e = cudaStreamSynchronize(p->setup_stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "plan setup");
     }
+    if (rc == CONV_OK && (flags & CONV_PLAN_AUTOTUNE)) rc = autotune(p);
     if (rc != CONV_OK) {
         conv_destroy(p);
         return rc;
@@ -252,6 +340,9 @@ conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
     info->M = p->Mb;
     info->transform_len = p->M;
     info->compact = p->compact ? 1 : 0;
+    info->elems = p->elems;
+    info->smem_twiddles = p->tws ? 1 : 0;
+    info->fused = p->fused ? 1 : 0;
     info->period_num = p->pnum;
     info->period_den = p->pden;
     info->b = p->b;

@@ -72,7 +72,7 @@ struct Batch {
 
 struct srv_s {
     size_t budget = 0, in_use = 0;
-    int max_inflight = 64, batch_max = 16, ls_workers = 4;
+    int max_inflight = 64, batch_max = 16, ls_workers = 4, plan_flags = 0;
     std::mutex mu;
     std::condition_variable cv_dispatch, cv_done, cv_ls;
     std::deque<std::shared_ptr<wsc::Req>> pending;
@@ -110,12 +110,15 @@ static PlanKey key_of(const srv_request &r)
 
 // Device bytes of a plan (moment table, twiddles, workspace) plus, for conv plans, the staging
 // buffers of one batch; estimated from the sizes before the plan exists.
-static size_t plan_bytes_estimate(const srv_request &r, int batch_max)
+static size_t plan_bytes_estimate(const srv_request &r, int batch_max, int flags)
 {
-    const long long n = r.n, M = n * r.period_num / r.period_den, h = M / 2 + 1;
+    const long long n = r.n, Mb = n * r.period_num / r.period_den;
+    const long long M = (flags & CONV_PLAN_COMPACT) ? 2 * n : Mb, h = M / 2 + 1;
     const size_t cz = 2 * elem_bytes_of(r.precision);
     const bool c2c = r.kind == SRV_LS || r.io != CONV_IO_R2R;
-    size_t ghat = (size_t)h * h * 8 * (r.kernel.family == CONV_K_HELMHOLTZ ? 2 : 1);
+    const long long hb = Mb / 2 + 1;
+    size_t ghat = (size_t)hb * hb * 8 * (r.kernel.family == CONV_K_HELMHOLTZ ? 2 : 1);
+    if (flags & CONV_PLAN_COMPACT) ghat += (size_t)h * h * 8 * (r.kernel.family == CONV_K_HELMHOLTZ ? 2 : 1);
     if (r.precision == CONV_P_FP32) ghat += ghat / 2;
     const int B = r.kind == SRV_LS ? 1 : batch_max;
     size_t ws = (size_t)(c2c ? M : h) * n * cz * B;
@@ -183,8 +186,8 @@ static std::shared_ptr<CachedPlan> get_plan(srv_t s, const srv_request &r, int &
     if (it != s->plans.end()) return it->second;
     auto cp = std::make_shared<CachedPlan>();
     const conv_io io = r.kind == SRV_LS ? CONV_IO_C2C : (conv_io)r.io;
-    status = conv_plan(&r.kernel, r.period_num, r.period_den, r.n, 0.0, (conv_precision)r.precision, io,
-                       r.kind == SRV_LS ? 1 : s->batch_max, &cp->plan);
+    status = conv_plan_ex(&r.kernel, r.period_num, r.period_den, r.n, 0.0, (conv_precision)r.precision, io,
+                          r.kind == SRV_LS ? 1 : s->batch_max, s->plan_flags, &cp->plan);
     if (status != CONV_OK) return nullptr;
     cudaStreamCreateWithFlags(&cp->stream, cudaStreamNonBlocking);
     conv_plan_info inf;
@@ -261,7 +264,7 @@ static void dispatcher_loop(srv_t s)
             if (s->inflight_reqs >= s->max_inflight) break;
             PlanKey k = key_of(q->r);
             const bool have = s->plans.count(k) != 0;
-            const size_t need = request_bytes(q->r) + (have ? 0 : plan_bytes_estimate(q->r, s->batch_max));
+            const size_t need = request_bytes(q->r) + (have ? 0 : plan_bytes_estimate(q->r, s->batch_max, s->plan_flags));
             if (need > s->budget) {  // can never fit
                 it = s->pending.erase(it);
                 s->inflight_reqs++;
@@ -388,11 +391,14 @@ using namespace wsc;
 
 extern "C" {
 
-conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch_max, int ls_workers, srv_t *out)
+conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch_max, int ls_workers,
+                       int plan_flags, srv_t *out)
 {
     if (!out || mem_budget_bytes == 0 || max_inflight < 1 || conv_batch_max < 1 || ls_workers < 1)
         return fail(CONV_EINVAL, "bad serving parameters");
+    if (plan_flags & ~(CONV_PLAN_COMPACT | CONV_PLAN_AUTOTUNE)) return fail(CONV_EINVAL, "unknown plan flags");
     srv_s *s = new srv_s();
+    s->plan_flags = plan_flags;
     s->budget = mem_budget_bytes;
     s->max_inflight = max_inflight;
     s->batch_max = conv_batch_max;

@@ -33,11 +33,11 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
                          double are, double aim, double beta, void *ws, cudaStream_t st);
 template <typename T, int E, bool TWS> conv_status set_attrs(int smem);
 template <typename T, int E, bool TWS> int blocks_per_sm(int threads, size_t smem);
-template <typename T, int E, bool TWS>
+template <typename T, int E, int ED, bool TWS>
 conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
                       double aim, double beta, void *ws, cudaStream_t st);
-template <typename T, int E, bool TWS> conv_status set_attrs_fused(int smem);
-template <typename T, int E, bool TWS> int blocks_per_sm_fused(int threads, size_t smem);
+template <typename T, int E, int ED, bool TWS> conv_status set_attrs_fused(int smem);
+template <typename T, int E, int ED, bool TWS> int blocks_per_sm_fused(int threads, size_t smem);
 
 // Launch shape of one pass family (rows or columns).
 struct LaunchShape {
@@ -65,6 +65,7 @@ struct conv_plan_s {
     int elems;  // complex elements per thread in the transform kernels
     bool tws;   // twiddle table staged in shared memory
     bool fused; // passes on the fused transform (global-memory first/last stages)
+    int ed = 0; // fused: 16 * first radix + last radix
     wsc::FFTDesc fft;
     wsc::FFTDesc *fft_dev = nullptr;  // device copy read by the pass kernels
     // FP64 moment quadrant [k2][k1], k1, k2 <= Mb/2: real or complex (ghat_bytes)

@@ -13,14 +13,15 @@ from paper_2107_03958_gb300.api import ConvPlan, Server, ls_solve
 pytestmark = pytest.mark.gpu
 
 
-def _conv_alone(n, kernel, kw, precision, io, u):
-    plan = ConvPlan(kernel, n=n, period=3, precision=precision, io=io, batch_max=1, **kw)
+def _conv_alone(n, kernel, kw, precision, io, u, compact):
+    plan = ConvPlan(kernel, n=n, period=3, precision=precision, io=io, batch_max=1, compact=compact, **kw)
     return plan.apply(u)
 
 
-def test_mixed_requests_equal_their_results_alone():
+@pytest.mark.parametrize("compact", [False, True])
+def test_mixed_requests_equal_their_results_alone(compact):
     rng = np.random.default_rng(7)
-    srv = Server(mem_budget_bytes=8 << 30, max_inflight=32, conv_batch_max=8, ls_workers=2)
+    srv = Server(mem_budget_bytes=8 << 30, max_inflight=32, conv_batch_max=8, ls_workers=2, compact=compact)
     reqs = []
     kinds = [("log", {"scale": 1.0}), ("pow", {"gamma": -1.0}), ("helmholtz", {"kappa": 20.0})]
     for i in range(24):
@@ -63,13 +64,13 @@ def test_mixed_requests_equal_their_results_alone():
     for r, res in zip(reqs, results):
         if r[0] == "ls":
             _, n, kappa, prec, (m, f, x) = r
-            plan = ConvPlan("helmholtz", n=n, period=3, precision=prec, io="c2c", kappa=kappa)
+            plan = ConvPlan("helmholtz", n=n, period=3, precision=prec, io="c2c", kappa=kappa, compact=compact)
             xa, info = ls_solve(plan, m, f, refine=(prec == "fp32"))
             assert res["rel_residual"] <= 1.05e-10
             assert torch.equal(xa, x), (n, kappa, prec)
         else:
             _, n, (kernel, kw, io), prec, (u, out) = r
-            alone = _conv_alone(n, kernel, kw, prec, io, u)
+            alone = _conv_alone(n, kernel, kw, prec, io, u, compact)
             assert torch.equal(alone, out), (n, kernel, prec, res["batched_with"])
 
 
