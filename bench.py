@@ -341,12 +341,14 @@ def profile_case(args):
     from paper_2107_03958_gb300 import inputs
     from paper_2107_03958_gb300.api import ConvPlan
     prec = "fp64" if args.only == "r2r64" else "fp32"
+    compact = os.environ.get("BENCH_PERIOD_B", "0") != "1"
     if args.only == "c2c":
         plan = ConvPlan("helmholtz", n=args.n, period=3, precision=prec, io="c2c",
-                        batch_max=args.batch, kappa=20.0)
+                        batch_max=args.batch, kappa=20.0, compact=compact)
         u = torch.tensor(inputs.bump_sums(args.n, args.batch), dtype=plan.cplx_dtype, device="cuda")
     else:
-        plan = ConvPlan("log", n=args.n, period=3, precision=prec, io="r2r", batch_max=args.batch)
+        plan = ConvPlan("log", n=args.n, period=3, precision=prec, io="r2r", batch_max=args.batch,
+                        compact=compact)
         u = torch.tensor(inputs.bump_sums(args.n, args.batch), dtype=plan.real_dtype, device="cuda")
     out = torch.empty(u.shape, dtype=plan.out_dtype(), device="cuda")
     for _ in range(args.warmup + args.steps):
