@@ -107,7 +107,9 @@ conv_status conv_workspace_size(conv_plan_t plan, int batch, size_t *bytes);
  *   mask: NULL or an n x n real array (plan precision) shared by the batch; it multiplies u at the
  *         load (the Fourier-smoothed indicator chi^n psi of Sec. 2.4, or a contrast).
  *   out:  batch x n x n, real (R2R) or complex (R2C, C2C); must not alias u.
- *   workspace: NULL (use the plan's, valid for batch <= batch_max) or conv_workspace_size bytes.
+ *   workspace: NULL (use the plan's, valid for batch <= batch_max) or conv_workspace_size bytes,
+ *              16-byte aligned.
+ * u, out and mask must be aligned to their element type (CONV_EINVAL otherwise).
  * Asynchronous on `stream`.  Three kernel launches. */
 conv_status conv_apply(conv_plan_t plan, const void *u, const void *mask, void *out, int batch,
                        void *workspace, void *stream);
@@ -214,6 +216,15 @@ conv_status ls_solve(conv_plan_t plan, const double *m, const void *f, void *x, 
  * synchronises `stream` (geometry-time operation). */
 conv_status conv_fs_mask(conv_plan_t plan, int shape, const double *geom, double delta, void *mask,
                          void *stream);
+
+/* Device status of the plan's pass kernels (no counterpart in the paper).  The fused passes fetch
+ * their next work item into shared memory with asynchronous copies while transforming the current
+ * one; every wait for such a copy is bounded (one second of wall time).  A wait that gives up
+ * makes its kernel record CONV_ETIMEOUT in the plan's device status word and leave without
+ * finishing, so the applies since then are incomplete.  conv_device_status synchronises `stream`,
+ * reads and clears that word (and the FP64 twin's of a mixed-precision LS plan) and returns it:
+ * CONV_OK, or CONV_ETIMEOUT.  ls_solve and the serving layer call it for their own work. */
+conv_status conv_device_status(conv_plan_t plan, void *stream);
 
 /* Per-pass device timing (benchmark instrumentation; no counterpart in the paper).  While enabled,
  * every apply on this plan records CUDA events around its three kernel launches on the apply's

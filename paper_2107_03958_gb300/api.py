@@ -130,6 +130,11 @@ class ConvPlan:
                                        ctypes.c_void_p(mask.data_ptr()), _stream_ptr(stream)))
         return mask
 
+    def device_status(self, stream=None):
+        """Synchronise `stream` and raise if a pass kernel's bounded wait for an asynchronous copy
+        gave up since the last check (the applies since then are incomplete)."""
+        N.check(self._lib.conv_device_status(self._h, _stream_ptr(stream)))
+
     def timing(self, enable):
         """Record per-pass CUDA events on every apply (benchmark instrumentation)."""
         N.check(self._lib.conv_timing_enable(self._h, int(bool(enable))))

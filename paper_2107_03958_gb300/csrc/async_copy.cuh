@@ -1,0 +1,93 @@
+// async_copy.cuh -- asynchronous global -> shared copies that let a persistent pass kernel fetch
+// its next work item while it transforms the current one.
+//
+//   bulk copies (TMA, cp.async.bulk): one thread moves a contiguous, 16-byte aligned run whose
+//     size is a multiple of 16 bytes; completion is counted in bytes on an mbarrier;
+//   cp.async: every thread moves 16-byte pieces of a strided gather; completion is per thread
+//     (cp.async.wait_all), made visible to the CTA by the next barrier.
+//
+// Every mbarrier wait is bounded in wall time (WSC_WAIT_NS, read from %globaltimer).  A wait that
+// gives up returns false; the caller records CONV_ETIMEOUT in the plan's device status word and
+// leaves the kernel after draining its own copies (again with a bound).
+#pragma once
+#include <cstdint>
+
+namespace wsc {
+
+#define WSC_WAIT_NS 1000000000ull  // one second
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// mbarrier with one expected arrival per phase (the issuing thread's arrive.expect_tx)
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete; false after WSC_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(bar, parity))
+        if (global_ns() - t0 > WSC_WAIT_NS) return false;
+    return true;
+}
+
+// Orders this thread's (and, after a CTA barrier, every thread's) generic-proxy accesses to shared
+// memory before later async-proxy writes (bulk copies) to it.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Contiguous global -> shared copy of `bytes` (multiple of 16; both addresses 16-byte aligned),
+// completing `bytes` transactions on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 16-byte global -> shared copy (both addresses 16-byte aligned), cached in L2 only.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// 8-byte global -> shared copy (both addresses 8-byte aligned).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+}  // namespace wsc

@@ -119,19 +119,26 @@ __device__ __forceinline__ void fstage_edge(typename cvec<T>::t *buf, const FFTD
     }
 }
 
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // Whole transform, at least two stages.  All threads of the CTA call it.  If src is FromSmem the
 // buffer must hold the input; if dst writes global memory, the caller must meet a barrier before
-// the buffer is written again.
+// the buffer is written again.  after0() runs on every thread once stage 0 has read all of its
+// inputs and the CTA has met the barrier that ends the stage (the moment a prefetch may overwrite
+// what src read).
 // ED encodes the first and last radix at compile time as 16 R_first + R_last (0: read both from
 // the descriptor).
-template <typename T, int E, int ED, bool INV, bool TWS, class Src, class Dst>
+template <typename T, int E, int ED, bool INV, bool TWS, class Src, class Dst, class After0 = NoHook>
 __device__ __forceinline__ void fft_fused(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
                                           const typename cvec<T>::t *__restrict__ tw, int lt, int tpt,
-                                          const Src &src, const Dst &dst)
+                                          const Src &src, const Dst &dst, const After0 &after0 = After0{})
 {
     const int nst = __ldg(&P->nst);
     if constexpr (ED == 0) fstage_edge<T, E, INV, TWS>(buf, P, 0, tw, lt, tpt, src, ToSmem{});
     else fstage<T, E, ED / 16, INV, TWS>(buf, P, 0, tw, lt, tpt, src, ToSmem{});
+    after0();
     for (int s = 1; s < nst - 1; ++s) {
         int lt_ = lt;
         asm volatile("" : "+r"(lt_));

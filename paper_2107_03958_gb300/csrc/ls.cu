@@ -489,5 +489,7 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
         info->rel_residual = res / fn;
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "ls_solve");
-    return rc;
+    // a pass kernel that gave up on a bounded wait leaves the solve's matvecs incomplete
+    const conv_status ds = conv_device_status(p, stream);
+    return ds != CONV_OK ? ds : rc;
 }

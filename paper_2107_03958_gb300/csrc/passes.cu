@@ -85,6 +85,10 @@ static int max_threads(conv_precision prec, int E)
         }                                                                                     \
     } while (0)
 
+// Twiddle powers a radix-R butterfly reads from its stage's table: w^k (R = 2); w^k, w^2k (R = 3,
+// 4; w^3k is their product); w^k, w^2k, w^4k (R = 5, 8; the other powers are products).
+static inline int tw_blocks(int R) { return R == 2 ? 1 : (R <= 4 ? 2 : 3); }
+
 // Radix sequence for L = 2^p 3^q 5^r whose radices divide E (E = 0: any of 8, 4, 2, 3, 5):
 // power-of-two radices first (8s when allowed, else 4s), then 3s, then 5s.
 static bool factorize(int L, int E, FFTDesc &d)
@@ -121,7 +125,7 @@ static bool factorize(int L, int E, FFTDesc &d)
         d.Ns[s] = (int)Ns;
         d.tws[s] = (int)(L / (Ns * R[s]));
         d.toff[s] = off;
-        off += 3 * (int)Ns;
+        off += tw_blocks(R[s]) * (int)Ns;
         d.mag[s] = ((1ULL << 40) + (unsigned long long)Ns - 1) / (unsigned long long)Ns;
         Ns *= R[s];
     }
@@ -129,14 +133,15 @@ static bool factorize(int L, int E, FFTDesc &d)
     return true;
 }
 
-// Per-stage twiddle blocks [w^k | w^{2k} | w^{4k}], w = exp(-2 pi i / (Ns R)), in long double.
+// Per-stage twiddle blocks [w^k | w^{2k} | w^{4k}] (the first tw_blocks(R) of them),
+// w = exp(-2 pi i / (Ns R)), in long double.
 void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im)
 {
     const long double PI_L = 3.141592653589793238462643383279502884L;
     re_im.assign(2 * (size_t)d.tw_len, 0.0);
     for (int s = 0; s < d.nst; ++s) {
         const long long Ns = d.Ns[s], NR = Ns * d.R[s];
-        for (int m = 0; m < 3; ++m)
+        for (int m = 0; m < tw_blocks(d.R[s]); ++m)
             for (long long k = 0; k < Ns; ++k) {
                 const long long e = ((1LL << m) * k) % NR;
                 const long double ang = 2.0L * PI_L * (long double)e / (long double)NR;
@@ -246,12 +251,31 @@ static conv_status set_all_attrs(int smem)
     return rc;
 }
 
-// One launch configuration: E elements per thread, twiddles in shared memory (tws_pref: 1 when
-// they fit, 0 never), fused passes (fused_pref: 1 when eligible, 0 never), G transforms per CTA
-// (force_g > 0 caps it).  Returns false if the configuration does not exist for this plan.
-static bool configure(conv_plan_s *p, int E, int tws_pref, int fused_pref, int force_g, int smem_optin, int sms)
+static size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Shared memory of a pass CTA with G groups: [twiddles][G transform buffers][G staging areas]
+// [G mbarriers], in the order stage_area() walks it on the device.
+static size_t pass_smem(size_t twb, size_t per, size_t stage_bytes, int G)
 {
-    const int M = p->M;
+    return round16(twb + per * G) + (round16(stage_bytes) + (stage_bytes ? 8 : 0)) * G;
+}
+
+// Most groups (<= 8, <= maxT / tpt) whose CTA fits `smem_optin`; 0 if not even one does.
+static int max_groups(int maxT, int tpt, size_t twb, size_t per, size_t stage_bytes, int smem_optin)
+{
+    int G = std::min(8, std::max(1, maxT / tpt));
+    while (G > 0 && pass_smem(twb, per, stage_bytes, G) > (size_t)smem_optin) --G;
+    return G;
+}
+
+// One launch configuration c = {E elements per thread, fused passes (1 when eligible, 0 never),
+// options of pass 1, 2, 3 (CFG_* bits: shared-memory twiddles when they fit, prefetch when it
+// fits (fused only), one transform per CTA)}.  An option that does not fit is dropped (twiddles
+// first, then prefetch).  Returns false if the configuration does not exist for this plan.
+static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sms)
+{
+    const int E = c[0], fused_pref = c[1];
+    const int M = p->M, n = p->n;
     const size_t esz = p->prec == CONV_P_FP64 ? 16 : 8;
     const size_t per = (size_t)(p->prec == CONV_P_FP64 ? padded_len<double>(M) : padded_len<float>(M)) * esz;
     FFTDesc d;
@@ -265,45 +289,73 @@ static bool configure(conv_plan_s *p, int E, int tws_pref, int fused_pref, int f
         tpt = generic_tpt(d);
     }
     if (tpt > maxT) return false;
+    const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d) : 0;
+    const bool fused = ed != 0;
     const size_t twb = (size_t)d.tw_len * esz;
-    const bool tws = tws_pref != 0 && E > 0 && twb + per <= (size_t)smem_optin;
-    if (tws_pref == 1 && !tws && E > 0 && twb + per > (size_t)smem_optin) {
-        // asked for shared-memory twiddles that do not fit: fall back silently
+    // staging: a row pair / row / column (n elements V) for passes 1 and 2; a row's spectrum for
+    // pass 3 (R2R: both spectra of a row pair for k <= M/2; C2C: all M values)
+    const size_t sb12 = (size_t)n * esz;
+    const size_t sb3 = (p->io == CONV_IO_R2R ? 2 * (size_t)p->h : (size_t)M) * esz;
+    auto shape = [&](int cfg, size_t stage_bytes, int nbuf, LaunchShape &S) -> bool {
+        const size_t pb = per * nbuf;
+        bool tws = (cfg & CFG_TWS) && E > 0;
+        size_t sb = fused && (cfg & CFG_PF) ? stage_bytes : 0;
+        int G = max_groups(maxT, tpt, tws ? twb : 0, pb, sb, smem_optin);
+        if (G < 1 && tws) {
+            tws = false;
+            G = max_groups(maxT, tpt, 0, pb, sb, smem_optin);
+        }
+        if (G < 1 && sb) {
+            sb = 0;
+            G = max_groups(maxT, tpt, 0, pb, 0, smem_optin);
+        }
+        if (G < 1) return false;
+        if (cfg & CFG_ONE) G = 1;
+        S.tpt = tpt;
+        S.groups = G;
+        S.tws = tws;
+        S.stage = (int)(sb / esz);
+        S.smem = pass_smem(tws ? twb : 0, pb, sb, G);
+        int bps = 1;
+        if (fused)
+            WSC_DISPATCH_FUSED(p->prec, E, ed, tws, bps = (blocks_per_sm_fused<T_, E_, ED_, W_>(tpt * G, S.smem)));
+        else
+            WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, S.smem)));
+        S.max_ctas = bps * sms;
+        return true;
+    };
+    LaunchShape R, C, I;
+    if (!shape(c[2], sb12, 1, R)) return false;
+    // R2C with complex ghat runs the split pipeline when its pass 2 fits two buffers per CTA;
+    // otherwise the C2C layout
+    bool split = false;
+    if (fused) {
+        split = p->io == CONV_IO_R2C && p->complex_ghat && shape(c[3], sb12, 2, C);
+        const size_t sbi = split ? 2 * (size_t)p->h * esz : sb3;
+        if ((!split && !shape(c[3], sb12, 1, C)) || !shape(c[4], sbi, 1, I)) return false;
+    } else {
+        C = I = R;  // the plain kernels share one twiddle option and shape
     }
-    const size_t avail = smem_optin - (tws ? twb : 0);
-    int G = std::max(1, maxT / tpt);
-    G = std::min<int>(G, (int)(avail / per));
-    G = std::min(G, 8);
-    if (G < 1) return false;
-    if (force_g > 0 && force_g <= G) G = force_g;
+    p->r2c_split = split;
     p->elems = E;
-    p->tws = tws;
+    p->tws = R.tws;
     p->fft = d;
-    p->rows.tpt = p->cols.tpt = tpt;
-    p->rows.groups = p->cols.groups = G;
-    p->rows.smem = p->cols.smem = (tws ? twb : 0) + per * G;
-    p->ed = fused_pref != 0 ? fused_edges(p->prec, E, d) : 0;
-    p->fused = p->ed != 0;
-    int bps = 1;
-    if (p->fused)
-        WSC_DISPATCH_FUSED(p->prec, E, p->ed, tws, bps = (blocks_per_sm_fused<T_, E_, ED_, W_>(tpt * G, p->rows.smem)));
-    else
-        WSC_DISPATCH(p->prec, E, tws, bps = (blocks_per_sm<T_, E_, W_>(tpt * G, p->rows.smem)));
-    p->rows.max_ctas = p->cols.max_ctas = bps * sms;
-    // fused pass 3 reads twiddles from global memory: its own shape, without the table
-    p->inv = p->rows;
-    if (p->fused && tws) {
-        int Gi = std::max(1, maxT / tpt);
-        Gi = std::min<int>(Gi, (int)(smem_optin / per));
-        Gi = std::min(Gi, 8);
-        if (force_g > 0 && force_g <= Gi) Gi = force_g;
-        p->inv.groups = Gi;
-        p->inv.smem = per * Gi;
-        int bi = 1;
-        WSC_DISPATCH_FUSED(p->prec, E, p->ed, false, bi = (blocks_per_sm_fused<T_, E_, ED_, W_>(tpt * Gi, p->inv.smem)));
-        p->inv.max_ctas = bi * sms;
-    }
+    p->ed = ed;
+    p->fused = fused;
+    p->rows = R;
+    p->cols = C;
+    p->inv = I;
     return true;
+}
+
+// Default options per pass, from FP32 measurements at n = 4096, batch 16: prefetch pays in the
+// row passes of the R2R and split R2C pipelines (contiguous row loads, strided spectrum gathers)
+// and not in their column passes or in the C2C passes, where it costs a transform per CTA.
+static Candidate default_candidate(const conv_plan_s *p, int E)
+{
+    if (p->io == CONV_IO_R2R || (p->io == CONV_IO_R2C && p->complex_ghat))
+        return {E, 1, CFG_TWS | CFG_PF, CFG_TWS, CFG_TWS | CFG_PF};
+    return {E, 1, CFG_TWS, CFG_TWS, 0};
 }
 
 static conv_status device_limits(conv_plan_s *p, int &smem_optin, int &sms)
@@ -326,9 +378,10 @@ static conv_status device_limits(conv_plan_s *p, int &smem_optin, int &sms)
     return CONV_OK;
 }
 
-// Default configuration: the first candidate E that exists, shared-memory twiddles and fused
-// passes whenever possible.  Environment overrides for experiments: WSCONV_ELEMS, WSCONV_GROUPS,
-// WSCONV_TWS (0/1), WSCONV_FUSED (0/1).
+// Default configuration: the first candidate E that exists, fused passes and the default options
+// of each pass.  Environment overrides for experiments: WSCONV_ELEMS, WSCONV_FUSED (0/1),
+// WSCONV_TWS (0: no pass keeps its table in shared memory), WSCONV_PF (0/1: prefetch in no / every
+// pass), WSCONV_GROUPS (1: one transform per CTA), WSCONV_CFG ("r,c,i": the CFG_* bits per pass).
 conv_status select_transform(conv_plan_s *p)
 {
     int smem_optin = 0, sms = 0;
@@ -336,22 +389,38 @@ conv_status select_transform(conv_plan_s *p)
     if (rc != CONV_OK) return rc;
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
     const int ncand = p->prec == CONV_P_FP64 ? 4 : 3;
-    const char *env_e = getenv("WSCONV_ELEMS"), *env_g = getenv("WSCONV_GROUPS"), *env_t = getenv("WSCONV_TWS");
-    const char *env_f = getenv("WSCONV_FUSED");
-    const int force_e = env_e ? atoi(env_e) : -1, force_g = env_g ? atoi(env_g) : 0;
-    const int tws_pref = env_t ? atoi(env_t) : 1, fused_pref = env_f ? atoi(env_f) : 1;
+    auto env = [](const char *k, int dflt) {
+        const char *v = getenv(k);
+        return v ? atoi(v) : dflt;
+    };
+    const int force_e = env("WSCONV_ELEMS", -1), tws = env("WSCONV_TWS", 1), pf = env("WSCONV_PF", -1);
+    const int one = env("WSCONV_GROUPS", 0) == 1;
+    int cfg3[3] = {-1, -1, -1};
+    if (const char *v = getenv("WSCONV_CFG")) sscanf(v, "%d,%d,%d", &cfg3[0], &cfg3[1], &cfg3[2]);
     for (int i = 0; i < ncand; ++i) {
         if (force_e >= 0 && cand[i] != force_e) continue;
-        if (configure(p, cand[i], tws_pref, fused_pref, force_g, smem_optin, sms)) return CONV_OK;
+        Candidate c = default_candidate(p, cand[i]);
+        c[1] = env("WSCONV_FUSED", 1);
+        for (int k = 0; k < 3; ++k) {
+            int &o = c[2 + k];
+            if (!tws) o &= ~CFG_TWS;
+            if (pf == 0) o &= ~CFG_PF;
+            if (pf == 1) o |= CFG_PF;
+            if (one) o |= CFG_ONE;
+            if (cfg3[k] >= 0) o = cfg3[k];
+        }
+        if (configure(p, c, smem_optin, sms)) return CONV_OK;
     }
     return fail(CONV_EUNSUPPORTED, "transform length " + std::to_string(p->M) +
                                        " is not 2^a 3^b 5^c or needs more threads than one CTA has");
 }
 
-// All configurations the autotuner may time: (E, twiddles in shared memory, fused).
-std::vector<std::array<int, 3>> transform_candidates(conv_plan_s *p)
+// The autotuner's search space, as families that share E and fused: within a family the options
+// of the three passes are chosen independently (each pass timed on its own), so a family lists
+// the distinct per-pass option sets, all passes taking the same one.
+std::vector<std::vector<Candidate>> transform_families(conv_plan_s *p)
 {
-    std::vector<std::array<int, 3>> out;
+    std::vector<std::vector<Candidate>> out;
     int smem_optin = 0, sms = 0;
     if (device_limits(p, smem_optin, sms) != CONV_OK) return out;
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
@@ -360,21 +429,32 @@ std::vector<std::array<int, 3>> transform_candidates(conv_plan_s *p)
     probe.tev_used.clear();
     probe.tev_free.clear();
     for (int i = 0; i < ncand; ++i)
-        for (int tws = 1; tws >= 0; --tws)
-            for (int fu = 1; fu >= 0; --fu) {
-                if (!configure(&probe, cand[i], tws, fu, 0, smem_optin, sms)) continue;
-                if ((int)probe.tws != tws || (int)probe.fused != fu) continue;  // not distinct
-                out.push_back({cand[i], tws, fu});
+        for (int fu = 1; fu >= 0; --fu) {
+            std::vector<Candidate> fam;
+            std::vector<std::array<int, 9>> seen;  // distinct (tws, staged, groups) of the three passes
+            for (int cfg = 0; cfg < (fu ? 8 : 2); ++cfg) {
+                const Candidate c = {cand[i], fu, cfg, cfg, cfg};
+                if (!configure(&probe, c, smem_optin, sms) || (int)probe.fused != fu) continue;
+                const std::array<int, 9> key = {probe.rows.tws, probe.rows.stage > 0, probe.rows.groups,
+                                                probe.cols.tws, probe.cols.stage > 0, probe.cols.groups,
+                                                probe.inv.tws,  probe.inv.stage > 0,  probe.inv.groups};
+                bool dup = false;
+                for (auto &k : seen) dup = dup || k == key;
+                if (dup) continue;
+                seen.push_back(key);
+                fam.push_back(c);
             }
+            if (!fam.empty()) out.push_back(fam);
+        }
     return out;
 }
 
-conv_status apply_candidate(conv_plan_s *p, const std::array<int, 3> &c)
+conv_status apply_candidate(conv_plan_s *p, const Candidate &c)
 {
     int smem_optin = 0, sms = 0;
     conv_status rc = device_limits(p, smem_optin, sms);
     if (rc != CONV_OK) return rc;
-    if (!configure(p, c[0], c[1], c[2], 0, smem_optin, sms)) return fail(CONV_EINVAL, "candidate does not apply");
+    if (!configure(p, c, smem_optin, sms)) return fail(CONV_EINVAL, "candidate does not apply");
     return CONV_OK;
 }
 
@@ -383,8 +463,8 @@ conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, voi
 {
     conv_status rc = CONV_OK;
     if (p->fused)
-        WSC_DISPATCH_FUSED(p->prec, p->elems, p->ed, p->tws,
-                           rc = (run_fused<T_, E_, ED_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
+        WSC_DISPATCH_FUSED(p->prec, p->elems, p->ed, false,
+                           rc = (run_fused<T_, E_, ED_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));
     else
         WSC_DISPATCH(p->prec, p->elems, p->tws,
                      rc = (run_pipeline<T_, E_, W_>(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st)));

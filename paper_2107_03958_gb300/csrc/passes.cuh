@@ -27,6 +27,10 @@ template <typename T> struct PassArgs {
     int batch;
     V alpha;               // pass 3 scale (already times 1/M^2)
     T beta;                // pass 3: out = beta u + alpha (.)
+    int *err;              // the plan's device status word (CONV_ETIMEOUT: a bounded wait gave up)
+    int stage_len;         // fused passes: elements V of each group's staging area (0: none)
+    int pf;                // fused passes: this launch prefetches work items into the staging areas
+    int vec;               // R2C pass 2: the output pairs may be stored as 16-byte vectors
 };
 
 // Shared-memory carve-up: [twiddles (M) if TWS][group 0 buffer][group 1 buffer]...
@@ -46,6 +50,23 @@ __device__ __forceinline__ typename cvec<T>::t *setup_smem(const PassArgs<T> &a,
         twp = a.tw;
     }
     return base + (size_t)g * padded_len<T>(a.M);
+}
+
+// Fused passes continue the carve-up with [staging 0]...[staging G-1][mbarrier 0]...[mbarrier G-1],
+// the staging block starting on a 16-byte boundary and every area a multiple of 16 bytes long
+// (pass_smem on the host computes the same sizes).  A pass with NBUF transform buffers per group
+// takes buffers NBUF g ... NBUF g + NBUF - 1 of the carve-up.
+template <typename T, bool TWS, int NBUF = 1>
+__device__ __forceinline__ typename cvec<T>::t *stage_area(const PassArgs<T> &a, int g, int G,
+                                                           unsigned long long *&bar)
+{
+    typedef typename cvec<T>::t V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    size_t off = (TWS ? (size_t)a.tw_len * sizeof(V) : 0) + (size_t)NBUF * G * padded_len<T>(a.M) * sizeof(V);
+    off = (off + 15) & ~(size_t)15;
+    const size_t st = ((size_t)a.stage_len * sizeof(V) + 15) & ~(size_t)15;
+    bar = reinterpret_cast<unsigned long long *>(smem_raw + off + (size_t)G * st) + g;
+    return reinterpret_cast<V *>(smem_raw + off + (size_t)g * st);
 }
 
 // ============================================================================ R2R pipeline
@@ -310,7 +331,7 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
     typedef typename cvec<T>::t V;
     const int n = p->n, M = p->M, h = p->h;
     const double sc = 1.0 / ((double)M * (double)M);
-    PassArgs<T> a;
+    PassArgs<T> a{};
     a.mask = reinterpret_cast<const T *>(mask);
     a.ghat = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
     a.u = u;

@@ -7,10 +7,58 @@
 //           writes the cropped, scaled result (plus beta u) to global memory.
 // Same work decomposition, layouts and results as passes.cuh; fewer shared-memory sweeps.
 #pragma once
+#include <type_traits>
+
+#include "async_copy.cuh"
 #include "fft_fused.cuh"
 #include "passes.cuh"
 
 namespace wsc {
+
+// ---------------------------------------------------------------------------- prefetch
+// With a.pf set, each thread group fetches the input of its next work item (unit + stride) into
+// its staging area as soon as stage 0 of the current item has read the staged input, so the
+// load latency hides behind the rest of the item's transforms.  Contiguous inputs (a row pair of
+// u, a row of a complex input, a column of W) move as one bulk copy on the group's mbarrier;
+// strided ones (the spectrum of a row pair or row, one element per k) as cp.async pieces.
+
+// A bounded wait gave up: record CONV_ETIMEOUT, wait (bounded again) for the copy still in flight
+// into this group's staging area, and let the caller leave the kernel.
+static __device__ __noinline__ void abandon(int *err, unsigned long long *bar, unsigned par, bool pending)
+{
+    if (threadIdx.x == 0 && err) atomicExch(err, (int)CONV_ETIMEOUT);
+    if (pending) mbar_wait(bar, par);
+}
+
+// Top of a work item in a bulk-copy pass: wait for its staged input.  False (for every thread of
+// the CTA) when some wait gave up.
+template <typename T>
+__device__ __forceinline__ bool await_bulk(const PassArgs<T> &a, unsigned long long *bar, unsigned &par,
+                                           bool valid)
+{
+    const bool ok = !valid || mbar_wait(bar, par);
+    if (__syncthreads_or(!ok)) {
+        abandon(a.err, bar, par, !ok);
+        return false;
+    }
+    if (valid) par ^= 1u;
+    return true;
+}
+
+// One thread of the group starts the bulk copy of `bytes` from `src` into the staging area.
+__device__ __forceinline__ void issue_bulk(void *stg, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(stg, src, bytes, bar);
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(typename cvec<T>::t *dst, const typename cvec<T>::t *src)
+{
+    if constexpr (sizeof(T) == 4) cp_async8(dst, src);
+    else cp_async16(dst, src);
+}
 
 // ============================================================================ R2R
 // The two spectra of a row pair sit side by side (W[k][j1], W[k][j1+1]); with n even the pair
@@ -45,6 +93,8 @@ __device__ __forceinline__ void store_pair(typename cvec<T>::t *p, typename cvec
     if (has2) p[1] = B;
 }
 
+// Pass 1.  Staging: rows j1, j1 + 1 of u (adjacent in memory), n T each; one bulk copy
+// (a.pf requires n sizeof(T) to be a multiple of 16 and u 16-byte aligned).
 template <typename T, int E, int ED, bool TWS>
 __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
 {
@@ -52,25 +102,47 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
-    const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2;
+    unsigned long long *bar;
+    T *stg = reinterpret_cast<T *>(stage_area<T, TWS>(a, g, G, bar));
+    const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2, stride = gridDim.x * G;
     const bool pair_vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0;
-    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+    auto fetch = [&](int unit) {
+        if (!a.pf || lt != 0 || unit >= a.units) return;
+        const int b = unit / pairs, j1 = 2 * (unit - b * pairs);
+        const unsigned bytes = (unsigned)((j1 + 1 < n ? 2 : 1) * (size_t)n * sizeof(T));
+        issue_bulk(stg, reinterpret_cast<const T *>(a.in) + (size_t)b * n * n + (size_t)j1 * n, bytes, bar);
+    };
+    unsigned par = 0;
+    if (a.pf) {
+        if (lt == 0) mbar_init(bar);
+        __syncthreads();
+        fetch(blockIdx.x * G + g);
+    }
+    for (int base = blockIdx.x * G; base < a.units; base += stride) {
         const int unit = base + g;
         const bool valid = unit < a.units;
+        if (a.pf && !await_bulk(a, bar, par, valid)) return;
         const int b = valid ? unit / pairs : 0, j1 = valid ? 2 * (unit - b * pairs) : 0;
         const bool has2 = valid && j1 + 1 < n;
         const T *ua = reinterpret_cast<const T *>(a.in) + (size_t)b * n * n + (size_t)j1 * n;
         const T *ma = a.mask ? a.mask + (size_t)j1 * n : nullptr;
         auto src = [&](int i) -> V {
             if (!valid || i >= n) return cmk<V>(0, 0);
-            T x = ua[i], y = has2 ? ua[n + i] : (T)0;
+            T x, y;
+            if (a.pf) {
+                x = stg[i];
+                y = has2 ? stg[n + i] : (T)0;
+            } else {
+                x = ua[i];
+                y = has2 ? ua[n + i] : (T)0;
+            }
             if (ma) {
                 x *= ma[i];
                 if (has2) y *= ma[n + i];
             }
             return cmk<V>(x, y);
         };
-        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, ToSmem{});
+        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
         if (valid) {
             V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * h * n;
             for (int k = lt; k < h; k += a.tpt) {
@@ -84,6 +156,8 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
     }
 }
 
+// Pass 2.  Staging: the column's n spectrum values (contiguous in W); one bulk copy (a.pf
+// requires n sizeof(V) to be a multiple of 16 and W 16-byte aligned).
 template <typename T, int E, int ED, bool TWS>
 __global__ void WSC_LB(T, E) kf_r2r_cols(const PassArgs<T> a)
 {
@@ -91,20 +165,40 @@ __global__ void WSC_LB(T, E) kf_r2r_cols(const PassArgs<T> a)
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
-    const int n = a.n, M = a.M, h = a.h;
+    unsigned long long *bar;
+    V *stg = stage_area<T, TWS>(a, g, G, bar);
+    const int n = a.n, M = a.M, h = a.h, stride = gridDim.x * G;
     const T *ghat = reinterpret_cast<const T *>(a.ghat);
-    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+    auto col_at = [&](int unit) -> V * {
+        const int k2 = unit / a.batch, b = unit - k2 * a.batch;
+        return reinterpret_cast<V *>(a.out) + (size_t)b * h * n + (size_t)k2 * n;
+    };
+    auto fetch = [&](int unit) {
+        if (!a.pf || lt != 0 || unit >= a.units) return;
+        issue_bulk(stg, col_at(unit), (unsigned)((size_t)n * sizeof(V)), bar);
+    };
+    unsigned par = 0;
+    if (a.pf) {
+        if (lt == 0) mbar_init(bar);
+        __syncthreads();
+        fetch(blockIdx.x * G + g);
+    }
+    for (int base = blockIdx.x * G; base < a.units; base += stride) {
         const int unit = base + g;
         const bool valid = unit < a.units;
-        const int k2 = valid ? unit / a.batch : 0, b = valid ? unit - k2 * a.batch : 0;
-        V *col = reinterpret_cast<V *>(a.out) + (size_t)b * h * n + (size_t)k2 * n;
+        if (a.pf && !await_bulk(a, bar, par, valid)) return;
+        const int k2 = valid ? unit / a.batch : 0;
+        V *col = col_at(valid ? unit : 0);
         const T *gc = ghat + (size_t)k2 * h;
-        auto src = [&](int i) -> V { return (valid && i < n) ? col[i] : cmk<V>(0, 0); };
+        auto src = [&](int i) -> V {
+            if (!valid || i >= n) return cmk<V>(0, 0);
+            return a.pf ? stg[i] : col[i];
+        };
         auto mul = smem_hook([&](int o, V &x) {
             const int k1 = o <= M / 2 ? o : M - o;
             x = cscale(x, __ldg(&gc[k1]));
         });
-        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul);
+        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
@@ -113,6 +207,8 @@ __global__ void WSC_LB(T, E) kf_r2r_cols(const PassArgs<T> a)
     }
 }
 
+// Pass 3.  Staging: the row pair's spectra W[k][j1], W[k][j1+1] for k <= M/2, side by side;
+// gathered by cp.async (a.pf requires W 16-byte aligned and, in FP32, n even).
 template <typename T, int E, int ED, bool TWS>
 __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
 {
@@ -120,12 +216,31 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
-    const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2;
+    unsigned long long *bar;
+    V *stg = stage_area<T, TWS>(a, g, G, bar);
+    const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2, stride = gridDim.x * G;
     const bool pair_vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
     const T alpha = a.alpha.x, beta = a.beta;
-    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+    auto gather = [&](int unit) {
+        if (!a.pf || unit >= a.units) return;
+        const int b = unit / pairs, j1 = 2 * (unit - b * pairs);
+        const V *Wp = reinterpret_cast<const V *>(a.in) + (size_t)b * h * n + j1;
+        const bool two = j1 + 1 < n;
+        for (int k = lt; k < h; k += a.tpt) {
+            cp_async16(stg + 2 * k, Wp + (size_t)k * n);  // FP32: both spectra (n even)
+            if constexpr (sizeof(T) == 8) {
+                if (two) cp_async16(stg + 2 * k + 1, Wp + (size_t)k * n + 1);
+            }
+        }
+    };
+    gather(blockIdx.x * G + g);
+    for (int base = blockIdx.x * G; base < a.units; base += stride) {
         const int unit = base + g;
         const bool valid = unit < a.units;
+        if (a.pf) {
+            cp_async_wait_all();
+            __syncthreads();
+        }
         const int b = valid ? unit / pairs : 0, j1 = valid ? 2 * (unit - b * pairs) : 0;
         const bool has2 = valid && j1 + 1 < n;
         const V *Wb = reinterpret_cast<const V *>(a.in) + (size_t)b * h * n;
@@ -133,9 +248,20 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
         auto src = [&](int i) -> V {
             if (!valid) return cmk<V>(0, 0);
             const bool lo = i <= M / 2;
-            const size_t k = (size_t)(lo ? i : M - i);
+            const int k = lo ? i : M - i;
             V A, B;
-            load_pair<T>(Wb + k * n + j1, A, B, has2, pair_vec);
+            if (a.pf) {
+                if constexpr (sizeof(T) == 4) {
+                    const float4 q = reinterpret_cast<const float4 *>(stg)[k];
+                    A = make_float2(q.x, q.y);
+                    B = make_float2(q.z, q.w);
+                } else {
+                    A = stg[2 * k];
+                    B = has2 ? stg[2 * k + 1] : cmk<V>(0, 0);
+                }
+            } else {
+                load_pair<T>(Wb + (size_t)k * n + j1, A, B, has2, pair_vec);
+            }
             return lo ? cmk<V>(A.x - B.y, A.y + B.x) : cmk<V>(A.x + B.y, B.x - A.y);
         };
         const size_t ro = (size_t)b * n * n + (size_t)j1 * n;
@@ -151,42 +277,200 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
             oa[o] = ra;
             if (has2) oa[n + o] = rb;
         };
-        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
+        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        __syncthreads();
+    }
+    if (a.pf) cp_async_wait_all();
+}
+
+// ============================================================================ R2C, complex ghat
+// Real densities with a complex, even multiplier (the Helmholtz kernel): A_n u = conv(u, g_r) +
+// i conv(u, g_i) with g_r, g_i the real, even kernels of Re ghat and Im ghat.  Pass 1 is the R2R
+// pass 1 (row-pair spectra W[k2][j1], k2 <= M/2); pass 2 transforms each column of W once and
+// multiplies it by Re ghat and by Im ghat, giving column k2 of the half spectra of both real
+// convolutions, stored side by side as W2[k2][j1] = (Wr, Wi); pass 3 packs Z_k = Wr_k + i Wi_k,
+// completes it to k < M by Hermitian symmetry of each part, and one inverse row transform gives
+// the complex output row conv(u, g_r) + i conv(u, g_i) directly.  2.25 M length-M transforms per
+// density instead of the C2C pipeline's 3 M.
+
+// Pass 2.  Two transform buffers per group: Re ghat's product transforms in the first, Im ghat's
+// in the second.  Staging: the column of W (one bulk copy, as in the R2R pass 2).
+template <typename T, int E, int ED, bool TWS>
+__global__ void WSC_LB(T, E) kf_r2c_cols(const PassArgs<T> a)
+{
+    typedef typename cvec<T>::t V;
+    const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
+    const V *twp;
+    V *bre = setup_smem<T, TWS>(a, twp, 2 * g);
+    V *bim = bre + padded_len<T>(a.M);
+    unsigned long long *bar;
+    V *stg = stage_area<T, TWS, 2>(a, g, G, bar);
+    const int n = a.n, M = a.M, h = a.h, stride = gridDim.x * G;
+    const V *cg = reinterpret_cast<const V *>(a.ghat);
+    auto col_off = [&](int unit) -> size_t {
+        const int k2 = unit / a.batch, b = unit - k2 * a.batch;
+        return (size_t)b * h * n + (size_t)k2 * n;
+    };
+    auto fetch = [&](int unit) {
+        if (!a.pf || lt != 0 || unit >= a.units) return;
+        issue_bulk(stg, reinterpret_cast<const V *>(a.in) + col_off(unit), (unsigned)((size_t)n * sizeof(V)), bar);
+    };
+    unsigned par = 0;
+    if (a.pf) {
+        if (lt == 0) mbar_init(bar);
+        __syncthreads();
+        fetch(blockIdx.x * G + g);
+    }
+    for (int base = blockIdx.x * G; base < a.units; base += stride) {
+        const int unit = base + g;
+        const bool valid = unit < a.units;
+        if (a.pf && !await_bulk(a, bar, par, valid)) return;
+        const int k2 = valid ? unit / a.batch : 0;
+        const size_t co = col_off(valid ? unit : 0);
+        const V *cin = reinterpret_cast<const V *>(a.in) + co;
+        auto src = [&](int i) -> V {
+            if (!valid || i >= n) return cmk<V>(0, 0);
+            return a.pf ? stg[i] : cin[i];
+        };
+        const V *gc = cg + (size_t)k2 * h;
+        auto mul = smem_hook([&](int o, V &x) {
+            const int k1 = o <= M / 2 ? o : M - o;
+            const V gk = __ldg(&gc[k1]);
+            bim[pidx<T>(o)] = cscale(x, gk.y);
+            x = cscale(x, gk.x);
+        });
+        fft_fused<T, E, ED, false, TWS>(bre, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_fused<T, E, ED, true, TWS>(bre, a.P, twp, lt, a.tpt, FromSmem{}, ToSmem{});
+        V *cout = reinterpret_cast<V *>(a.out) + 2 * co;
+        auto dst = [&](int o, V xi) {
+            if (!valid || o >= n) return;
+            const V xr = bre[pidx<T>(o)];
+            if constexpr (sizeof(T) == 4) {
+                if (a.vec) {
+                    *reinterpret_cast<float4 *>(cout + 2 * o) = make_float4(xr.x, xr.y, xi.x, xi.y);
+                    return;
+                }
+            }
+            cout[2 * o] = xr;
+            cout[2 * o + 1] = xi;
+        };
+        fft_fused<T, E, ED, true, TWS>(bim, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
 
-// ============================================================================ C2C
-template <typename T, int E, int ED, bool TWS, bool IN_REAL>
-__global__ void WSC_LB(T, E) kf_c2c_rows_fwd(const PassArgs<T> a)
+// Pass 3.  Staging: the row's pairs W2[k][j1] = (Wr, Wi), k <= M/2, gathered by cp.async
+// (16-byte pieces; a.pf requires W2 16-byte aligned).
+template <typename T, int E, int ED, bool TWS>
+__global__ void WSC_LB(T, E) kf_r2c_rows_inv(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
-    const int n = a.n, M = a.M;
-    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+    unsigned long long *bar;
+    V *stg = stage_area<T, TWS>(a, g, G, bar);
+    const int n = a.n, M = a.M, h = a.h, stride = gridDim.x * G;
+    auto gather = [&](int unit) {
+        if (!a.pf || unit >= a.units) return;
+        const int b = unit / n, j1 = unit - b * n;
+        const V *Wp = reinterpret_cast<const V *>(a.in) + 2 * ((size_t)b * h * n + j1);
+        for (int k = lt; k < h; k += a.tpt) {
+            cp_async16(stg + 2 * k, Wp + 2 * (size_t)k * n);
+            if constexpr (sizeof(T) == 8) cp_async16(stg + 2 * k + 1, Wp + 2 * (size_t)k * n + 1);
+        }
+    };
+    gather(blockIdx.x * G + g);
+    for (int base = blockIdx.x * G; base < a.units; base += stride) {
         const int unit = base + g;
         const bool valid = unit < a.units;
+        if (a.pf) {
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        const int b = valid ? unit / n : 0, j1 = valid ? unit - b * n : 0;
+        const V *Wb = reinterpret_cast<const V *>(a.in) + 2 * ((size_t)b * h * n + j1);
+        // Z_k = Wr_k + i Wi_k (k <= M/2), Z_k = conj Wr_{M-k} + i conj Wi_{M-k} (k > M/2)
+        auto src = [&](int i) -> V {
+            if (!valid) return cmk<V>(0, 0);
+            const bool lo = i <= M / 2;
+            const int k = lo ? i : M - i;
+            V A, B;
+            if (a.pf) {
+                A = stg[2 * k];
+                B = stg[2 * k + 1];
+            } else {
+                A = Wb[2 * (size_t)k * n];
+                B = Wb[2 * (size_t)k * n + 1];
+            }
+            return lo ? cmk<V>(A.x - B.y, A.y + B.x) : cmk<V>(A.x + B.y, B.x - A.y);
+        };
+        const size_t ro = (size_t)b * n * n + (size_t)j1 * n;
+        V *o_ = reinterpret_cast<V *>(a.out) + ro;
+        const T *ua = reinterpret_cast<const T *>(a.u) + ro;
+        auto dst = [&](int o, V z) {
+            if (!valid || o >= n) return;
+            z = cmul(z, a.alpha);
+            if (a.beta != (T)0) z.x += a.beta * ua[o];
+            o_[o] = z;
+        };
+        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        __syncthreads();
+    }
+    if (a.pf) cp_async_wait_all();
+}
+
+// ============================================================================ C2C
+// Pass 1.  Staging: row j1 of the input (n T real or n V complex); one bulk copy (a.pf requires
+// its byte length to be a multiple of 16 and the input 16-byte aligned).
+template <typename T, int E, int ED, bool TWS, bool IN_REAL>
+__global__ void WSC_LB(T, E) kf_c2c_rows_fwd(const PassArgs<T> a)
+{
+    typedef typename cvec<T>::t V;
+    typedef typename std::conditional<IN_REAL, T, V>::type I;
+    const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
+    const V *twp;
+    V *buf = setup_smem<T, TWS>(a, twp, g);
+    unsigned long long *bar;
+    I *stg = reinterpret_cast<I *>(stage_area<T, TWS>(a, g, G, bar));
+    const int n = a.n, M = a.M, stride = gridDim.x * G;
+    const I *in = reinterpret_cast<const I *>(a.in);
+    auto fetch = [&](int unit) {
+        if (!a.pf || lt != 0 || unit >= a.units) return;
+        const int b = unit / n, j1 = unit - b * n;
+        issue_bulk(stg, in + (size_t)b * n * n + (size_t)j1 * n, (unsigned)((size_t)n * sizeof(I)), bar);
+    };
+    unsigned par = 0;
+    if (a.pf) {
+        if (lt == 0) mbar_init(bar);
+        __syncthreads();
+        fetch(blockIdx.x * G + g);
+    }
+    for (int base = blockIdx.x * G; base < a.units; base += stride) {
+        const int unit = base + g;
+        const bool valid = unit < a.units;
+        if (a.pf && !await_bulk(a, bar, par, valid)) return;
         const int b = valid ? unit / n : 0, j1 = valid ? unit - b * n : 0;
         const size_t ro = (size_t)b * n * n + (size_t)j1 * n;
         const T *mr = a.mask ? a.mask + (size_t)j1 * n : nullptr;
         auto src = [&](int i) -> V {
             if (!valid || i >= n) return cmk<V>(0, 0);
+            const I x = a.pf ? stg[i] : in[ro + i];
             V z;
-            if (IN_REAL) z = cmk<V>(reinterpret_cast<const T *>(a.in)[ro + i], (T)0);
-            else z = reinterpret_cast<const V *>(a.in)[ro + i];
+            if constexpr (IN_REAL) z = cmk<V>(x, (T)0);
+            else z = x;
             return mr ? cscale(z, mr[i]) : z;
         };
         V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * M * n;
         auto dst = [&](int o, V z) {
             if (valid) Wb[(size_t)o * n + j1] = z;
         };
-        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
+        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
         __syncthreads();
     }
 }
 
+// Pass 2.  Staging: the column's n spectrum values; one bulk copy (as in the R2R pass 2).
 template <typename T, int E, int ED, bool TWS, bool CG>
 __global__ void WSC_LB(T, E) kf_c2c_cols(const PassArgs<T> a)
 {
@@ -194,20 +478,40 @@ __global__ void WSC_LB(T, E) kf_c2c_cols(const PassArgs<T> a)
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
-    const int n = a.n, M = a.M, h = a.h;
-    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+    unsigned long long *bar;
+    V *stg = stage_area<T, TWS>(a, g, G, bar);
+    const int n = a.n, M = a.M, h = a.h, stride = gridDim.x * G;
+    auto col_at = [&](int unit) -> V * {
+        const int k2 = unit / a.batch, b = unit - k2 * a.batch;
+        return reinterpret_cast<V *>(a.out) + (size_t)b * M * n + (size_t)k2 * n;
+    };
+    auto fetch = [&](int unit) {
+        if (!a.pf || lt != 0 || unit >= a.units) return;
+        issue_bulk(stg, col_at(unit), (unsigned)((size_t)n * sizeof(V)), bar);
+    };
+    unsigned par = 0;
+    if (a.pf) {
+        if (lt == 0) mbar_init(bar);
+        __syncthreads();
+        fetch(blockIdx.x * G + g);
+    }
+    for (int base = blockIdx.x * G; base < a.units; base += stride) {
         const int unit = base + g;
         const bool valid = unit < a.units;
-        const int k2 = valid ? unit / a.batch : 0, b = valid ? unit - k2 * a.batch : 0;
-        V *col = reinterpret_cast<V *>(a.out) + (size_t)b * M * n + (size_t)k2 * n;
+        if (a.pf && !await_bulk(a, bar, par, valid)) return;
+        const int k2 = valid ? unit / a.batch : 0;
+        V *col = col_at(valid ? unit : 0);
         const int k2q = k2 <= M / 2 ? k2 : M - k2;
-        auto src = [&](int i) -> V { return (valid && i < n) ? col[i] : cmk<V>(0, 0); };
+        auto src = [&](int i) -> V {
+            if (!valid || i >= n) return cmk<V>(0, 0);
+            return a.pf ? stg[i] : col[i];
+        };
         auto mul = smem_hook([&](int o, V &x) {
             const int k1 = o <= M / 2 ? o : M - o;
             if (CG) x = cmul(x, __ldg(reinterpret_cast<const V *>(a.ghat) + (size_t)k2q * h + k1));
             else x = cscale(x, __ldg(reinterpret_cast<const T *>(a.ghat) + (size_t)k2q * h + k1));
         });
-        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul);
+        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
@@ -216,6 +520,8 @@ __global__ void WSC_LB(T, E) kf_c2c_cols(const PassArgs<T> a)
     }
 }
 
+// Pass 3.  Staging: the row's spectrum W[i][j1], i < M, one element per i; gathered by cp.async
+// (8-byte pieces in FP32, 16-byte in FP64; a.pf requires W aligned to the element size).
 template <typename T, int E, int ED, bool TWS, bool IN_REAL>
 __global__ void WSC_LB(T, E) kf_c2c_rows_inv(const PassArgs<T> a)
 {
@@ -223,13 +529,29 @@ __global__ void WSC_LB(T, E) kf_c2c_rows_inv(const PassArgs<T> a)
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
-    const int n = a.n, M = a.M;
-    for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
+    unsigned long long *bar;
+    V *stg = stage_area<T, TWS>(a, g, G, bar);
+    const int n = a.n, M = a.M, stride = gridDim.x * G;
+    auto gather = [&](int unit) {
+        if (!a.pf || unit >= a.units) return;
+        const int b = unit / n, j1 = unit - b * n;
+        const V *Wp = reinterpret_cast<const V *>(a.in) + (size_t)b * M * n + j1;
+        for (int i = lt; i < M; i += a.tpt) cp_async_elem<T>(stg + i, Wp + (size_t)i * n);
+    };
+    gather(blockIdx.x * G + g);
+    for (int base = blockIdx.x * G; base < a.units; base += stride) {
         const int unit = base + g;
         const bool valid = unit < a.units;
+        if (a.pf) {
+            cp_async_wait_all();
+            __syncthreads();
+        }
         const int b = valid ? unit / n : 0, j1 = valid ? unit - b * n : 0;
         const V *Wb = reinterpret_cast<const V *>(a.in) + (size_t)b * M * n;
-        auto src = [&](int i) -> V { return valid ? Wb[(size_t)i * n + j1] : cmk<V>(0, 0); };
+        auto src = [&](int i) -> V {
+            if (!valid) return cmk<V>(0, 0);
+            return a.pf ? stg[i] : Wb[(size_t)i * n + j1];
+        };
         const size_t ro = (size_t)b * n * n + (size_t)j1 * n;
         V *o_ = reinterpret_cast<V *>(a.out) + ro;
         auto dst = [&](int o, V z) {
@@ -245,9 +567,10 @@ __global__ void WSC_LB(T, E) kf_c2c_rows_inv(const PassArgs<T> a)
             }
             o_[o] = z;
         };
-        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst);
+        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
+    if (a.pf) cp_async_wait_all();
 }
 
 // ============================================================================ host glue
@@ -257,6 +580,8 @@ template <typename T, int E, int ED, bool TWS> conv_status set_attrs_fused(int s
     WSC_ATTR((kf_r2r_rows_fwd<T, E, ED, TWS>));
     WSC_ATTR((kf_r2r_cols<T, E, ED, TWS>));
     WSC_ATTR((kf_r2r_rows_inv<T, E, ED, TWS>));
+    WSC_ATTR((kf_r2c_cols<T, E, ED, TWS>));
+    WSC_ATTR((kf_r2c_rows_inv<T, E, ED, TWS>));
     WSC_ATTR((kf_c2c_rows_fwd<T, E, ED, TWS, true>));
     WSC_ATTR((kf_c2c_rows_fwd<T, E, ED, TWS, false>));
     WSC_ATTR((kf_c2c_cols<T, E, ED, TWS, true>));
@@ -278,14 +603,15 @@ template <typename T, int E, int ED, bool TWS> int blocks_per_sm_fused(int threa
     return nb > 0 ? nb : 1;
 }
 
-template <typename T, int E, int ED, bool TWS>
+template <typename T, int E, int ED>
 conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
                       double aim, double beta, void *ws, cudaStream_t st)
 {
     typedef typename cvec<T>::t V;
     const int n = p->n, M = p->M, h = p->h;
     const double sc = 1.0 / ((double)M * (double)M);
-    PassArgs<T> a;
+    PassArgs<T> a{};
+    a.err = p->dev_err;
     a.mask = reinterpret_cast<const T *>(mask);
     a.ghat = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
     a.u = u;
@@ -303,6 +629,23 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         long long need = (units + S.groups - 1) / S.groups;
         return (unsigned)std::min<long long>(need, (long long)S.max_ctas);
     };
+    // prefetch needs the staged runs to start on 16 bytes (bulk copies, 16-byte cp.async) or on
+    // their element size (8-byte cp.async), and bulk copy lengths that are multiples of 16
+    auto al = [](const void *q, size_t m) { return (reinterpret_cast<uintptr_t>(q) % m) == 0; };
+    const bool ws16 = al(ws, 16);
+    const bool pf_cols = C.stage > 0 && ws16 && (n * sizeof(V)) % 16 == 0;
+    // one launch of kernel K<T, E, ED, tws[, X]> in shape S, with S's twiddle option
+#define WSC_TARGS(T_, E_, ED_) T_, E_, ED_
+#define WSC_LAUNCH(S, K, TA)                                                                   \
+    do {                                                                                      \
+        if ((S).tws) K<WSC_TARGS TA, true><<<grid(S, a.units), (S).tpt * (S).groups, (S).smem, st>>>(a);  \
+        else K<WSC_TARGS TA, false><<<grid(S, a.units), (S).tpt * (S).groups, (S).smem, st>>>(a);      \
+    } while (0)
+#define WSC_LAUNCH2(S, K, TA, X)                                                                  \
+    do {                                                                                         \
+        if ((S).tws) K<WSC_TARGS TA, true, X><<<grid(S, a.units), (S).tpt * (S).groups, (S).smem, st>>>(a); \
+        else K<WSC_TARGS TA, false, X><<<grid(S, a.units), (S).tpt * (S).groups, (S).smem, st>>>(a);     \
+    } while (0)
     cudaEvent_t *ev = timing_slot(p);
     if (ev) cudaEventRecord(ev[0], st);
     if (p->io == CONV_IO_R2R) {
@@ -310,45 +653,87 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.in = u;
         a.out = ws;
         a.units = batch * ((n + 1) / 2);
-        kf_r2r_rows_fwd<T, E, ED, TWS><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+        a.stage_len = R.stage;
+        a.pf = R.stage > 0 && al(u, 16) && (n * sizeof(T)) % 16 == 0;
+        WSC_LAUNCH(R, kf_r2r_rows_fwd, (T, E, ED));
         if (ev) cudaEventRecord(ev[1], st);
         a.tpt = C.tpt;
         a.in = ws;
         a.units = batch * h;
-        kf_r2r_cols<T, E, ED, TWS><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
+        a.stage_len = C.stage;
+        a.pf = pf_cols;
+        WSC_LAUNCH(C, kf_r2r_cols, (T, E, ED));
         if (ev) cudaEventRecord(ev[2], st);
         a.tpt = I.tpt;
         a.out = out;
         a.units = batch * ((n + 1) / 2);
-        kf_r2r_rows_inv<T, E, ED, false><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
+        a.stage_len = I.stage;
+        a.pf = I.stage > 0 && ws16 && (sizeof(T) == 8 || n % 2 == 0);
+        WSC_LAUNCH(I, kf_r2r_rows_inv, (T, E, ED));
+    } else if (p->r2c_split) {
+        a.tpt = R.tpt;
+        a.in = u;
+        a.out = ws;
+        a.units = batch * ((n + 1) / 2);
+        a.stage_len = R.stage;
+        a.pf = R.stage > 0 && al(u, 16) && (n * sizeof(T)) % 16 == 0;
+        WSC_LAUNCH(R, kf_r2r_rows_fwd, (T, E, ED));
+        if (ev) cudaEventRecord(ev[1], st);
+        // W2 follows W on the next even element (the workspace holds batch (3 h n + 1) values)
+        V *W2 = reinterpret_cast<V *>(ws) + (((size_t)batch * h * n + 1) & ~(size_t)1);
+        a.tpt = C.tpt;
+        a.in = ws;
+        a.out = W2;
+        a.units = batch * h;
+        a.stage_len = C.stage;
+        a.pf = pf_cols;
+        a.vec = al(W2, 16);
+        WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
+        if (ev) cudaEventRecord(ev[2], st);
+        a.tpt = I.tpt;
+        a.in = W2;
+        a.out = out;
+        a.units = batch * n;
+        a.stage_len = I.stage;
+        a.pf = I.stage > 0 && al(W2, 16);
+        WSC_LAUNCH(I, kf_r2c_rows_inv, (T, E, ED));
     } else {
         const bool in_real = p->io == CONV_IO_R2C;
         a.tpt = R.tpt;
         a.in = u;
         a.out = ws;
         a.units = batch * n;
+        a.stage_len = R.stage;
+        a.pf = R.stage > 0 && al(u, 16) && (n * (in_real ? sizeof(T) : sizeof(V))) % 16 == 0;
         if (in_real)
-            kf_c2c_rows_fwd<T, E, ED, TWS, true><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+            WSC_LAUNCH2(R, kf_c2c_rows_fwd, (T, E, ED), true);
         else
-            kf_c2c_rows_fwd<T, E, ED, TWS, false><<<grid(R, a.units), R.tpt * R.groups, R.smem, st>>>(a);
+            WSC_LAUNCH2(R, kf_c2c_rows_fwd, (T, E, ED), false);
         if (ev) cudaEventRecord(ev[1], st);
         a.tpt = C.tpt;
         a.in = ws;
         a.units = batch * M;
+        a.stage_len = C.stage;
+        a.pf = pf_cols;
         if (p->complex_ghat)
-            kf_c2c_cols<T, E, ED, TWS, true><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
+            WSC_LAUNCH2(C, kf_c2c_cols, (T, E, ED), true);
         else
-            kf_c2c_cols<T, E, ED, TWS, false><<<grid(C, a.units), C.tpt * C.groups, C.smem, st>>>(a);
+            WSC_LAUNCH2(C, kf_c2c_cols, (T, E, ED), false);
         if (ev) cudaEventRecord(ev[2], st);
         a.tpt = I.tpt;
         a.out = out;
         a.units = batch * n;
+        a.stage_len = I.stage;
+        a.pf = I.stage > 0 && al(ws, sizeof(V));
         if (in_real)
-            kf_c2c_rows_inv<T, E, ED, false, true><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
+            WSC_LAUNCH2(I, kf_c2c_rows_inv, (T, E, ED), true);
         else
-            kf_c2c_rows_inv<T, E, ED, false, false><<<grid(I, a.units), I.tpt * I.groups, I.smem, st>>>(a);
+            WSC_LAUNCH2(I, kf_c2c_rows_inv, (T, E, ED), false);
     }
     if (ev) cudaEventRecord(ev[3], st);
+#undef WSC_LAUNCH2
+#undef WSC_LAUNCH
+#undef WSC_TARGS
     WSC_CUDA(cudaGetLastError());
     return CONV_OK;
 }

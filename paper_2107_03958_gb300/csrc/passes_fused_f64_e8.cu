@@ -2,22 +2,19 @@
 #include "passes_fused.cuh"
 
 namespace wsc {
-template conv_status run_fused<double, 8, 136, true>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
+template conv_status run_fused<double, 8, 136>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
 template conv_status set_attrs_fused<double, 8, 136, true>(int);
 template int blocks_per_sm_fused<double, 8, 136, true>(int, size_t);
-template conv_status run_fused<double, 8, 136, false>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
 template conv_status set_attrs_fused<double, 8, 136, false>(int);
 template int blocks_per_sm_fused<double, 8, 136, false>(int, size_t);
-template conv_status run_fused<double, 8, 130, true>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
+template conv_status run_fused<double, 8, 130>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
 template conv_status set_attrs_fused<double, 8, 130, true>(int);
 template int blocks_per_sm_fused<double, 8, 130, true>(int, size_t);
-template conv_status run_fused<double, 8, 130, false>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
 template conv_status set_attrs_fused<double, 8, 130, false>(int);
 template int blocks_per_sm_fused<double, 8, 130, false>(int, size_t);
-template conv_status run_fused<double, 8, 132, true>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
+template conv_status run_fused<double, 8, 132>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
 template conv_status set_attrs_fused<double, 8, 132, true>(int);
 template int blocks_per_sm_fused<double, 8, 132, true>(int, size_t);
-template conv_status run_fused<double, 8, 132, false>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
 template conv_status set_attrs_fused<double, 8, 132, false>(int);
 template int blocks_per_sm_fused<double, 8, 132, false>(int, size_t);
 }  // namespace wsc

@@ -29,6 +29,9 @@ conv_status cuda_fail(cudaError_t e, const char *what)
 
 size_t spectrum_elems(const conv_plan_s *p)
 {
+    // R2C with complex ghat: the split pipeline's W and W2 (3 h n, plus one for W2's alignment),
+    // which also holds the C2C layout (M n) that the unfused passes use
+    if (p->io == CONV_IO_R2C && p->complex_ghat) return 3 * (size_t)p->h * p->n + 1;
     return (size_t)(p->io == CONV_IO_R2R ? p->h : p->M) * p->n;
 }
 
@@ -56,8 +59,8 @@ static conv_status upload_twiddles(conv_plan_s *p)
     return CONV_OK;
 }
 
-std::vector<std::array<int, 3>> transform_candidates(conv_plan_s *p);
-conv_status apply_candidate(conv_plan_s *p, const std::array<int, 3> &c);
+std::vector<std::vector<Candidate>> transform_families(conv_plan_s *p);
+conv_status apply_candidate(conv_plan_s *p, const Candidate &c);
 
 // Re-upload the stage table and twiddles after the launch configuration changed.
 static conv_status reupload(conv_plan_s *p)
@@ -71,13 +74,15 @@ static conv_status reupload(conv_plan_s *p)
     return CONV_OK;
 }
 
-// Autotuner: time every launch configuration (per-thread count, shared-memory twiddles, fused
-// passes) on zero densities at the plan's batch size and keep the fastest.  Choices are cached per
-// (transform length, n, precision, io, batch, compact) for the process.
+// Autotuner: for every family of launch configurations (elements per thread, fused or not) time
+// each distinct option set on zero densities at the plan's batch size, pass by pass; keep each
+// pass's fastest option (fused passes choose independently; the plain passes share one) and the
+// family with the least total.  Choices are cached per (transform length, n, precision, io,
+// batch, compact) for the process.
 static conv_status autotune(conv_plan_s *p)
 {
     static std::mutex mu;
-    static std::map<std::array<int, 6>, std::array<int, 3>> cache;
+    static std::map<std::array<int, 6>, Candidate> cache;
     const std::array<int, 6> key = {p->M, p->n, (int)p->prec, (int)p->io, p->batch_max, p->compact ? 1 : 0};
     {
         std::lock_guard<std::mutex> lk(mu);
@@ -87,8 +92,10 @@ static conv_status autotune(conv_plan_s *p)
             return rc == CONV_OK ? reupload(p) : rc;
         }
     }
-    auto cands = transform_candidates(p);
-    if (cands.size() <= 1) return CONV_OK;
+    const auto fams = transform_families(p);
+    size_t total = 0;
+    for (const auto &f : fams) total += f.size();
+    if (total <= 1) return CONV_OK;
     const int B = p->batch_max;
     const size_t rsz = p->prec == CONV_P_FP64 ? 8 : 4;
     const size_t in_b = (size_t)B * p->n * p->n * rsz * (p->io == CONV_IO_C2C ? 2 : 1);
@@ -100,34 +107,46 @@ static conv_status autotune(conv_plan_s *p)
         return fail(CONV_ENOMEM, "autotuner buffers");
     }
     cudaMemsetAsync(u, 0, in_b, p->setup_stream);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    std::array<int, 3> pick = cands[0];
+    const bool was_timing = p->timing;
+    double best_total = 1e300;
+    Candidate pick = fams[0][0];
     conv_status rc = CONV_OK;
-    for (const auto &c : cands) {
-        rc = apply_candidate(p, c);
-        if (rc == CONV_OK) rc = reupload(p);
-        if (rc != CONV_OK) break;
-        for (int w = 0; w < 2; ++w) launch_pipeline(p, u, nullptr, out, B, 1.0, 0.0, 0.0, p->ws, p->setup_stream);
-        cudaEventRecord(e0, p->setup_stream);
-        for (int r = 0; r < 3; ++r) launch_pipeline(p, u, nullptr, out, B, 1.0, 0.0, 0.0, p->ws, p->setup_stream);
-        cudaEventRecord(e1, p->setup_stream);
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "autotuner run");
-            break;
+    for (const auto &fam : fams) {
+        const bool fused = fam[0][1] != 0;
+        double best_ms[3] = {1e300, 1e300, 1e300}, best_sum = 1e300;
+        Candidate fpick = fam[0];
+        for (const auto &c : fam) {
+            rc = apply_candidate(p, c);
+            if (rc == CONV_OK) rc = reupload(p);
+            if (rc != CONV_OK) break;
+            p->timing = false;
+            for (int w = 0; w < 2; ++w) launch_pipeline(p, u, nullptr, out, B, 1.0, 0.0, 0.0, p->ws, p->setup_stream);
+            p->timing = true;
+            for (int r = 0; r < 3; ++r) launch_pipeline(p, u, nullptr, out, B, 1.0, 0.0, 0.0, p->ws, p->setup_stream);
+            p->timing = false;
+            double ms[3];
+            long long cnt = 0;
+            rc = conv_timing_read(p, ms, &cnt);
+            if (rc != CONV_OK) break;
+            if (fused) {
+                for (int k = 0; k < 3; ++k)
+                    if (ms[k] < best_ms[k]) {
+                        best_ms[k] = ms[k];
+                        fpick[2 + k] = c[2 + k];
+                    }
+            } else if (ms[0] + ms[1] + ms[2] < best_sum) {
+                best_sum = ms[0] + ms[1] + ms[2];
+                fpick = c;
+            }
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            pick = c;
+        if (rc != CONV_OK) break;
+        const double tot = fused ? best_ms[0] + best_ms[1] + best_ms[2] : best_sum;
+        if (tot < best_total) {
+            best_total = tot;
+            pick = fpick;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    p->timing = was_timing;
     cudaFree(u);
     cudaFree(out);
     if (rc != CONV_OK) return rc;
@@ -267,12 +286,17 @@ conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_d
     }
     conv_status rc = select_transform(p);
     if (rc == CONV_OK) {
-        if (cudaMalloc(&p->fft_dev, sizeof(FFTDesc)) != cudaSuccess) {
+        // the stage table, then the device status word on the next 16-byte boundary
+        const size_t err_off = (sizeof(FFTDesc) + 15) & ~(size_t)15;
+        if (cudaMalloc(&p->fft_dev, err_off + 16) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(CONV_ENOMEM, "cudaMalloc of the stage table failed");
-        } else if (cudaMemcpyAsync(p->fft_dev, &p->fft, sizeof(FFTDesc), cudaMemcpyHostToDevice, p->setup_stream) !=
-                   cudaSuccess) {
-            rc = cuda_fail(cudaGetLastError(), "stage table upload");
+        } else {
+            p->dev_err = reinterpret_cast<int *>(reinterpret_cast<char *>(p->fft_dev) + err_off);
+            if (cudaMemcpyAsync(p->fft_dev, &p->fft, sizeof(FFTDesc), cudaMemcpyHostToDevice, p->setup_stream) !=
+                    cudaSuccess ||
+                cudaMemsetAsync(p->dev_err, 0, sizeof(int), p->setup_stream) != cudaSuccess)
+                rc = cuda_fail(cudaGetLastError(), "stage table upload");
         }
     }
     if (rc == CONV_OK) rc = upload_twiddles(p);
@@ -297,6 +321,24 @@ conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_d
     return CONV_OK;
 }
 
+conv_status conv_device_status(conv_plan_t p, void *stream)
+{
+    if (!p) return fail(CONV_EINVAL, "null plan");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    WSC_CUDA(cudaStreamSynchronize(st));
+    int word = 0;
+    WSC_CUDA(cudaMemcpyAsync(&word, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WSC_CUDA(cudaStreamSynchronize(st));
+    if (word != 0) {
+        WSC_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), st));
+        WSC_CUDA(cudaStreamSynchronize(st));
+        return fail((conv_status)word, "a pass kernel's bounded wait for an asynchronous copy gave up; the "
+                                       "results of the applies since the last check are incomplete");
+    }
+    if (p->fp64_twin) return conv_device_status(p->fp64_twin, stream);
+    return CONV_OK;
+}
+
 conv_status conv_workspace_size(conv_plan_t p, int batch, size_t *bytes)
 {
     if (!p || !bytes || batch < 0) return fail(CONV_EINVAL, "bad argument");
@@ -316,6 +358,13 @@ conv_status conv_apply_axpby(conv_plan_t p, const void *u, const void *mask, voi
     if (p->io == CONV_IO_R2R && alpha_im != 0.0)
         return fail(CONV_EINVAL, "a real-to-real plan needs a real alpha");
     if (batch > 65535) return fail(CONV_EINVAL, "batch must be <= 65535");
+    // element alignment of the caller's arrays; 16 bytes for a caller's workspace
+    const size_t rb = p->prec == CONV_P_FP64 ? 8 : 4;
+    auto al = [](const void *q, size_t m) { return (reinterpret_cast<uintptr_t>(q) % m) == 0; };
+    if (!al(u, p->io == CONV_IO_C2C ? 2 * rb : rb) || !al(out, p->io == CONV_IO_R2R ? rb : 2 * rb) ||
+        (mask && !al(mask, rb)))
+        return fail(CONV_EINVAL, "u, out and mask must be aligned to their element size");
+    if (workspace && !al(workspace, 16)) return fail(CONV_EINVAL, "the workspace must be 16-byte aligned");
     void *ws = workspace;
     if (!ws) {
         if (batch > p->batch_max)

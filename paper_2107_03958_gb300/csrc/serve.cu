@@ -66,6 +66,7 @@ struct Batch {
     std::vector<std::shared_ptr<Req>> reqs;
     std::shared_ptr<CachedPlan> cp;
     cudaEvent_t ev = nullptr;
+    int pin = -1;  // pinned slot receiving the plan's device status word after the apply
 };
 
 }  // namespace wsc
@@ -73,6 +74,8 @@ struct Batch {
 struct srv_s {
     size_t budget = 0, in_use = 0;
     int max_inflight = 64, batch_max = 16, ls_workers = 4, plan_flags = 0;
+    int *status_pin = nullptr;  // pinned host slots, one per batch in flight
+    std::vector<int> free_pins;
     std::mutex mu;
     std::condition_variable cv_dispatch, cv_done, cv_ls;
     std::deque<std::shared_ptr<wsc::Req>> pending;
@@ -121,7 +124,8 @@ static size_t plan_bytes_estimate(const srv_request &r, int batch_max, int flags
     if (flags & CONV_PLAN_COMPACT) ghat += (size_t)h * h * 8 * (r.kernel.family == CONV_K_HELMHOLTZ ? 2 : 1);
     if (r.precision == CONV_P_FP32) ghat += ghat / 2;
     const int B = r.kind == SRV_LS ? 1 : batch_max;
-    size_t ws = (size_t)(c2c ? M : h) * n * cz * B;
+    const bool split = r.kind == SRV_CONV && r.io == CONV_IO_R2C && r.kernel.family == CONV_K_HELMHOLTZ;
+    size_t ws = (size_t)(split ? 3 * h + 1 : (c2c ? M : h)) * n * cz * B;
     size_t stage = 0;
     if (r.kind == SRV_CONV) {
         const size_t in_b = (size_t)n * n * (r.io == CONV_IO_C2C ? cz : cz / 2);
@@ -241,6 +245,12 @@ static void launch_batch(srv_t s, Batch &bt)
         for (int i = 0; i < B; ++i)
             cudaMemcpyAsync(bt.reqs[i]->r.out, (char *)cp->stage_out + i * ob, ob, cudaMemcpyDeviceToDevice, cp->stream);
     }
+    if (st == CONV_OK && !s->free_pins.empty()) {
+        bt.pin = s->free_pins.back();
+        s->free_pins.pop_back();
+        s->status_pin[bt.pin] = 0;
+        cudaMemcpyAsync(&s->status_pin[bt.pin], cp->plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost, cp->stream);
+    }
     cudaEventCreateWithFlags(&bt.ev, cudaEventDisableTiming);
     cudaEventRecord(bt.ev, cp->stream);
     for (auto &q : bt.reqs) {
@@ -340,6 +350,14 @@ static void completer_loop(srv_t s)
             const double t = now_s();
             for (auto &bt : done) {
                 cudaEventDestroy(bt.ev);
+                if (bt.pin >= 0) {
+                    // a pass kernel gave up on a bounded wait: the batch's results are incomplete
+                    if (s->status_pin[bt.pin] != 0) {
+                        for (auto &q : bt.reqs) q->res.status = (conv_status)s->status_pin[bt.pin];
+                        cudaMemsetAsync(bt.cp->plan->dev_err, 0, sizeof(int), bt.cp->stream);
+                    }
+                    s->free_pins.push_back(bt.pin);
+                }
                 for (auto &q : bt.reqs) finish(s, q, q->res.status, t);
             }
             if (!done.empty()) {
@@ -404,6 +422,12 @@ conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch
     s->batch_max = conv_batch_max;
     s->ls_workers = ls_workers;
     cudaGetDevice(&s->device);
+    if (cudaHostAlloc(&s->status_pin, (size_t)(max_inflight + 1) * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return fail(CONV_ENOMEM, "pinned status slots");
+    }
+    for (int i = max_inflight; i >= 0; --i) s->free_pins.push_back(i);
     s->dispatcher = std::thread(dispatcher_loop, s);
     s->completer = std::thread(completer_loop, s);
     for (int i = 0; i < ls_workers; ++i) s->workers.emplace_back(ls_worker, s);
@@ -483,6 +507,7 @@ void srv_destroy(srv_t s)
         cudaFree(kv.second->stage_in);
         cudaFree(kv.second->stage_out);
     }
+    cudaFreeHost(s->status_pin);
     delete s;
 }
 

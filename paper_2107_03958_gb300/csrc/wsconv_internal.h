@@ -33,18 +33,27 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
                          double are, double aim, double beta, void *ws, cudaStream_t st);
 template <typename T, int E, bool TWS> conv_status set_attrs(int smem);
 template <typename T, int E, bool TWS> int blocks_per_sm(int threads, size_t smem);
-template <typename T, int E, int ED, bool TWS>
+template <typename T, int E, int ED>
 conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
                       double aim, double beta, void *ws, cudaStream_t st);
 template <typename T, int E, int ED, bool TWS> conv_status set_attrs_fused(int smem);
 template <typename T, int E, int ED, bool TWS> int blocks_per_sm_fused(int threads, size_t smem);
 
 // Launch shape of one pass family (rows or columns).
+// Per-pass launch options (bits): twiddle table in shared memory, prefetch of the next work item
+// (fused passes), one transform per CTA instead of the most that fit.
+enum { CFG_TWS = 1, CFG_PF = 2, CFG_ONE = 4 };
+// A launch configuration: {E, fused passes, options of pass 1, of pass 2, of pass 3}.  Unfused
+// passes share pass 1's twiddle option.
+typedef std::array<int, 5> Candidate;
+
 struct LaunchShape {
     int tpt;       // threads per transform
     int groups;    // transforms per CTA
     size_t smem;   // dynamic shared memory bytes
     int max_ctas;  // persistent grid size (CTAs resident at once)
+    int stage;     // fused passes: elements of each group's prefetch staging area (0: no prefetch)
+    bool tws;      // twiddle table in shared memory
 };
 
 }  // namespace wsc
@@ -60,6 +69,7 @@ struct conv_plan_s {
     conv_io io;
     int batch_max;
     bool complex_ghat;
+    bool r2c_split = false;  // R2C with complex ghat on the split pipeline (fused passes)
     int device;
     cudaStream_t setup_stream = nullptr;  // private stream for plan-time device work
     int elems;  // complex elements per thread in the transform kernels
@@ -68,6 +78,7 @@ struct conv_plan_s {
     int ed = 0; // fused: 16 * first radix + last radix
     wsc::FFTDesc fft;
     wsc::FFTDesc *fft_dev = nullptr;  // device copy read by the pass kernels
+    int *dev_err = nullptr;           // device status word, in the stage-table allocation
     // FP64 moment quadrant [k2][k1], k1, k2 <= Mb/2: real or complex (ghat_bytes)
     double *ghat_paper = nullptr;
     // FP64 multiplier of the passes, quadrant [k2][k1], k1, k2 < h: the moments (aliases ghat_paper)

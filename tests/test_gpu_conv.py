@@ -83,6 +83,11 @@ CASES = [
     (15, 2, "log", "r2r"),  # odd n: the last row pair is ragged (M = 30: generic radix-5 path)
     (9, 2, "pow-1", "r2r"),  # M = 18 = 2 * 3 * 3: generic path
     (3, 4, "log", "r2r"), (4, 3, "log", "c2c"), (2, 3, "pow-1", "r2c"),  # tiny transforms
+    # R2C with the complex Helmholtz multiplier: the split pipeline (row pairs, one forward and two
+    # inverse column transforms, packed inverse rows) wherever its fused passes exist
+    (256, 3, "helm20", "r2c"), (15, 2, "helm20", "r2c"),
+    (9, 8, "helm20", "r2c"),  # M = 72, h n = 333 odd: the second spectrum array is realigned
+    (27, 4, "helm20", "r2c"),  # M = 108 = 4 * 3^3: FP64 E = 12 fused passes, h n odd
 ]
 
 
@@ -101,6 +106,7 @@ def test_conv_matches_oracle(n, period, name, io, prec, compact):
         u = u + 1j * rng.standard_normal((B, n, n))
     ut = torch.tensor(u, dtype=plan.in_dtype(), device="cuda")
     out = plan.apply(ut).cpu().numpy()
+    plan.device_status()
     ref = _oracle_conv(u, plan, kw)
     if io == "r2r":
         assert np.max(np.abs(ref.imag)) <= 1e-12 * np.max(np.abs(ref))
@@ -181,6 +187,65 @@ def test_invalid_arguments_are_reported():
         plan.apply(u)  # batch > batch_max without a workspace
     with pytest.raises(ConvError, match="EINVAL"):
         plan.apply(u[0], out=u[0])  # aliasing
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_caller_workspace_r2c_split_and_alignment(prec):
+    """R2C Helmholtz through a caller's workspace of exactly conv_workspace_size bytes (odd h n: the
+    second spectrum array starts one element late) equals the plan's own workspace; misaligned
+    workspaces and arrays are rejected."""
+    from paper_2107_03958_gb300._native import ConvError
+    n, B = 9, 3
+    plan = ConvPlan("helmholtz", n=n, period=8, precision=prec, io="r2c", batch_max=B, kappa=20.0)
+    u = torch.tensor(np.random.default_rng(2).standard_normal((B, n, n)), dtype=plan.real_dtype, device="cuda")
+    ws = torch.empty(plan.workspace_bytes(B) + 64, dtype=torch.uint8, device="cuda")
+    out = plan.apply(u, workspace=ws[16:16 + plan.workspace_bytes(B)])
+    assert torch.equal(out, plan.apply(u))
+    with pytest.raises(ConvError, match="EINVAL"):
+        plan.apply(u, workspace=ws[8:8 + plan.workspace_bytes(B)])
+    import ctypes
+    from paper_2107_03958_gb300 import _native as N
+    raw = torch.empty(B * n * n * u.element_size() + 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ConvError, match="EINVAL"):  # u one byte past an element boundary
+        N.check(plan._lib.conv_apply(plan._h, ctypes.c_void_p(raw.data_ptr() + 1), None,
+                                     ctypes.c_void_p(out.data_ptr()), B, None, None))
+    plan.device_status()
+
+
+@pytest.mark.parametrize("name,io", [("log", "r2r"), ("helm20", "r2c")])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autotuned_plan_matches_oracle(name, io, prec):
+    """The autotuner (per-pass options chosen by timing) changes launch shapes only: its plan still
+    matches the oracle."""
+    n, B = 256, 4
+    kw = KERNELS[name]
+    plan = ConvPlan(n=n, period=3, precision=prec, io=io, batch_max=B, compact=True, autotune=True, **kw)
+    u = inputs.bump_sums(n, B, seed=21)
+    out = plan.apply(torch.tensor(u, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+    plan.device_status()
+    ref = _oracle_conv(u, plan, kw)
+    if io == "r2r":
+        ref = ref.real
+    for i in range(B):
+        assert _relerr(ref[i], out[i]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("compact", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_helmholtz_r2c(prec, compact):
+    """n = 4096, b = 3, batch 16, Helmholtz kappa = 20 (the benchmark's R2C line): densities 0 and
+    13 against the oracle's full FFT convolution."""
+    n, B = 4096, 16
+    kw = KERNELS["helm20"]
+    plan = ConvPlan(n=n, period=3, precision=prec, io="r2c", batch_max=B, compact=compact, **kw)
+    u = inputs.bump_sums(n, B)
+    out = plan.apply(torch.tensor(u, dtype=plan.real_dtype, device="cuda"))
+    plan.device_status()
+    kind, okw = _oracle_kw(kw)
+    g = O.ghat_full(kind, plan.M, plan.b, plan.a, **okw)
+    for i in (0, 13):
+        ref = O.conv(u[i], plan.M, g)
+        assert _relerr(ref, out[i].cpu().numpy()) <= TOL[prec]
 
 
 @pytest.mark.parametrize("compact", [False, True])
