@@ -39,9 +39,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--no-extras", action="store_true", help="headline only (no FP64/n=2048/LS legs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--only", choices=["r2r", "r2r64", "c2c"], default=None,
+    ap.add_argument("--only", choices=["r2r", "r2r64", "r2c", "c2c"], default=None,
                     help="profiling case: warmup + steps applies of one plan (log kernel R2R FP32, "
-                         "R2R FP64, or Helmholtz C2C FP32), no other legs")
+                         "R2R FP64, Helmholtz R2C or C2C FP32), no other legs")
     return ap.parse_args()
 
 
@@ -342,10 +342,11 @@ def profile_case(args):
     from paper_2107_03958_gb300.api import ConvPlan
     prec = "fp64" if args.only == "r2r64" else "fp32"
     compact = os.environ.get("BENCH_PERIOD_B", "0") != "1"
-    if args.only == "c2c":
-        plan = ConvPlan("helmholtz", n=args.n, period=3, precision=prec, io="c2c",
+    if args.only in ("c2c", "r2c"):
+        plan = ConvPlan("helmholtz", n=args.n, period=3, precision=prec, io=args.only,
                         batch_max=args.batch, kappa=20.0, compact=compact)
-        u = torch.tensor(inputs.bump_sums(args.n, args.batch), dtype=plan.cplx_dtype, device="cuda")
+        dt = plan.cplx_dtype if args.only == "c2c" else plan.real_dtype
+        u = torch.tensor(inputs.bump_sums(args.n, args.batch), dtype=dt, device="cuda")
     else:
         plan = ConvPlan("log", n=args.n, period=3, precision=prec, io="r2r", batch_max=args.batch,
                         compact=compact)
