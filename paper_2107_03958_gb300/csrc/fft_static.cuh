@@ -1,0 +1,152 @@
+// fft_static.cuh -- the fused Stockham transform of fft_fused.cuh for a length fixed at compile
+// time, L = 2^L2, with the radix sequence of the runtime plan (radix-8 stages, then one radix-4
+// or radix-2 stage for the remaining factor), so the twiddle table is the same.
+//
+// With R, Ns and the thread count known, every shared-memory, twiddle and global index of a
+// stage is a per-thread base plus a compile-time offset:
+//   inputs   e = j + q L/R, j = lt + b tpt:   pidx(e) = pidx(lt) + c + (c >> PS),  c = b tpt + q L/R;
+//   outputs  o = (j / Ns) R Ns + (j mod Ns) + p Ns, with j / Ns and j mod Ns split into a thread
+//            part (jq0, k0) and a constant (cj, ck) of butterfly b, and pidx(o) = T0 + C(b) + C(p),
+//            T0 from (jq0, k0), the constants from the padding period PAD = 2^PS (tpt, and so
+//            b tpt, is a multiple of PAD).
+// The runtime path recomputes these per element (shifts, magic-number divisions, stage-table
+// loads); here each stage computes a handful of per-thread bases and the rest folds into the
+// load/store immediates.
+#pragma once
+#include "fft_fused.cuh"
+
+namespace wsc {
+
+__host__ __device__ constexpr int tw_blocks_c(int R) { return R == 2 ? 1 : (R <= 4 ? 2 : 3); }
+
+// Stage structure of a length-2^L2 transform.
+template <int L2> struct Pow2Stages {
+    static constexpr int L = 1 << L2;
+    static constexpr int N8 = L2 / 3, REM = L2 % 3;
+    static constexpr int NST = N8 + (REM ? 1 : 0);
+    __host__ __device__ static constexpr int lR(int s) { return s < N8 ? 3 : REM; }
+    __host__ __device__ static constexpr int R(int s) { return 1 << lR(s); }
+    __host__ __device__ static constexpr int lNs(int s)
+    {
+        int v = 0;
+        for (int i = 0; i < s; ++i) v += lR(i);
+        return v;
+    }
+    __host__ __device__ static constexpr int toff(int s)
+    {
+        int o = 0;
+        for (int i = 0; i < s; ++i) o += tw_blocks_c(R(i)) << lNs(i);
+        return o;
+    }
+};
+
+// One radix-R stage S; every thread owns E/R butterflies j = lt + b tpt.
+template <typename T, int E, int L2, int S, bool INV, bool TWS, class Src, class Dst>
+__device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw, int lt,
+                                       const Src &src, const Dst &dst)
+{
+    typedef typename cvec<T>::t V;
+    typedef Pow2Stages<L2> P;
+    constexpr int R = P::R(S), lNs = P::lNs(S), Ns = 1 << lNs, RN = R * Ns;
+    constexpr int TPT = P::L / E, NB = E / R, NBF = NB * TPT;
+    constexpr int PS = pad_shift<T>::v, PAD = 1 << PS;
+    static_assert(E % R == 0, "radix must divide the elements per thread");
+    static_assert(TPT % PAD == 0, "threads per transform must be a multiple of the padding period");
+    constexpr bool SRC_SMEM = std::is_same<Src, FromSmem>::value;
+    constexpr bool DST_SMEM = writes_smem<Dst>::value;
+    // per-thread bases of this stage
+    const int pl = lt + (lt >> PS);
+    int k0, jq0;
+    if constexpr (Ns <= TPT) {
+        k0 = lt & (Ns - 1);
+        jq0 = lt >> lNs;
+    } else {
+        k0 = lt;
+        jq0 = 0;
+    }
+    int T0;
+    if constexpr (RN <= PAD) {
+        const int x = jq0 * RN;
+        T0 = x + (x >> PS) + k0;
+    } else if constexpr (Ns < PAD) {
+        T0 = jq0 * (RN + RN / PAD) + k0;
+    } else {
+        T0 = jq0 * (RN + RN / PAD) + k0 + (k0 >> PS);
+    }
+    const int O0 = jq0 * RN + k0;
+    V v[NB][R];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int c = b * TPT + q * NBF;
+            if constexpr (SRC_SMEM) v[b][q] = buf[pl + c + (c >> PS)];
+            else v[b][q] = src(lt + c);
+        }
+    }
+    if constexpr (SRC_SMEM && DST_SMEM) __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int cb = b * TPT, ck = cb & (Ns - 1), cj = cb >> lNs;
+        if constexpr (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw + P::toff(S) + ck, Ns, k0);
+        dftR<R, INV>(v[b]);
+        const int Cb = RN <= PAD ? cj * RN + ((cj * RN) >> PS) : cj * (RN + RN / PAD) + ck + (ck >> PS);
+#pragma unroll
+        for (int p = 0; p < R; ++p) {
+            const int Cp = RN <= PAD ? p * Ns : (Ns < PAD ? p * Ns + ((p * Ns) >> PS) : p * (Ns + Ns / PAD));
+            const int o = O0 + cj * RN + ck + p * Ns;
+            if constexpr (std::is_same<Dst, ToSmem>::value) {
+                buf[T0 + Cb + Cp] = v[b][p];
+            } else if constexpr (DST_SMEM) {
+                V x = v[b][p];
+                dst.f(o, x);
+                buf[T0 + Cb + Cp] = x;
+            } else {
+                dst(o, v[b][p]);
+            }
+        }
+        asm volatile("" ::: "memory");
+    }
+    if constexpr (DST_SMEM) __syncthreads();
+}
+
+template <typename T, int E, int L2, bool INV, bool TWS, class Src, class Dst, class After0, int S>
+__device__ __forceinline__ void fft_static_from(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw,
+                                                int lt, const Src &src, const Dst &dst, const After0 &after0)
+{
+    constexpr int NST = Pow2Stages<L2>::NST;
+    static_assert(NST >= 2, "at least two stages");
+    // keep each stage's per-thread bases from being hoisted to the kernel start (register pressure)
+    int lt_ = lt;
+    asm volatile("" : "+r"(lt_));
+    if constexpr (S == 0) {
+        sstage<T, E, L2, 0, INV, TWS>(buf, tw, lt_, src, ToSmem{});
+        after0();
+    } else if constexpr (S == NST - 1) {
+        sstage<T, E, L2, S, INV, TWS>(buf, tw, lt_, FromSmem{}, dst);
+    } else {
+        sstage<T, E, L2, S, INV, TWS>(buf, tw, lt_, FromSmem{}, ToSmem{});
+    }
+    if constexpr (S + 1 < NST) fft_static_from<T, E, L2, INV, TWS, Src, Dst, After0, S + 1>(buf, tw, lt, src, dst, after0);
+}
+
+// Whole transform of length 2^L2; same contract as fft_fused.
+template <typename T, int E, int L2, bool INV, bool TWS, class Src, class Dst, class After0>
+__device__ __forceinline__ void fft_static(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw, int lt,
+                                           const Src &src, const Dst &dst, const After0 &after0)
+{
+    fft_static_from<T, E, L2, INV, TWS, Src, Dst, After0, 0>(buf, tw, lt, src, dst, after0);
+}
+
+// The pass kernels' transform: ED >= 1000 selects the static path for length 2^(ED - 1000);
+// otherwise the runtime-descriptor path of fft_fused with edge radices ED.
+template <typename T, int E, int ED, bool INV, bool TWS, class Src, class Dst, class After0 = NoHook>
+__device__ __forceinline__ void fft_any(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
+                                        const typename cvec<T>::t *__restrict__ tw, int lt, int tpt, const Src &src,
+                                        const Dst &dst, const After0 &after0 = After0{})
+{
+    if constexpr (ED >= 1000) fft_static<T, E, ED - 1000, INV, TWS>(buf, tw, lt, src, dst, after0);
+    else fft_fused<T, E, ED, INV, TWS>(buf, P, tw, lt, tpt, src, dst, after0);
+}
+
+}  // namespace wsc

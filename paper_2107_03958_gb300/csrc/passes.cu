@@ -178,6 +178,18 @@ static int generic_tpt(const FFTDesc &P)
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 130; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 130; constexpr bool W_ = false; CALL; } \
         } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1011) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1011; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 1011; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1012) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1012; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 1012; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1013) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1013; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 1013; constexpr bool W_ = false; CALL; } \
+        } \
         else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 132) { \
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 132; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 132; constexpr bool W_ = false; CALL; } \
@@ -205,6 +217,9 @@ static int generic_tpt(const FFTDesc &P)
     } while (0)
 
 static const int kFusedSets[][3] = {
+    {1, 16, 1011},  // static power-of-two lengths 2^11, 2^12, 2^13
+    {1, 16, 1012},
+    {1, 16, 1013},
     {1, 24, 131},
     {1, 16, 136},
     {1, 16, 130},
@@ -216,11 +231,20 @@ static const int kFusedSets[][3] = {
     {0, 8, 132},
 };
 
-// Fused passes exist for these (precision, E, first radix, last radix); everything else runs the
-// plain passes.
-static int fused_edges(conv_precision prec, int E, const FFTDesc &d)
+// Fused passes exist for these (precision, E, ED): ED = 16 first radix + last radix with the
+// stage structure read from the runtime descriptor, or ED = 1000 + log2 L with the whole stage
+// structure fixed at compile time (fft_static.cuh); everything else runs the plain passes.
+// static_pref = 0 skips the compile-time lengths.
+static int fused_edges(conv_precision prec, int E, const FFTDesc &d, int static_pref = 1)
 {
     if (d.nst < 2) return 0;
+    // a power-of-two length with a compile-time instantiation: 1000 + log2 L
+    if (static_pref && (d.L & (d.L - 1)) == 0) {
+        int l2 = 0;
+        while ((1 << l2) < d.L) ++l2;
+        for (const auto &f : kFusedSets)
+            if ((f[0] == 1) == (prec == CONV_P_FP32) && f[1] == E && f[2] == 1000 + l2) return 1000 + l2;
+    }
     const int ed = 16 * d.R[0] + d.R[d.nst - 1];
     for (const auto &f : kFusedSets)
         if ((f[0] == 1) == (prec == CONV_P_FP32) && f[1] == E && f[2] == ed) return ed;
@@ -268,7 +292,21 @@ static int max_groups(int maxT, int tpt, size_t twb, size_t per, size_t stage_by
     return G;
 }
 
-// One launch configuration c = {E elements per thread, fused passes (1 when eligible, 0 never),
+// Default options per pass (CFG_DEFAULT in a candidate), from FP32 measurements at n = 4096,
+// batch 16.  Runtime stage structure: prefetch pays in the row passes of the R2R and split R2C
+// pipelines (contiguous row loads, strided spectrum gathers) and not in their column passes or in
+// the C2C passes, where it costs a transform per CTA.  Compile-time lengths (one transform per
+// CTA, 128 registers): prefetch everywhere, and the column pass reads its twiddles through L1.
+static int default_options(const conv_plan_s *p, int ed, int pass)
+{
+    const bool rows_pf = p->io == CONV_IO_R2R || (p->io == CONV_IO_R2C && p->complex_ghat);
+    if (ed >= 1000) return pass == 0 ? CFG_PF : pass == 1 ? CFG_PF : (rows_pf ? CFG_TWS | CFG_PF : CFG_TWS);
+    if (!rows_pf) return pass == 2 ? 0 : CFG_TWS;
+    return pass == 1 ? CFG_TWS : CFG_TWS | CFG_PF;
+}
+
+// One launch configuration c = {E elements per thread, fused passes (1 when eligible, preferring a
+// compile-time length; 2 when eligible, runtime stage structure; 0 never),
 // options of pass 1, 2, 3 (CFG_* bits: shared-memory twiddles when they fit, prefetch when it
 // fits (fused only), one transform per CTA)}.  An option that does not fit is dropped (twiddles
 // first, then prefetch).  Returns false if the configuration does not exist for this plan.
@@ -280,7 +318,7 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
     const size_t per = (size_t)(p->prec == CONV_P_FP64 ? padded_len<double>(M) : padded_len<float>(M)) * esz;
     FFTDesc d;
     if (!factorize(M, E, d)) return false;
-    const int maxT = max_threads(p->prec, E);
+    int maxT = max_threads(p->prec, E);
     int tpt;
     if (E > 0) {
         if (M % E) return false;
@@ -289,8 +327,12 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         tpt = generic_tpt(d);
     }
     if (tpt > maxT) return false;
-    const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d) : 0;
+    const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d, fused_pref == 1) : 0;
     const bool fused = ed != 0;
+    if (ed >= 1000) {  // the compile-time-length kernels' launch bound
+        maxT = std::min(maxT, WSC_STATIC_MAXT);
+        if (tpt > maxT) return false;
+    }
     const size_t twb = (size_t)d.tw_len * esz;
     // staging: a row pair / row / column (n elements V) for passes 1 and 2; a row's spectrum for
     // pass 3 (R2R: both spectra of a row pair for k <= M/2; C2C: all M values)
@@ -324,15 +366,17 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         S.max_ctas = bps * sms;
         return true;
     };
+    int opt[3];
+    for (int k = 0; k < 3; ++k) opt[k] = c[2 + k] == CFG_DEFAULT ? default_options(p, ed, k) : c[2 + k];
     LaunchShape R, C, I;
-    if (!shape(c[2], sb12, 1, R)) return false;
+    if (!shape(opt[0], sb12, 1, R)) return false;
     // R2C with complex ghat runs the split pipeline when its pass 2 fits two buffers per CTA;
     // otherwise the C2C layout
     bool split = false;
     if (fused) {
-        split = p->io == CONV_IO_R2C && p->complex_ghat && shape(c[3], sb12, 2, C);
+        split = p->io == CONV_IO_R2C && p->complex_ghat && shape(opt[1], sb12, 2, C);
         const size_t sbi = split ? 2 * (size_t)p->h * esz : sb3;
-        if ((!split && !shape(c[3], sb12, 1, C)) || !shape(c[4], sbi, 1, I)) return false;
+        if ((!split && !shape(opt[1], sb12, 1, C)) || !shape(opt[2], sbi, 1, I)) return false;
     } else {
         C = I = R;  // the plain kernels share one twiddle option and shape
     }
@@ -348,15 +392,6 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
     return true;
 }
 
-// Default options per pass, from FP32 measurements at n = 4096, batch 16: prefetch pays in the
-// row passes of the R2R and split R2C pipelines (contiguous row loads, strided spectrum gathers)
-// and not in their column passes or in the C2C passes, where it costs a transform per CTA.
-static Candidate default_candidate(const conv_plan_s *p, int E)
-{
-    if (p->io == CONV_IO_R2R || (p->io == CONV_IO_R2C && p->complex_ghat))
-        return {E, 1, CFG_TWS | CFG_PF, CFG_TWS, CFG_TWS | CFG_PF};
-    return {E, 1, CFG_TWS, CFG_TWS, 0};
-}
 
 static conv_status device_limits(conv_plan_s *p, int &smem_optin, int &sms)
 {
@@ -399,12 +434,11 @@ conv_status select_transform(conv_plan_s *p)
     if (const char *v = getenv("WSCONV_CFG")) sscanf(v, "%d,%d,%d", &cfg3[0], &cfg3[1], &cfg3[2]);
     for (int i = 0; i < ncand; ++i) {
         if (force_e >= 0 && cand[i] != force_e) continue;
-        Candidate c = default_candidate(p, cand[i]);
-        c[1] = env("WSCONV_FUSED", 1);
+        Candidate c = {cand[i], env("WSCONV_FUSED", 1), CFG_DEFAULT, CFG_DEFAULT, CFG_DEFAULT};
         for (int k = 0; k < 3; ++k) {
             int &o = c[2 + k];
+            if (!tws || pf >= 0 || one) o = CFG_TWS;  // an override starts from twiddles in shared memory
             if (!tws) o &= ~CFG_TWS;
-            if (pf == 0) o &= ~CFG_PF;
             if (pf == 1) o |= CFG_PF;
             if (one) o |= CFG_ONE;
             if (cfg3[k] >= 0) o = cfg3[k];
@@ -428,13 +462,16 @@ std::vector<std::vector<Candidate>> transform_families(conv_plan_s *p)
     conv_plan_s probe = *p;
     probe.tev_used.clear();
     probe.tev_free.clear();
-    for (int i = 0; i < ncand; ++i)
-        for (int fu = 1; fu >= 0; --fu) {
+    for (int i = 0; i < ncand; ++i) {
+        int ed_static = -1;
+        for (int fu : {1, 2, 0}) {
             std::vector<Candidate> fam;
             std::vector<std::array<int, 9>> seen;  // distinct (tws, staged, groups) of the three passes
             for (int cfg = 0; cfg < (fu ? 8 : 2); ++cfg) {
                 const Candidate c = {cand[i], fu, cfg, cfg, cfg};
-                if (!configure(&probe, c, smem_optin, sms) || (int)probe.fused != fu) continue;
+                if (!configure(&probe, c, smem_optin, sms) || probe.fused != (fu != 0)) continue;
+                if (fu == 1) ed_static = probe.ed;
+                if (fu == 2 && probe.ed == ed_static) break;  // no compile-time length: same as fu = 1
                 const std::array<int, 9> key = {probe.rows.tws, probe.rows.stage > 0, probe.rows.groups,
                                                 probe.cols.tws, probe.cols.stage > 0, probe.cols.groups,
                                                 probe.inv.tws,  probe.inv.stage > 0,  probe.inv.groups};
@@ -446,6 +483,7 @@ std::vector<std::vector<Candidate>> transform_families(conv_plan_s *p)
             }
             if (!fam.empty()) out.push_back(fam);
         }
+    }
     return out;
 }
 

@@ -10,10 +10,12 @@
 #include <type_traits>
 
 #include "async_copy.cuh"
-#include "fft_fused.cuh"
+#include "fft_static.cuh"
 #include "passes.cuh"
 
 namespace wsc {
+
+#define WSC_LBF(T, E, ED) __launch_bounds__(maxt_fused<T, E, ED>::v, 1)
 
 // ---------------------------------------------------------------------------- prefetch
 // With a.pf set, each thread group fetches the input of its next work item (unit + stride) into
@@ -96,7 +98,7 @@ __device__ __forceinline__ void store_pair(typename cvec<T>::t *p, typename cvec
 // Pass 1.  Staging: rows j1, j1 + 1 of u (adjacent in memory), n T each; one bulk copy
 // (a.pf requires n sizeof(T) to be a multiple of 16 and u 16-byte aligned).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -142,7 +144,7 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
             }
             return cmk<V>(x, y);
         };
-        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
         if (valid) {
             V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * h * n;
             for (int k = lt; k < h; k += a.tpt) {
@@ -159,7 +161,7 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_fwd(const PassArgs<T> a)
 // Pass 2.  Staging: the column's n spectrum values (contiguous in W); one bulk copy (a.pf
 // requires n sizeof(V) to be a multiple of 16 and W 16-byte aligned).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LB(T, E) kf_r2r_cols(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -198,11 +200,11 @@ __global__ void WSC_LB(T, E) kf_r2r_cols(const PassArgs<T> a)
             const int k1 = o <= M / 2 ? o : M - o;
             x = cscale(x, __ldg(&gc[k1]));
         });
-        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -210,7 +212,7 @@ __global__ void WSC_LB(T, E) kf_r2r_cols(const PassArgs<T> a)
 // Pass 3.  Staging: the row pair's spectra W[k][j1], W[k][j1+1] for k <= M/2, side by side;
 // gathered by cp.async (a.pf requires W 16-byte aligned and, in FP32, n even).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -277,7 +279,7 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
             oa[o] = ra;
             if (has2) oa[n + o] = rb;
         };
-        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -296,7 +298,7 @@ __global__ void WSC_LB(T, E) kf_r2r_rows_inv(const PassArgs<T> a)
 // Pass 2.  Two transform buffers per group: Re ghat's product transforms in the first, Im ghat's
 // in the second.  Staging: the column of W (one bulk copy, as in the R2R pass 2).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LB(T, E) kf_r2c_cols(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -339,8 +341,8 @@ __global__ void WSC_LB(T, E) kf_r2c_cols(const PassArgs<T> a)
             bim[pidx<T>(o)] = cscale(x, gk.y);
             x = cscale(x, gk.x);
         });
-        fft_fused<T, E, ED, false, TWS>(bre, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
-        fft_fused<T, E, ED, true, TWS>(bre, a.P, twp, lt, a.tpt, FromSmem{}, ToSmem{});
+        fft_any<T, E, ED, false, TWS>(bre, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, true, TWS>(bre, a.P, twp, lt, a.tpt, FromSmem{}, ToSmem{});
         V *cout = reinterpret_cast<V *>(a.out) + 2 * co;
         auto dst = [&](int o, V xi) {
             if (!valid || o >= n) return;
@@ -354,7 +356,7 @@ __global__ void WSC_LB(T, E) kf_r2c_cols(const PassArgs<T> a)
             cout[2 * o] = xr;
             cout[2 * o + 1] = xi;
         };
-        fft_fused<T, E, ED, true, TWS>(bim, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS>(bim, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -362,7 +364,7 @@ __global__ void WSC_LB(T, E) kf_r2c_cols(const PassArgs<T> a)
 // Pass 3.  Staging: the row's pairs W2[k][j1] = (Wr, Wi), k <= M/2, gathered by cp.async
 // (16-byte pieces; a.pf requires W2 16-byte aligned).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LB(T, E) kf_r2c_rows_inv(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2c_rows_inv(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -414,7 +416,7 @@ __global__ void WSC_LB(T, E) kf_r2c_rows_inv(const PassArgs<T> a)
             if (a.beta != (T)0) z.x += a.beta * ua[o];
             o_[o] = z;
         };
-        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -424,7 +426,7 @@ __global__ void WSC_LB(T, E) kf_r2c_rows_inv(const PassArgs<T> a)
 // Pass 1.  Staging: row j1 of the input (n T real or n V complex); one bulk copy (a.pf requires
 // its byte length to be a multiple of 16 and the input 16-byte aligned).
 template <typename T, int E, int ED, bool TWS, bool IN_REAL>
-__global__ void WSC_LB(T, E) kf_c2c_rows_fwd(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_c2c_rows_fwd(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     typedef typename std::conditional<IN_REAL, T, V>::type I;
@@ -465,14 +467,14 @@ __global__ void WSC_LB(T, E) kf_c2c_rows_fwd(const PassArgs<T> a)
         auto dst = [&](int o, V z) {
             if (valid) Wb[(size_t)o * n + j1] = z;
         };
-        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
         __syncthreads();
     }
 }
 
 // Pass 2.  Staging: the column's n spectrum values; one bulk copy (as in the R2R pass 2).
 template <typename T, int E, int ED, bool TWS, bool CG>
-__global__ void WSC_LB(T, E) kf_c2c_cols(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_c2c_cols(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -511,11 +513,11 @@ __global__ void WSC_LB(T, E) kf_c2c_cols(const PassArgs<T> a)
             if (CG) x = cmul(x, __ldg(reinterpret_cast<const V *>(a.ghat) + (size_t)k2q * h + k1));
             else x = cscale(x, __ldg(reinterpret_cast<const T *>(a.ghat) + (size_t)k2q * h + k1));
         });
-        fft_fused<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -523,7 +525,7 @@ __global__ void WSC_LB(T, E) kf_c2c_cols(const PassArgs<T> a)
 // Pass 3.  Staging: the row's spectrum W[i][j1], i < M, one element per i; gathered by cp.async
 // (8-byte pieces in FP32, 16-byte in FP64; a.pf requires W aligned to the element size).
 template <typename T, int E, int ED, bool TWS, bool IN_REAL>
-__global__ void WSC_LB(T, E) kf_c2c_rows_inv(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_c2c_rows_inv(const PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -567,7 +569,7 @@ __global__ void WSC_LB(T, E) kf_c2c_rows_inv(const PassArgs<T> a)
             }
             o_[o] = z;
         };
-        fft_fused<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();

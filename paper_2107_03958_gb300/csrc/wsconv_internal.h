@@ -27,6 +27,12 @@ conv_status cuda_fail(cudaError_t e, const char *what);
 // Threads-per-CTA bound of the pass kernels for E complex elements per thread (E = 0: generic
 // guarded stages): keeps the E values in registers.
 template <typename T, int E> struct maxt { static const int v = (E == 0 || (int)(2 * sizeof(T) * E) > 160) ? 512 : 1024; };
+// Fused passes: the compile-time-length transforms (ED >= 1000) unroll every stage into straight-
+// line code and get 128 registers per thread (at most 512 threads per CTA).
+#define WSC_STATIC_MAXT 512
+template <typename T, int E, int ED> struct maxt_fused {
+    static const int v = ED >= 1000 ? WSC_STATIC_MAXT : maxt<T, E>::v;
+};
 
 template <typename T, int E, bool TWS>
 conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
@@ -42,7 +48,7 @@ template <typename T, int E, int ED, bool TWS> int blocks_per_sm_fused(int threa
 // Launch shape of one pass family (rows or columns).
 // Per-pass launch options (bits): twiddle table in shared memory, prefetch of the next work item
 // (fused passes), one transform per CTA instead of the most that fit.
-enum { CFG_TWS = 1, CFG_PF = 2, CFG_ONE = 4 };
+enum { CFG_TWS = 1, CFG_PF = 2, CFG_ONE = 4, CFG_DEFAULT = -1 };
 // A launch configuration: {E, fused passes, options of pass 1, of pass 2, of pass 3}.  Unfused
 // passes share pass 1's twiddle option.
 typedef std::array<int, 5> Candidate;

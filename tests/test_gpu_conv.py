@@ -230,6 +230,33 @@ def test_autotuned_plan_matches_oracle(name, io, prec):
         assert _relerr(ref[i], out[i]) <= TOL[prec]
 
 
+@pytest.mark.parametrize("io", ["r2r", "r2c", "c2c"])
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_compile_time_lengths_match_oracle_and_runtime_stages(n, io, monkeypatch):
+    """FP32 compact embedding, L = 2n = 2^11, 2^12: the transforms whose stage structure is fixed at
+    compile time match the oracle and the runtime-descriptor transforms of the same plan."""
+    kw = KERNELS["helm20" if io != "r2r" else "pow-1"]
+    B = 2
+    rng = np.random.default_rng(n + len(io))
+    u = inputs.bump_sums(n, B, seed=n)
+    if io == "c2c":
+        u = u + 1j * rng.standard_normal((B, n, n)) * 0.1
+    outs = []
+    for fused in ("1", "2"):
+        monkeypatch.setenv("WSCONV_FUSED", fused)
+        plan = ConvPlan(n=n, period=3, precision="fp32", io=io, batch_max=B, compact=True, **kw)
+        info = plan.info
+        assert info.fused == 1 and info.static_log2 == (int(np.log2(2 * n)) if fused == "1" else 0)
+        outs.append(plan.apply(torch.tensor(u, dtype=plan.in_dtype(), device="cuda")).cpu().numpy())
+        plan.device_status()
+    ref = _oracle_conv(u, plan, kw)
+    if io == "r2r":
+        ref = ref.real
+    for i in range(B):
+        assert _relerr(ref[i], outs[0][i]) <= TOL["fp32"]
+        assert _relerr(outs[1][i], outs[0][i]) <= 1e-6
+
+
 @pytest.mark.parametrize("compact", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_full_size_helmholtz_r2c(prec, compact):
