@@ -122,17 +122,62 @@ template <bool INV, typename V> __device__ __forceinline__ void dft8(V *x) {
     x[7] = csub(e[3], o3);
 }
 
+// x * (a + i b) for a constant unit root, conjugated for the inverse transform
+template <bool INV, typename V> __device__ __forceinline__ V cmulc(V x, decltype(V::x) a, decltype(V::x) b)
+{
+    if (INV) b = -b;
+    return cmk<V>(x.x * a - x.y * b, x.x * b + x.y * a);
+}
+
+// 16 points as 4 x 4: length-4 transforms over n = r + 4t (t), twiddles w16^{r m}, length-4
+// transforms over r; X[m + 4 s] = sum_r w4^{r s} w16^{r m} sum_t w4^{t m} x[r + 4t].
+template <bool INV, typename V> __device__ __forceinline__ void dft16(V *x) {
+    typedef decltype(V::x) T;
+    const T c = (T)0.9238795325112867561281831893967882;   // cos(pi/8)
+    const T s = (T)0.3826834323650897717284599840303989;   // sin(pi/8)
+    const T r2 = (T)0.7071067811865475244008443621048490;  // cos(pi/4)
+    V y[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        y[r][0] = x[r];
+        y[r][1] = x[r + 4];
+        y[r][2] = x[r + 8];
+        y[r][3] = x[r + 12];
+        dft4<INV>(y[r]);  // y[r][m], m = 0..3
+    }
+    // w16^{r m}: forward w16 = e^{-i pi/8}
+    y[1][1] = cmulc<INV>(y[1][1], c, -s);
+    y[1][2] = cmulc<INV>(y[1][2], r2, -r2);
+    y[1][3] = cmulc<INV>(y[1][3], s, -c);
+    y[2][1] = cmulc<INV>(y[2][1], r2, -r2);
+    y[2][2] = rot<INV>(y[2][2]);
+    y[2][3] = cmulc<INV>(y[2][3], -r2, -r2);
+    y[3][1] = cmulc<INV>(y[3][1], s, -c);
+    y[3][2] = cmulc<INV>(y[3][2], -r2, -r2);
+    y[3][3] = cmulc<INV>(y[3][3], -c, s);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        V z[4] = {y[0][m], y[1][m], y[2][m], y[3][m]};
+        dft4<INV>(z);
+        x[m] = z[0];
+        x[m + 4] = z[1];
+        x[m + 8] = z[2];
+        x[m + 12] = z[3];
+    }
+}
+
 template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x) {
     if (R == 2) dft2<INV>(x);
     else if (R == 3) dft3<INV>(x);
     else if (R == 4) dft4<INV>(x);
     else if (R == 5) dft5<INV>(x);
-    else dft8<INV>(x);
+    else if (R == 8) dft8<INV>(x);
+    else dft16<INV>(x);
 }
 
 // ---------------------------------------------------------------- twiddles
-// x[q] *= w^{qk}, q = 1..R-1, from the stage's block tab = [w^k | w^{2k} | w^{4k}] (k < Ns):
-// powers 1, 2, 4 are read; 3, 5, 6, 7 are products of two of them.
+// x[q] *= w^{qk}, q = 1..R-1, from the stage's block tab = [w^k | w^{2k} | w^{4k} | w^{8k}] (k < Ns;
+// only the blocks the radix needs): powers 1, 2, 4 (and 8) are read; the others are products.
 template <typename T, bool TWS>
 __device__ __forceinline__ typename cvec<T>::t tw_load(const typename cvec<T>::t *__restrict__ tw, int t)
 {
@@ -160,9 +205,22 @@ __device__ __forceinline__ void apply_twiddles(typename cvec<T>::t *x, const typ
     if (INV) w4.y = -w4.y;
     x[4] = cmul(x[4], w4);
     if constexpr (R == 5) return;
-    x[5] = cmul(x[5], cmul(w1, w4));
-    x[6] = cmul(x[6], cmul(w2, w4));
-    x[7] = cmul(x[7], cmul(w3, w4));
+    const V w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+    x[5] = cmul(x[5], w5);
+    x[6] = cmul(x[6], w6);
+    x[7] = cmul(x[7], w7);
+    if constexpr (R == 8) return;
+    // radix 16: a fourth block w^{8k}; powers 9..15 = (1..7) + 8
+    V w8 = tw_load<T, TWS>(tab, 3 * Ns + k);
+    if (INV) w8.y = -w8.y;
+    x[8] = cmul(x[8], w8);
+    x[9] = cmul(x[9], cmul(w1, w8));
+    x[10] = cmul(x[10], cmul(w2, w8));
+    x[11] = cmul(x[11], cmul(w3, w8));
+    x[12] = cmul(x[12], cmul(w4, w8));
+    x[13] = cmul(x[13], cmul(w5, w8));
+    x[14] = cmul(x[14], cmul(w6, w8));
+    x[15] = cmul(x[15], cmul(w7, w8));
 }
 
 // ---------------------------------------------------------------- one Stockham stage

@@ -1,6 +1,7 @@
 // fft_static.cuh -- the fused Stockham transform of fft_fused.cuh for a length fixed at compile
-// time, L = 2^L2, with the radix sequence of the runtime plan (radix-8 stages, then one radix-4
-// or radix-2 stage for the remaining factor), so the twiddle table is the same.
+// time, L = 2^L2, in radix-16 stages (and one radix-2, -4 or -8 stage for the remaining factor):
+// one shared-memory round trip per four bits, and no stage with Ns = 8, whose stride-8 stores
+// conflict in the padded layout.
 //
 // With R, Ns and the thread count known, every shared-memory, twiddle and global index of a
 // stage is a per-thread base plus a compile-time offset:
@@ -17,14 +18,15 @@
 
 namespace wsc {
 
-__host__ __device__ constexpr int tw_blocks_c(int R) { return R == 2 ? 1 : (R <= 4 ? 2 : 3); }
+__host__ __device__ constexpr int tw_blocks_c(int R) { return R == 2 ? 1 : (R <= 4 ? 2 : (R <= 8 ? 3 : 4)); }
 
-// Stage structure of a length-2^L2 transform.
+// Stage structure of a length-2^L2 transform: radix-16 stages, then one radix-2^(L2 mod 4) stage
+// (the host's factorize with radix16 set gives the same sequence and twiddle table).
 template <int L2> struct Pow2Stages {
     static constexpr int L = 1 << L2;
-    static constexpr int N8 = L2 / 3, REM = L2 % 3;
-    static constexpr int NST = N8 + (REM ? 1 : 0);
-    __host__ __device__ static constexpr int lR(int s) { return s < N8 ? 3 : REM; }
+    static constexpr int N16 = L2 / 4, REM = L2 % 4;
+    static constexpr int NST = N16 + (REM ? 1 : 0);
+    __host__ __device__ static constexpr int lR(int s) { return s < N16 ? 4 : REM; }
     __host__ __device__ static constexpr int R(int s) { return 1 << lR(s); }
     __host__ __device__ static constexpr int lNs(int s)
     {

@@ -86,12 +86,14 @@ static int max_threads(conv_precision prec, int E)
     } while (0)
 
 // Twiddle powers a radix-R butterfly reads from its stage's table: w^k (R = 2); w^k, w^2k (R = 3,
-// 4; w^3k is their product); w^k, w^2k, w^4k (R = 5, 8; the other powers are products).
-static inline int tw_blocks(int R) { return R == 2 ? 1 : (R <= 4 ? 2 : 3); }
+// 4; w^3k is their product); w^k, w^2k, w^4k (R = 5, 8); w^k, w^2k, w^4k, w^8k (R = 16); the
+// other powers are products.
+static inline int tw_blocks(int R) { return R == 2 ? 1 : (R <= 4 ? 2 : (R <= 8 ? 3 : 4)); }
 
 // Radix sequence for L = 2^p 3^q 5^r whose radices divide E (E = 0: any of 8, 4, 2, 3, 5):
-// power-of-two radices first (8s when allowed, else 4s), then 3s, then 5s.
-static bool factorize(int L, int E, FFTDesc &d)
+// power-of-two radices first (8s when allowed, else 4s), then 3s, then 5s.  radix16: a power of
+// two as radix-16 stages and one stage for the remainder (the compile-time-length transforms).
+static bool factorize(int L, int E, FFTDesc &d, bool radix16 = false)
 {
     int rem = L, p2 = 0, p3 = 0, p5 = 0;
     while (rem % 2 == 0) { rem /= 2; ++p2; }
@@ -101,7 +103,10 @@ static bool factorize(int L, int E, FFTDesc &d)
     auto ok = [E](int r) { return E == 0 || E % r == 0; };
     if ((p3 && !ok(3)) || (p5 && !ok(5))) return false;
     std::vector<int> R;
-    if (ok(8)) {
+    if (radix16 && p3 == 0 && p5 == 0 && E > 0 && E % 16 == 0) {
+        for (int i = 0; i < p2 / 4; ++i) R.push_back(16);
+        if (p2 % 4) R.push_back(1 << (p2 % 4));
+    } else if (ok(8)) {
         for (int i = 0; i < p2 / 3; ++i) R.push_back(8);
         if (p2 % 3 == 2) R.push_back(4);
         if (p2 % 3 == 1) R.push_back(2);
@@ -329,7 +334,9 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
     if (tpt > maxT) return false;
     const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d, fused_pref == 1) : 0;
     const bool fused = ed != 0;
-    if (ed >= 1000) {  // the compile-time-length kernels' launch bound
+    if (ed >= 1000) {
+        // the compile-time-length kernels: radix-16 stages, their launch bound
+        if (!factorize(M, E, d, true)) return false;
         maxT = std::min(maxT, WSC_STATIC_MAXT);
         if (tpt > maxT) return false;
     }
