@@ -4,7 +4,9 @@
 //   bulk copies (TMA, cp.async.bulk): one thread moves a contiguous, 16-byte aligned run whose
 //     size is a multiple of 16 bytes; completion is counted in bytes on an mbarrier;
 //   cp.async: every thread moves 16-byte pieces of a strided gather; completion is per thread
-//     (cp.async.wait_all), made visible to the CTA by the next barrier.
+//     (cp.async.wait_all), made visible to the CTA by the next barrier;
+//   TMA tiled copies (cp.async.bulk.tensor): one thread moves a box of a strided array described
+//     by a tensor map; loads complete on an mbarrier, stores in bulk groups.
 //
 // Every mbarrier wait is bounded in wall time (WSC_WAIT_NS, read from %globaltimer).  A wait that
 // gives up returns false; the caller records CONV_ETIMEOUT in the plan's device status word and
@@ -89,5 +91,29 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// TMA tiled copies over a 3-D tensor map (the map lives in kernel parameter space).  Shared
+// addresses 128-byte aligned; the inner coordinate x times 8 bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *map, int x, int y, int z, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const void *map, int x, int y, int z, const void *src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_addr(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// this thread's committed bulk stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's committed bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 }  // namespace wsc

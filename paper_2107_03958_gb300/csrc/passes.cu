@@ -280,13 +280,14 @@ static conv_status set_all_attrs(int smem)
     return rc;
 }
 
-static size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+static size_t round128(size_t x) { return (x + 127) & ~(size_t)127; }
 
 // Shared memory of a pass CTA with G groups: [twiddles][G transform buffers][G staging areas]
 // [G mbarriers], in the order stage_area() walks it on the device.
 static size_t pass_smem(size_t twb, size_t per, size_t stage_bytes, int G)
 {
-    return round16(twb + per * G) + (round16(stage_bytes) + (stage_bytes ? 8 : 0)) * G;
+    // staging: 128 bytes of slack to start it on a 128-byte shared address
+    return twb + per * G + (stage_bytes ? 128 + (round128(stage_bytes) + 8) * G : 0);
 }
 
 // Most groups (<= 8, <= maxT / tpt) whose CTA fits `smem_optin`; 0 if not even one does.
@@ -298,16 +299,21 @@ static int max_groups(int maxT, int tpt, size_t twb, size_t per, size_t stage_by
 }
 
 // Default options per pass (CFG_DEFAULT in a candidate), from FP32 measurements at n = 4096,
-// batch 16.  Runtime stage structure: prefetch pays in the row passes of the R2R and split R2C
-// pipelines (contiguous row loads, strided spectrum gathers) and not in their column passes or in
-// the C2C passes, where it costs a transform per CTA.  Compile-time lengths (one transform per
-// CTA, 128 registers): prefetch everywhere, and the column pass reads its twiddles through L1.
+// batch 16 (per-pass ms of the R2R / split R2C plans in parentheses).
+//   Runtime stage structure: prefetch pays in the row passes of the R2R and split R2C pipelines and
+//   not in their column passes or in the C2C passes, where it costs a transform per CTA; TMA
+//   copies of the strided spectrum pairs pay in both row passes (pass 1 2.15 -> 1.81, pass 3
+//   2.07 -> 1.81).
+//   Compile-time lengths (one transform per CTA, 128 registers): prefetch everywhere, twiddles
+//   through L1; TMA loads in pass 3 (1.64 -> 1.35, split 3.20 -> 2.45) but not TMA stores in
+//   pass 1: boxes of 16-byte runs drain at about 7 cycles per run per SM, slower than this
+//   transform (1.72 -> 2.9).
 static int default_options(const conv_plan_s *p, int ed, int pass)
 {
-    const bool rows_pf = p->io == CONV_IO_R2R || (p->io == CONV_IO_R2C && p->complex_ghat);
-    if (ed >= 1000) return pass == 0 ? CFG_PF : pass == 1 ? CFG_PF : (rows_pf ? CFG_TWS | CFG_PF : CFG_TWS);
-    if (!rows_pf) return pass == 2 ? 0 : CFG_TWS;
-    return pass == 1 ? CFG_TWS : CFG_TWS | CFG_PF;
+    const bool pairs = p->io == CONV_IO_R2R || (p->io == CONV_IO_R2C && p->complex_ghat);
+    if (ed >= 1000) return pass == 2 ? (pairs ? CFG_PF | CFG_TMA : CFG_TWS) : CFG_PF;
+    if (!pairs) return pass == 2 ? 0 : CFG_TWS;
+    return pass == 1 ? CFG_TWS : CFG_TWS | CFG_PF | CFG_TMA;
 }
 
 // One launch configuration c = {E elements per thread, fused passes (1 when eligible, preferring a
@@ -341,28 +347,49 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         if (tpt > maxT) return false;
     }
     const size_t twb = (size_t)d.tw_len * esz;
-    // staging: a row pair / row / column (n elements V) for passes 1 and 2; a row's spectrum for
-    // pass 3 (R2R: both spectra of a row pair for k <= M/2; C2C: all M values)
-    const size_t sb12 = (size_t)n * esz;
-    const size_t sb3 = (p->io == CONV_IO_R2R ? 2 * (size_t)p->h : (size_t)M) * esz;
-    auto shape = [&](int cfg, size_t stage_bytes, int nbuf, LaunchShape &S) -> bool {
+    // Staging per group (fused passes), by pass:
+    //   pass 1: prefetched input rows (n elements V, rounded to 128 B), then with TMA stores the
+    //           row pair's spectrum pairs, nbox x TMA_ROWS x 2 elements;
+    //   pass 2: the prefetched column (n elements);
+    //   pass 3: the row's spectrum: row-pair / (Wr, Wi) pairs for k <= M/2 (2 h, or the TMA boxes'
+    //           nbox x TMA_ROWS x 2), or all M values (C2C).
+    const size_t nbox_b = (size_t)((p->h + TMA_ROWS - 1) / TMA_ROWS) * TMA_ROWS * 2 * esz;
+    auto stage_bytes = [&](int pass, bool pairs, bool pf, bool tma) -> size_t {
+        if (pass == 0) return (pf ? round128((size_t)n * esz) : 0) + (tma ? nbox_b : 0);
+        if (pass == 1) return pf ? (size_t)n * esz : 0;
+        if (!pf) return 0;
+        if (!pairs) return (size_t)M * esz;
+        return tma ? nbox_b : 2 * (size_t)p->h * esz;
+    };
+    // pairs: the pass works on 16/32-byte spectrum pairs (R2R, split R2C) and may use TMA
+    auto shape = [&](int cfg, int pass, bool pairs, int nbuf, LaunchShape &S) -> bool {
         const size_t pb = per * nbuf;
         bool tws = (cfg & CFG_TWS) && E > 0;
-        size_t sb = fused && (cfg & CFG_PF) ? stage_bytes : 0;
-        int G = max_groups(maxT, tpt, tws ? twb : 0, pb, sb, smem_optin);
+        bool pf = fused && (cfg & CFG_PF);
+        bool tma = fused && pairs && (cfg & CFG_TMA) && (pass == 0 || (pass == 2 && pf));
+        auto G_now = [&] { return max_groups(maxT, tpt, tws ? twb : 0, pb, stage_bytes(pass, pairs, pf, tma), smem_optin); };
+        int G = G_now();
         if (G < 1 && tws) {
             tws = false;
-            G = max_groups(maxT, tpt, 0, pb, sb, smem_optin);
+            G = G_now();
         }
-        if (G < 1 && sb) {
-            sb = 0;
-            G = max_groups(maxT, tpt, 0, pb, 0, smem_optin);
+        if (G < 1 && tma) {
+            tma = false;
+            G = G_now();
+        }
+        if (G < 1 && pf) {
+            pf = false;
+            tma = false;
+            G = G_now();
         }
         if (G < 1) return false;
         if (cfg & CFG_ONE) G = 1;
+        const size_t sb = stage_bytes(pass, pairs, pf, tma);
         S.tpt = tpt;
         S.groups = G;
         S.tws = tws;
+        S.pf = pf;
+        S.tma = tma;
         S.stage = (int)(sb / esz);
         S.smem = pass_smem(tws ? twb : 0, pb, sb, G);
         int bps = 1;
@@ -376,15 +403,17 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
     int opt[3];
     for (int k = 0; k < 3; ++k) opt[k] = c[2 + k] == CFG_DEFAULT ? default_options(p, ed, k) : c[2 + k];
     LaunchShape R, C, I;
-    if (!shape(opt[0], sb12, 1, R)) return false;
     // R2C with complex ghat runs the split pipeline when its pass 2 fits two buffers per CTA;
     // otherwise the C2C layout
     bool split = false;
     if (fused) {
-        split = p->io == CONV_IO_R2C && p->complex_ghat && shape(opt[1], sb12, 2, C);
-        const size_t sbi = split ? 2 * (size_t)p->h * esz : sb3;
-        if ((!split && !shape(opt[1], sb12, 1, C)) || !shape(opt[2], sbi, 1, I)) return false;
+        split = p->io == CONV_IO_R2C && p->complex_ghat && shape(opt[1], 1, false, 2, C);
+        const bool pairs = p->io == CONV_IO_R2R || split;
+        if (!shape(opt[0], 0, pairs, 1, R) || (!split && !shape(opt[1], 1, false, 1, C)) ||
+            !shape(opt[2], 2, pairs, 1, I))
+            return false;
     } else {
+        if (!shape(opt[0], 0, false, 1, R)) return false;
         C = I = R;  // the plain kernels share one twiddle option and shape
     }
     p->r2c_split = split;
@@ -473,15 +502,15 @@ std::vector<std::vector<Candidate>> transform_families(conv_plan_s *p)
         int ed_static = -1;
         for (int fu : {1, 2, 0}) {
             std::vector<Candidate> fam;
-            std::vector<std::array<int, 9>> seen;  // distinct (tws, staged, groups) of the three passes
-            for (int cfg = 0; cfg < (fu ? 8 : 2); ++cfg) {
+            std::vector<std::array<int, 12>> seen;  // distinct (tws, pf, tma, groups) of the three passes
+            for (int cfg = 0; cfg < (fu ? 16 : 2); ++cfg) {
                 const Candidate c = {cand[i], fu, cfg, cfg, cfg};
                 if (!configure(&probe, c, smem_optin, sms) || probe.fused != (fu != 0)) continue;
                 if (fu == 1) ed_static = probe.ed;
                 if (fu == 2 && probe.ed == ed_static) break;  // no compile-time length: same as fu = 1
-                const std::array<int, 9> key = {probe.rows.tws, probe.rows.stage > 0, probe.rows.groups,
-                                                probe.cols.tws, probe.cols.stage > 0, probe.cols.groups,
-                                                probe.inv.tws,  probe.inv.stage > 0,  probe.inv.groups};
+                const std::array<int, 12> key = {probe.rows.tws, probe.rows.pf, probe.rows.tma, probe.rows.groups,
+                                                 probe.cols.tws, probe.cols.pf, probe.cols.tma, probe.cols.groups,
+                                                 probe.inv.tws,  probe.inv.pf,  probe.inv.tma,  probe.inv.groups};
                 bool dup = false;
                 for (auto &k : seen) dup = dup || k == key;
                 if (dup) continue;

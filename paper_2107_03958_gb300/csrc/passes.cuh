@@ -31,7 +31,18 @@ template <typename T> struct PassArgs {
     int stage_len;         // fused passes: elements V of each group's staging area (0: none)
     int pf;                // fused passes: this launch prefetches work items into the staging areas
     int vec;               // R2C pass 2: the output pairs may be stored as 16-byte vectors
+    int tma;               // pass 1: spectra leave by TMA stores; pass 3: spectra arrive by TMA loads
+    CUtensorMap tmap;      // the spectrum array's map for those copies (kernel parameter space)
 };
+
+// Staging of a fused pass 1 with TMA stores: [input rows (prefetch), rounded to 128 bytes]
+// [output pairs: nbox x TMA_ROWS x 2 elements]; pass 3 with TMA loads: [nbox x TMA_ROWS x 2].
+template <typename T> __host__ __device__ inline int tma_boxes(int h) { return (h + TMA_ROWS - 1) / TMA_ROWS; }
+template <typename T> __host__ __device__ inline int stage_in_len(int n, bool pf)
+{
+    const int per128 = 128 / (int)(2 * sizeof(T));
+    return pf ? (n + per128 - 1) / per128 * per128 : 0;
+}
 
 // Shared-memory carve-up: [twiddles (M) if TWS][group 0 buffer][group 1 buffer]...
 template <typename T, bool TWS>
@@ -53,7 +64,8 @@ __device__ __forceinline__ typename cvec<T>::t *setup_smem(const PassArgs<T> &a,
 }
 
 // Fused passes continue the carve-up with [staging 0]...[staging G-1][mbarrier 0]...[mbarrier G-1],
-// the staging block starting on a 16-byte boundary and every area a multiple of 16 bytes long
+// the staging block starting on a 128-byte shared-memory address and every area a multiple of
+// 128 bytes long
 // (pass_smem on the host computes the same sizes).  A pass with NBUF transform buffers per group
 // takes buffers NBUF g ... NBUF g + NBUF - 1 of the carve-up.
 template <typename T, bool TWS, int NBUF = 1>
@@ -63,8 +75,10 @@ __device__ __forceinline__ typename cvec<T>::t *stage_area(const PassArgs<T> &a,
     typedef typename cvec<T>::t V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     size_t off = (TWS ? (size_t)a.tw_len * sizeof(V) : 0) + (size_t)NBUF * G * padded_len<T>(a.M) * sizeof(V);
-    off = (off + 15) & ~(size_t)15;
-    const size_t st = ((size_t)a.stage_len * sizeof(V) + 15) & ~(size_t)15;
+    // 128-byte aligned shared address (TMA boxes); the host reserves 128 bytes of slack for it
+    const size_t base = (size_t)__cvta_generic_to_shared(smem_raw);
+    off = ((base + off + 127) & ~(size_t)127) - base;
+    const size_t st = ((size_t)a.stage_len * sizeof(V) + 127) & ~(size_t)127;
     bar = reinterpret_cast<unsigned long long *>(smem_raw + off + (size_t)G * st) + g;
     return reinterpret_cast<V *>(smem_raw + off + (size_t)g * st);
 }

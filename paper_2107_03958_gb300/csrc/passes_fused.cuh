@@ -98,7 +98,7 @@ __device__ __forceinline__ void store_pair(typename cvec<T>::t *p, typename cvec
 // Pass 1.  Staging: rows j1, j1 + 1 of u (adjacent in memory), n T each; one bulk copy
 // (a.pf requires n sizeof(T) to be a multiple of 16 and u 16-byte aligned).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -108,6 +108,9 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const PassArgs<T> a)
     T *stg = reinterpret_cast<T *>(stage_area<T, TWS>(a, g, G, bar));
     const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2, stride = gridDim.x * G;
     const bool pair_vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0;
+    // TMA stores: the spectrum pairs (A_k, B_k) of the item, k < h, side by side in shared memory
+    V *ost = reinterpret_cast<V *>(stg) + stage_in_len<T>(n, a.pf);
+    constexpr int WPE = (int)(sizeof(V) / 8);  // 8-byte words per element
     auto fetch = [&](int unit) {
         if (!a.pf || lt != 0 || unit >= a.units) return;
         const int b = unit / pairs, j1 = 2 * (unit - b * pairs);
@@ -145,23 +148,43 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const PassArgs<T> a)
             return cmk<V>(x, y);
         };
         fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
+        if (a.tma) {
+            // the previous item's stores have to have read the pairs before they are rewritten
+            if (lt == 0) bulk_wait_read();
+            __syncthreads();
+        }
         if (valid) {
             V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * h * n;
             for (int k = lt; k < h; k += a.tpt) {
                 V Zk = buf[pidx<T>(k)], Zm = buf[pidx<T>(k == 0 ? 0 : M - k)];
                 const V A = cmk<V>((T)0.5 * (Zk.x + Zm.x), (T)0.5 * (Zk.y - Zm.y));
                 const V B = cmk<V>((T)0.5 * (Zk.y + Zm.y), (T)-0.5 * (Zk.x - Zm.x));
-                store_pair<T>(Wb + (size_t)k * n + j1, A, B, has2, pair_vec);
+                if (a.tma) {
+                    ost[2 * k] = A;
+                    ost[2 * k + 1] = B;
+                } else {
+                    store_pair<T>(Wb + (size_t)k * n + j1, A, B, has2, pair_vec);
+                }
+            }
+        }
+        if (a.tma) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (lt == 0 && valid) {
+                for (int i = 0; i < tma_boxes<T>(h); ++i)
+                    tma_store_3d(&a.tmap, j1 * WPE, i * TMA_ROWS, b, ost + 2 * i * TMA_ROWS);
+                bulk_commit();
             }
         }
         __syncthreads();
     }
+    if (a.tma && lt == 0) bulk_wait_all();
 }
 
 // Pass 2.  Staging: the column's n spectrum values (contiguous in W); one bulk copy (a.pf
 // requires n sizeof(V) to be a multiple of 16 and W 16-byte aligned).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -212,7 +235,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const PassArgs<T> a)
 // Pass 3.  Staging: the row pair's spectra W[k][j1], W[k][j1+1] for k <= M/2, side by side;
 // gathered by cp.async (a.pf requires W 16-byte aligned and, in FP32, n even).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -223,9 +246,19 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const PassArgs<T> a)
     const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2, stride = gridDim.x * G;
     const bool pair_vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
     const T alpha = a.alpha.x, beta = a.beta;
+    constexpr int WPE = (int)(sizeof(V) / 8);
     auto gather = [&](int unit) {
         if (!a.pf || unit >= a.units) return;
         const int b = unit / pairs, j1 = 2 * (unit - b * pairs);
+        if (a.tma) {  // TMA boxes of TMA_ROWS pairs; rows k >= h arrive as zeros
+            if (lt == 0) {
+                const int nb = tma_boxes<T>(h);
+                fence_proxy_async_smem();
+                mbar_expect_tx(bar, (unsigned)(nb * 2 * TMA_ROWS * sizeof(V)));
+                for (int i = 0; i < nb; ++i) tma_load_3d(stg + 2 * i * TMA_ROWS, &a.tmap, j1 * WPE, i * TMA_ROWS, b, bar);
+            }
+            return;
+        }
         const V *Wp = reinterpret_cast<const V *>(a.in) + (size_t)b * h * n + j1;
         const bool two = j1 + 1 < n;
         for (int k = lt; k < h; k += a.tpt) {
@@ -235,13 +268,22 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const PassArgs<T> a)
             }
         }
     };
+    unsigned par = 0;
+    if (a.pf && a.tma) {
+        if (lt == 0) mbar_init(bar);
+        __syncthreads();
+    }
     gather(blockIdx.x * G + g);
     for (int base = blockIdx.x * G; base < a.units; base += stride) {
         const int unit = base + g;
         const bool valid = unit < a.units;
         if (a.pf) {
-            cp_async_wait_all();
-            __syncthreads();
+            if (a.tma) {
+                if (!await_bulk(a, bar, par, valid)) return;
+            } else {
+                cp_async_wait_all();
+                __syncthreads();
+            }
         }
         const int b = valid ? unit / pairs : 0, j1 = valid ? 2 * (unit - b * pairs) : 0;
         const bool has2 = valid && j1 + 1 < n;
@@ -298,7 +340,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const PassArgs<T> a)
 // Pass 2.  Two transform buffers per group: Re ghat's product transforms in the first, Im ghat's
 // in the second.  Staging: the column of W (one bulk copy, as in the R2R pass 2).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -364,7 +406,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const PassArgs<T> a)
 // Pass 3.  Staging: the row's pairs W2[k][j1] = (Wr, Wi), k <= M/2, gathered by cp.async
 // (16-byte pieces; a.pf requires W2 16-byte aligned).
 template <typename T, int E, int ED, bool TWS>
-__global__ void WSC_LBF(T, E, ED) kf_r2c_rows_inv(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_r2c_rows_inv(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -373,22 +415,42 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_rows_inv(const PassArgs<T> a)
     unsigned long long *bar;
     V *stg = stage_area<T, TWS>(a, g, G, bar);
     const int n = a.n, M = a.M, h = a.h, stride = gridDim.x * G;
+    constexpr int WPE = (int)(sizeof(V) / 8);
     auto gather = [&](int unit) {
         if (!a.pf || unit >= a.units) return;
         const int b = unit / n, j1 = unit - b * n;
+        if (a.tma) {  // TMA boxes of TMA_ROWS (Wr, Wi) pairs; rows k >= h arrive as zeros
+            if (lt == 0) {
+                const int nb = tma_boxes<T>(h);
+                fence_proxy_async_smem();
+                mbar_expect_tx(bar, (unsigned)(nb * 2 * TMA_ROWS * sizeof(V)));
+                for (int i = 0; i < nb; ++i)
+                    tma_load_3d(stg + 2 * i * TMA_ROWS, &a.tmap, 2 * j1 * WPE, i * TMA_ROWS, b, bar);
+            }
+            return;
+        }
         const V *Wp = reinterpret_cast<const V *>(a.in) + 2 * ((size_t)b * h * n + j1);
         for (int k = lt; k < h; k += a.tpt) {
             cp_async16(stg + 2 * k, Wp + 2 * (size_t)k * n);
             if constexpr (sizeof(T) == 8) cp_async16(stg + 2 * k + 1, Wp + 2 * (size_t)k * n + 1);
         }
     };
+    unsigned par = 0;
+    if (a.pf && a.tma) {
+        if (lt == 0) mbar_init(bar);
+        __syncthreads();
+    }
     gather(blockIdx.x * G + g);
     for (int base = blockIdx.x * G; base < a.units; base += stride) {
         const int unit = base + g;
         const bool valid = unit < a.units;
         if (a.pf) {
-            cp_async_wait_all();
-            __syncthreads();
+            if (a.tma) {
+                if (!await_bulk(a, bar, par, valid)) return;
+            } else {
+                cp_async_wait_all();
+                __syncthreads();
+            }
         }
         const int b = valid ? unit / n : 0, j1 = valid ? unit - b * n : 0;
         const V *Wb = reinterpret_cast<const V *>(a.in) + 2 * ((size_t)b * h * n + j1);
@@ -426,7 +488,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_rows_inv(const PassArgs<T> a)
 // Pass 1.  Staging: row j1 of the input (n T real or n V complex); one bulk copy (a.pf requires
 // its byte length to be a multiple of 16 and the input 16-byte aligned).
 template <typename T, int E, int ED, bool TWS, bool IN_REAL>
-__global__ void WSC_LBF(T, E, ED) kf_c2c_rows_fwd(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_c2c_rows_fwd(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     typedef typename std::conditional<IN_REAL, T, V>::type I;
@@ -474,7 +536,7 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_rows_fwd(const PassArgs<T> a)
 
 // Pass 2.  Staging: the column's n spectrum values; one bulk copy (as in the R2R pass 2).
 template <typename T, int E, int ED, bool TWS, bool CG>
-__global__ void WSC_LBF(T, E, ED) kf_c2c_cols(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_c2c_cols(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -525,7 +587,7 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_cols(const PassArgs<T> a)
 // Pass 3.  Staging: the row's spectrum W[i][j1], i < M, one element per i; gathered by cp.async
 // (8-byte pieces in FP32, 16-byte in FP64; a.pf requires W aligned to the element size).
 template <typename T, int E, int ED, bool TWS, bool IN_REAL>
-__global__ void WSC_LBF(T, E, ED) kf_c2c_rows_inv(const PassArgs<T> a)
+__global__ void WSC_LBF(T, E, ED) kf_c2c_rows_inv(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
@@ -635,7 +697,14 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
     // their element size (8-byte cp.async), and bulk copy lengths that are multiples of 16
     auto al = [](const void *q, size_t m) { return (reinterpret_cast<uintptr_t>(q) % m) == 0; };
     const bool ws16 = al(ws, 16);
-    const bool pf_cols = C.stage > 0 && ws16 && (n * sizeof(V)) % 16 == 0;
+    const bool pf_cols = C.pf && ws16 && (n * sizeof(V)) % 16 == 0;
+    // TMA over the spectrum pairs: W (pass 1 stores; R2R pass 3 loads) or W2 (split pass 3 loads),
+    // n (or 2n) elements of sizeof(V) / 8 words per k2 row, h rows, `batch` densities
+    constexpr unsigned WPE = (unsigned)(sizeof(V) / 8);
+    auto tma_map = [&](const LaunchShape &S, const void *base, unsigned long long elems_per_row) {
+        a.tma = S.tma && encode_rows_map(&a.tmap, base, elems_per_row * WPE, (unsigned long long)h,
+                                         (unsigned long long)batch, 2 * WPE);
+    };
     // one launch of kernel K<T, E, ED, tws[, X]> in shape S, with S's twiddle option
 #define WSC_TARGS(T_, E_, ED_) T_, E_, ED_
 #define WSC_LAUNCH(S, K, TA)                                                                   \
@@ -656,7 +725,8 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.out = ws;
         a.units = batch * ((n + 1) / 2);
         a.stage_len = R.stage;
-        a.pf = R.stage > 0 && al(u, 16) && (n * sizeof(T)) % 16 == 0;
+        a.pf = R.pf && al(u, 16) && (n * sizeof(T)) % 16 == 0;
+        tma_map(R, ws, n);
         WSC_LAUNCH(R, kf_r2r_rows_fwd, (T, E, ED));
         if (ev) cudaEventRecord(ev[1], st);
         a.tpt = C.tpt;
@@ -664,13 +734,16 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.units = batch * h;
         a.stage_len = C.stage;
         a.pf = pf_cols;
+        a.tma = 0;
         WSC_LAUNCH(C, kf_r2r_cols, (T, E, ED));
         if (ev) cudaEventRecord(ev[2], st);
         a.tpt = I.tpt;
         a.out = out;
         a.units = batch * ((n + 1) / 2);
         a.stage_len = I.stage;
-        a.pf = I.stage > 0 && ws16 && (sizeof(T) == 8 || n % 2 == 0);
+        a.pf = I.pf && ws16 && (sizeof(T) == 8 || n % 2 == 0);
+        if (a.pf) tma_map(I, ws, n);
+        else a.tma = 0;
         WSC_LAUNCH(I, kf_r2r_rows_inv, (T, E, ED));
     } else if (p->r2c_split) {
         a.tpt = R.tpt;
@@ -678,7 +751,8 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.out = ws;
         a.units = batch * ((n + 1) / 2);
         a.stage_len = R.stage;
-        a.pf = R.stage > 0 && al(u, 16) && (n * sizeof(T)) % 16 == 0;
+        a.pf = R.pf && al(u, 16) && (n * sizeof(T)) % 16 == 0;
+        tma_map(R, ws, n);
         WSC_LAUNCH(R, kf_r2r_rows_fwd, (T, E, ED));
         if (ev) cudaEventRecord(ev[1], st);
         // W2 follows W on the next even element (the workspace holds batch (3 h n + 1) values)
@@ -689,6 +763,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.units = batch * h;
         a.stage_len = C.stage;
         a.pf = pf_cols;
+        a.tma = 0;
         a.vec = al(W2, 16);
         WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
         if (ev) cudaEventRecord(ev[2], st);
@@ -697,7 +772,9 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.out = out;
         a.units = batch * n;
         a.stage_len = I.stage;
-        a.pf = I.stage > 0 && al(W2, 16);
+        a.pf = I.pf && al(W2, 16);
+        if (a.pf) tma_map(I, W2, 2 * (unsigned long long)n);
+        else a.tma = 0;
         WSC_LAUNCH(I, kf_r2c_rows_inv, (T, E, ED));
     } else {
         const bool in_real = p->io == CONV_IO_R2C;
@@ -706,7 +783,8 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.out = ws;
         a.units = batch * n;
         a.stage_len = R.stage;
-        a.pf = R.stage > 0 && al(u, 16) && (n * (in_real ? sizeof(T) : sizeof(V))) % 16 == 0;
+        a.pf = R.pf && al(u, 16) && (n * (in_real ? sizeof(T) : sizeof(V))) % 16 == 0;
+        a.tma = 0;
         if (in_real)
             WSC_LAUNCH2(R, kf_c2c_rows_fwd, (T, E, ED), true);
         else
@@ -726,7 +804,8 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.out = out;
         a.units = batch * n;
         a.stage_len = I.stage;
-        a.pf = I.stage > 0 && al(ws, sizeof(V));
+        a.pf = I.pf && al(ws, sizeof(V));
+        a.tma = 0;
         if (in_real)
             WSC_LAUNCH2(I, kf_c2c_rows_inv, (T, E, ED), true);
         else

@@ -1,5 +1,6 @@
 // wsconv_internal.h -- plan object and helpers shared by the library's translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <array>
@@ -47,8 +48,15 @@ template <typename T, int E, int ED, bool TWS> int blocks_per_sm_fused(int threa
 
 // Launch shape of one pass family (rows or columns).
 // Per-pass launch options (bits): twiddle table in shared memory, prefetch of the next work item
-// (fused passes), one transform per CTA instead of the most that fit.
-enum { CFG_TWS = 1, CFG_PF = 2, CFG_ONE = 4, CFG_DEFAULT = -1 };
+// (fused passes), one transform per CTA instead of the most that fit, TMA tiled copies for the
+// row passes' strided spectrum accesses (R2R and split R2C: pass 1 stores, pass 3 loads).
+enum { CFG_TWS = 1, CFG_PF = 2, CFG_ONE = 4, CFG_TMA = 8, CFG_DEFAULT = -1 };
+
+// rows (k2 values) per TMA box
+#define TMA_ROWS 256
+// tma.cu
+bool encode_rows_map(CUtensorMap *m, const void *base, unsigned long long words, unsigned long long rows,
+                     unsigned long long batch, unsigned box_words);
 // A launch configuration: {E, fused passes, options of pass 1, of pass 2, of pass 3}.  Unfused
 // passes share pass 1's twiddle option.
 typedef std::array<int, 5> Candidate;
@@ -60,6 +68,8 @@ struct LaunchShape {
     int max_ctas;  // persistent grid size (CTAs resident at once)
     int stage;     // fused passes: elements of each group's prefetch staging area (0: no prefetch)
     bool tws;      // twiddle table in shared memory
+    bool pf;       // fused passes: prefetch of the next work item into the staging area
+    bool tma;      // pass 1: TMA stores of the spectra; pass 3: TMA loads into the staging area
 };
 
 }  // namespace wsc
