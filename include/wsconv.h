@@ -114,6 +114,23 @@ conv_status conv_workspace_size(conv_plan_t plan, int batch, size_t *bytes);
 conv_status conv_apply(conv_plan_t plan, const void *u, const void *mask, void *out, int batch,
                        void *workspace, void *stream);
 
+/* conv_apply for densities in HOST memory (no counterpart in the paper; the host link is slower
+ * than the passes, so the copies have to overlap them).  The batch runs in chunks of
+ * ceil(batch_max / 4) densities: chunk i's upload, passes and download overlap chunk i+1's upload
+ * and chunk i-1's download, on three streams the plan creates at the first call together with
+ * two device slots of a chunk's densities and results.
+ *   u_host:   batch x n x n, layout and type as conv_apply's u, host memory.
+ *   out_host: batch x n x n, layout and type as conv_apply's out, host memory.
+ *   mask:     NULL or a DEVICE n x n array, as in conv_apply.
+ * Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister): pageable memory works,
+ * but its copies do not overlap.  Ordered on `stream` like conv_apply: it starts after earlier
+ * work on `stream`, later work on `stream` starts after out_host is complete, and the call
+ * returns without waiting.  It uses the plan's workspace and device slots: calls on one plan
+ * must not overlap (on different streams or threads).  Returns CONV_EINVAL for bad arguments or
+ * while per-pass timing is on, CONV_ENOMEM when the slots cannot be allocated. */
+conv_status conv_apply_host(conv_plan_t plan, const void *u_host, const void *mask, void *out_host, int batch,
+                            void *stream);
+
 /* conv_apply without any allocation (the paper has no counterpart; this is a deployment aid).
  * For callers that cannot call cudaMalloc when they run the convolution: code under a device
  * memory budget that forbids new allocations, real-time loops where an allocation may block, or

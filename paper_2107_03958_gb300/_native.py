@@ -88,6 +88,8 @@ PROTOTYPES = {
     "conv_fs_mask": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "conv_device_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "conv_apply_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_void_p]),
     "conv_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "conv_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_longlong)]),

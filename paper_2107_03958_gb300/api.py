@@ -120,6 +120,27 @@ class ConvPlan:
 
     __call__ = apply
 
+    def apply_host(self, u, out=None, mask=None, stream=None):
+        """A_n(u * mask) for densities in host memory (CPU tensors; pinned for overlap), with the
+        host<->device copies pipelined against the passes; returns `out` (a CPU tensor).  Ordered
+        on `stream`; synchronise it before reading `out`."""
+        if u.device.type != "cpu":
+            raise ValueError("apply_host takes host tensors")
+        if u.dtype != self.in_dtype() or tuple(u.shape[-2:]) != (self.n, self.n) or not u.is_contiguous():
+            raise ValueError("u must be a contiguous (..., n, n) %s host tensor" % self.in_dtype())
+        batch = 1 if u.dim() == 2 else int(np.prod(u.shape[:-2]))
+        if out is None:
+            out = torch.empty(u.shape, dtype=self.out_dtype()).pin_memory()
+        if out.device.type != "cpu" or out.dtype != self.out_dtype() or out.shape != u.shape or not out.is_contiguous():
+            raise ValueError("out must be a contiguous host tensor of u's shape and %s" % self.out_dtype())
+        if mask is not None:
+            self._check_grid(mask, self.real_dtype, "mask")
+        N.check(self._lib.conv_apply_host(
+            self._h, ctypes.c_void_p(u.data_ptr()),
+            ctypes.c_void_p(mask.data_ptr()) if mask is not None else None,
+            ctypes.c_void_p(out.data_ptr()), batch, _stream_ptr(stream)))
+        return out
+
     def fs_mask(self, shape, geom, delta=0.15, stream=None):
         """Fourier-smoothed indicator chi^n psi on the n x n grid (Sec. 2.4, eq. (tfs)).
         shape 'disk': geom = (c1, c2, r); 'rect': geom = (x0, x1, y0, y1)."""

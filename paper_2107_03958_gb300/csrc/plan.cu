@@ -189,6 +189,7 @@ const char *conv_last_error(void) { return g_last_error.c_str(); }
 void conv_destroy(conv_plan_t p)
 {
     if (!p) return;
+    destroy_hostpipe(p);
     if (p->ghat64 && p->ghat64 != p->ghat_paper) cudaFree(p->ghat64);
     if (p->ghat_paper) cudaFree(p->ghat_paper);
     if (p->ghat32) cudaFree(p->ghat32);

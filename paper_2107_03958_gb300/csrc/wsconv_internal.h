@@ -114,6 +114,8 @@ struct conv_plan_s {
     // per-pass timing instrumentation
     bool timing = false;
     std::vector<std::array<cudaEvent_t, 4>> tev_used, tev_free;
+    // host-buffer pipeline (host_io.cu), created by the first conv_apply_host
+    struct HostPipe *hostpipe = nullptr;
 };
 
 namespace wsc {
@@ -127,4 +129,5 @@ conv_status select_transform(conv_plan_s *p);
 // ghat.cu
 conv_status build_ghat(conv_plan_s *p);
 size_t spectrum_elems(const conv_plan_s *p);  // complex elements of the workspace per density
+void destroy_hostpipe(conv_plan_s *p);          // host_io.cu
 }  // namespace wsc

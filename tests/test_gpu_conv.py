@@ -212,6 +212,34 @@ def test_caller_workspace_r2c_split_and_alignment(prec):
     plan.device_status()
 
 
+@pytest.mark.parametrize("name,io,prec", [("log", "r2r", "fp32"), ("helm20", "r2c", "fp32"),
+                                          ("helm20", "c2c", "fp64"), ("pow-1", "r2r", "fp64")])
+def test_host_buffer_apply_equals_device_apply(name, io, prec):
+    """conv_apply_host (chunks of ceil(batch_max/4) densities, uploads/passes/downloads overlapped)
+    gives bitwise the device-buffer result, for a ragged last chunk, with a mask, from pinned and
+    from pageable host memory."""
+    n, B = 256, 11
+    kw = KERNELS[name]
+    plan = ConvPlan(n=n, period=3, precision=prec, io=io, batch_max=8, compact=True, **kw)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal((B, n, n))
+    if io == "c2c":
+        u = u + 1j * rng.standard_normal((B, n, n))
+    u_host = torch.tensor(u, dtype=plan.in_dtype()).pin_memory()
+    mask = torch.tensor(rng.uniform(0, 1, (n, n)), dtype=plan.real_dtype, device="cuda")
+    ws = torch.empty(plan.workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    ref = plan.apply(u_host.cuda(), mask=mask, workspace=ws).cpu()
+    s = torch.cuda.Stream()
+    out = plan.apply_host(u_host, mask=mask, stream=s)
+    s.synchronize()
+    assert torch.equal(out, ref)
+    pageable = torch.empty(ref.shape, dtype=ref.dtype)
+    plan.apply_host(u_host.clone(), out=pageable, mask=mask)
+    torch.cuda.synchronize()
+    assert torch.equal(pageable, ref)
+    plan.device_status()
+
+
 @pytest.mark.parametrize("name,io", [("log", "r2r"), ("helm20", "r2c")])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_autotuned_plan_matches_oracle(name, io, prec):
