@@ -166,6 +166,42 @@ template <bool INV, typename V> __device__ __forceinline__ void dft16(V *x) {
     }
 }
 
+// dft16 of x[0..7] followed by eight zeros (the first stage of a zero-extended transform):
+// the first layer's length-4 transforms see (x[r], x[r+4], 0, 0).
+template <bool INV, typename V> __device__ __forceinline__ void dft16_half_in(V *x) {
+    typedef decltype(V::x) T;
+    const T c = (T)0.9238795325112867561281831893967882;
+    const T s = (T)0.3826834323650897717284599840303989;
+    const T r2 = (T)0.7071067811865475244008443621048490;
+    V y[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const V a = x[r], b = x[r + 4], rb = rot<INV>(b);
+        y[r][0] = cadd(a, b);
+        y[r][1] = cadd(a, rb);
+        y[r][2] = csub(a, b);
+        y[r][3] = csub(a, rb);
+    }
+    y[1][1] = cmulc<INV>(y[1][1], c, -s);
+    y[1][2] = cmulc<INV>(y[1][2], r2, -r2);
+    y[1][3] = cmulc<INV>(y[1][3], s, -c);
+    y[2][1] = cmulc<INV>(y[2][1], r2, -r2);
+    y[2][2] = rot<INV>(y[2][2]);
+    y[2][3] = cmulc<INV>(y[2][3], -r2, -r2);
+    y[3][1] = cmulc<INV>(y[3][1], s, -c);
+    y[3][2] = cmulc<INV>(y[3][2], -r2, -r2);
+    y[3][3] = cmulc<INV>(y[3][3], -c, s);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        V z[4] = {y[0][m], y[1][m], y[2][m], y[3][m]};
+        dft4<INV>(z);
+        x[m] = z[0];
+        x[m + 4] = z[1];
+        x[m + 8] = z[2];
+        x[m + 12] = z[3];
+    }
+}
+
 template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x) {
     if (R == 2) dft2<INV>(x);
     else if (R == 3) dft3<INV>(x);

@@ -43,7 +43,10 @@ template <int L2> struct Pow2Stages {
 };
 
 // One radix-R stage S; every thread owns E/R butterflies j = lt + b tpt.
-template <typename T, int E, int L2, int S, bool INV, bool TWS, class Src, class Dst>
+// HIN: the transform's inputs e >= L/2 are zero (a zero-extended half): stage 0 loads only
+// q < R/2 and runs the half-input butterfly.  HOUT: only outputs o < L/2 are used (a cropped
+// half): the last stage stores only p < R/2, and the arithmetic feeding the rest drops out.
+template <typename T, int E, int L2, int S, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst>
 __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw, int lt,
                                        const Src &src, const Dst &dst)
 {
@@ -56,6 +59,9 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
     static_assert(TPT % PAD == 0, "threads per transform must be a multiple of the padding period");
     constexpr bool SRC_SMEM = std::is_same<Src, FromSmem>::value;
     constexpr bool DST_SMEM = writes_smem<Dst>::value;
+    constexpr bool half_in = HIN && S == 0, half_out = HOUT && S == P::NST - 1;
+    static_assert(!half_in || R == 16, "the half-input butterfly is radix 16");
+    __builtin_assume(lt >= 0 && lt < TPT);
     // per-thread bases of this stage
     const int pl = lt + (lt >> PS);
     int k0, jq0;
@@ -82,7 +88,8 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int c = b * TPT + q * NBF;
-            if constexpr (SRC_SMEM) v[b][q] = buf[pl + c + (c >> PS)];
+            if (half_in && q >= R / 2) v[b][q] = cmk<V>(0, 0);
+            else if constexpr (SRC_SMEM) v[b][q] = buf[pl + c + (c >> PS)];
             else v[b][q] = src(lt + c);
         }
     }
@@ -91,10 +98,11 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
     for (int b = 0; b < NB; ++b) {
         const int cb = b * TPT, ck = cb & (Ns - 1), cj = cb >> lNs;
         if constexpr (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw + P::toff(S) + ck, Ns, k0);
-        dftR<R, INV>(v[b]);
+        if constexpr (half_in) dft16_half_in<INV>(v[b]);
+        else dftR<R, INV>(v[b]);
         const int Cb = RN <= PAD ? cj * RN + ((cj * RN) >> PS) : cj * (RN + RN / PAD) + ck + (ck >> PS);
 #pragma unroll
-        for (int p = 0; p < R; ++p) {
+        for (int p = 0; p < (half_out ? R / 2 : R); ++p) {
             const int Cp = RN <= PAD ? p * Ns : (Ns < PAD ? p * Ns + ((p * Ns) >> PS) : p * (Ns + Ns / PAD));
             const int o = O0 + cj * RN + ck + p * Ns;
             if constexpr (std::is_same<Dst, ToSmem>::value) {
@@ -112,7 +120,7 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
     if constexpr (DST_SMEM) __syncthreads();
 }
 
-template <typename T, int E, int L2, bool INV, bool TWS, class Src, class Dst, class After0, int S>
+template <typename T, int E, int L2, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst, class After0, int S>
 __device__ __forceinline__ void fft_static_from(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw,
                                                 int lt, const Src &src, const Dst &dst, const After0 &after0)
 {
@@ -122,33 +130,40 @@ __device__ __forceinline__ void fft_static_from(typename cvec<T>::t *buf, const 
     int lt_ = lt;
     asm volatile("" : "+r"(lt_));
     if constexpr (S == 0) {
-        sstage<T, E, L2, 0, INV, TWS>(buf, tw, lt_, src, ToSmem{});
+        sstage<T, E, L2, 0, INV, TWS, HIN, HOUT>(buf, tw, lt_, src, ToSmem{});
         after0();
     } else if constexpr (S == NST - 1) {
-        sstage<T, E, L2, S, INV, TWS>(buf, tw, lt_, FromSmem{}, dst);
+        sstage<T, E, L2, S, INV, TWS, HIN, HOUT>(buf, tw, lt_, FromSmem{}, dst);
     } else {
-        sstage<T, E, L2, S, INV, TWS>(buf, tw, lt_, FromSmem{}, ToSmem{});
+        sstage<T, E, L2, S, INV, TWS, HIN, HOUT>(buf, tw, lt_, FromSmem{}, ToSmem{});
     }
-    if constexpr (S + 1 < NST) fft_static_from<T, E, L2, INV, TWS, Src, Dst, After0, S + 1>(buf, tw, lt, src, dst, after0);
+    if constexpr (S + 1 < NST)
+        fft_static_from<T, E, L2, INV, TWS, HIN, HOUT, Src, Dst, After0, S + 1>(buf, tw, lt, src, dst, after0);
 }
 
 // Whole transform of length 2^L2; same contract as fft_fused.
-template <typename T, int E, int L2, bool INV, bool TWS, class Src, class Dst, class After0>
+template <typename T, int E, int L2, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst, class After0>
 __device__ __forceinline__ void fft_static(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw, int lt,
                                            const Src &src, const Dst &dst, const After0 &after0)
 {
-    fft_static_from<T, E, L2, INV, TWS, Src, Dst, After0, 0>(buf, tw, lt, src, dst, after0);
+    fft_static_from<T, E, L2, INV, TWS, HIN, HOUT, Src, Dst, After0, 0>(buf, tw, lt, src, dst, after0);
 }
 
-// The pass kernels' transform: ED >= 1000 selects the static path for length 2^(ED - 1000);
-// otherwise the runtime-descriptor path of fft_fused with edge radices ED.
-template <typename T, int E, int ED, bool INV, bool TWS, class Src, class Dst, class After0 = NoHook>
+// The pass kernels' transform: ED >= 1000 selects the static path for length 2^(ED - 1000)
+// (which the host picks only for n = L/2, so HIN and HOUT hold there: zero-extended inputs,
+// cropped outputs); otherwise the runtime-descriptor path of fft_fused with edge radices ED,
+// which reads and writes every element.
+template <typename T, int E, int ED, bool INV, bool TWS, bool HIN = false, bool HOUT = false, class Src, class Dst,
+          class After0 = NoHook>
 __device__ __forceinline__ void fft_any(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
                                         const typename cvec<T>::t *__restrict__ tw, int lt, int tpt, const Src &src,
                                         const Dst &dst, const After0 &after0 = After0{})
 {
-    if constexpr (ED >= 1000) fft_static<T, E, ED - 1000, INV, TWS>(buf, tw, lt, src, dst, after0);
+    if constexpr (ED >= 1000) fft_static<T, E, ED - 1000, INV, TWS, HIN, HOUT>(buf, tw, lt, src, dst, after0);
     else fft_fused<T, E, ED, INV, TWS>(buf, P, tw, lt, tpt, src, dst, after0);
 }
+
+// Transform length of the compile-time path (0 for the runtime path).
+template <int ED> __host__ __device__ constexpr int static_len() { return ED >= 1000 ? 1 << (ED >= 1000 ? ED - 1000 : 0) : 0; }
 
 }  // namespace wsc

@@ -338,7 +338,8 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         tpt = generic_tpt(d);
     }
     if (tpt > maxT) return false;
-    const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d, fused_pref == 1) : 0;
+    // compile-time lengths only for n = L/2 (their transforms prune the zero half and the crop)
+    const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d, fused_pref == 1 && 2 * n == M) : 0;
     const bool fused = ed != 0;
     if (ed >= 1000) {
         // the compile-time-length kernels: radix-16 stages, their launch bound

@@ -17,6 +17,10 @@ namespace wsc {
 
 #define WSC_LBF(T, E, ED) __launch_bounds__(maxt_fused<T, E, ED>::v, 1)
 
+// The compile-time-length kernels run only for n = L/2 (the host selects them so): their forward
+// transforms see zero-extended halves and their inverse transforms' outputs are cropped to a half.
+template <int ED> __device__ constexpr bool halved() { return ED >= 1000; }
+
 // ---------------------------------------------------------------------------- prefetch
 // With a.pf set, each thread group fetches the input of its next work item (unit + stride) into
 // its staging area as soon as stage 0 of the current item has read the staged input, so the
@@ -147,7 +151,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const __grid_constant__ PassAr
             }
             return cmk<V>(x, y);
         };
-        fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
         if (a.tma) {
             // the previous item's stores have to have read the pairs before they are rewritten
             if (lt == 0) bulk_wait_read();
@@ -220,14 +224,14 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const __grid_constant__ PassArgs<T
             return a.pf ? stg[i] : col[i];
         };
         auto mul = smem_hook([&](int o, V &x) {
-            const int k1 = o <= M / 2 ? o : M - o;
+            const int Lm = halved<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             x = cscale(x, __ldg(&gc[k1]));
         });
-        fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -321,7 +325,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const __grid_constant__ PassAr
             oa[o] = ra;
             if (has2) oa[n + o] = rb;
         };
-        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -378,13 +382,13 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T
         };
         const V *gc = cg + (size_t)k2 * h;
         auto mul = smem_hook([&](int o, V &x) {
-            const int k1 = o <= M / 2 ? o : M - o;
+            const int Lm = halved<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             const V gk = __ldg(&gc[k1]);
             bim[pidx<T>(o)] = cscale(x, gk.y);
             x = cscale(x, gk.x);
         });
-        fft_any<T, E, ED, false, TWS>(bre, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
-        fft_any<T, E, ED, true, TWS>(bre, a.P, twp, lt, a.tpt, FromSmem{}, ToSmem{});
+        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(bre, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(bre, a.P, twp, lt, a.tpt, FromSmem{}, ToSmem{});
         V *cout = reinterpret_cast<V *>(a.out) + 2 * co;
         auto dst = [&](int o, V xi) {
             if (!valid || o >= n) return;
@@ -398,7 +402,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T
             cout[2 * o] = xr;
             cout[2 * o + 1] = xi;
         };
-        fft_any<T, E, ED, true, TWS>(bim, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(bim, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -478,7 +482,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_rows_inv(const __grid_constant__ PassAr
             if (a.beta != (T)0) z.x += a.beta * ua[o];
             o_[o] = z;
         };
-        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -529,7 +533,7 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_rows_fwd(const __grid_constant__ PassAr
         auto dst = [&](int o, V z) {
             if (valid) Wb[(size_t)o * n + j1] = z;
         };
-        fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
         __syncthreads();
     }
 }
@@ -571,15 +575,15 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_cols(const __grid_constant__ PassArgs<T
             return a.pf ? stg[i] : col[i];
         };
         auto mul = smem_hook([&](int o, V &x) {
-            const int k1 = o <= M / 2 ? o : M - o;
+            const int Lm = halved<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             if (CG) x = cmul(x, __ldg(reinterpret_cast<const V *>(a.ghat) + (size_t)k2q * h + k1));
             else x = cscale(x, __ldg(reinterpret_cast<const T *>(a.ghat) + (size_t)k2q * h + k1));
         });
-        fft_any<T, E, ED, false, TWS>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -631,7 +635,7 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_rows_inv(const __grid_constant__ PassAr
             }
             o_[o] = z;
         };
-        fft_any<T, E, ED, true, TWS>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();

@@ -285,6 +285,24 @@ def test_compile_time_lengths_match_oracle_and_runtime_stages(n, io, monkeypatch
         assert _relerr(outs[1][i], outs[0][i]) <= 1e-6
 
 
+@pytest.mark.parametrize("io", ["r2r", "r2c"])
+def test_compile_time_length_on_the_period_2_grid(io):
+    """b = 2 makes M = 2n a power of two without the compact embedding: the compile-time
+    transforms (zero half pruned, cropped half) on the paper's own period-b multiplier."""
+    n, B = 1024, 2
+    kw = KERNELS["log" if io == "r2r" else "helm20"]
+    plan = ConvPlan(n=n, period=2, trunc_a=0.9, precision="fp32", io=io, batch_max=B, **kw)
+    assert plan.info.static_log2 == 11
+    u = inputs.bump_sums(n, B, seed=77)
+    out = plan.apply(torch.tensor(u, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+    plan.device_status()
+    ref = _oracle_conv(u, plan, kw)
+    if io == "r2r":
+        ref = ref.real
+    for i in range(B):
+        assert _relerr(ref[i], out[i]) <= TOL["fp32"]
+
+
 @pytest.mark.parametrize("compact", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_full_size_helmholtz_r2c(prec, compact):
