@@ -183,6 +183,18 @@ static int generic_tpt(const FFTDesc &P)
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 130; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 130; constexpr bool W_ = false; CALL; } \
         } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1008) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1008; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 1008; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1009) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1009; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 1009; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1010) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1010; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 1010; constexpr bool W_ = false; CALL; } \
+        } \
         else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1011) { \
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1011; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 1011; constexpr bool W_ = false; CALL; } \
@@ -222,7 +234,10 @@ static int generic_tpt(const FFTDesc &P)
     } while (0)
 
 static const int kFusedSets[][3] = {
-    {1, 16, 1011},  // static power-of-two lengths 2^11, 2^12, 2^13
+    {1, 16, 1008},  // compile-time power-of-two lengths 2^8 ... 2^13
+    {1, 16, 1009},
+    {1, 16, 1010},
+    {1, 16, 1011},
     {1, 16, 1012},
     {1, 16, 1013},
     {1, 24, 131},
