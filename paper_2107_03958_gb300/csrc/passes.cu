@@ -31,7 +31,8 @@ namespace wsc {
 // Per-thread element counts with exact (unguarded) kernels, in order of preference.  A count E
 // admits radices dividing E; FP64 prefers radix-4 stages (E = 12 or 8), FP32 radix-8 (E = 24 or
 // 16).  E = 0 is the generic guarded path (any 2^a 3^b 5^c).
-static const int kElems64[] = {12, 24, 8, 0};
+// FP64 E = 16 exists only as the compile-time-length transforms (radix 16, 128 registers)
+static const int kElems64[] = {16, 12, 24, 8, 0};
 static const int kElems32[] = {24, 16, 0};
 
 static int max_threads(conv_precision prec, int E)
@@ -183,6 +184,22 @@ static int generic_tpt(const FFTDesc &P)
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 130; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 130; constexpr bool W_ = false; CALL; } \
         } \
+        else if ((prec) == CONV_P_FP64 && (E) == 16 && (ED) == 1010) { \
+            if (tws) { typedef double T_; constexpr int E_ = 16, ED_ = 1010; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 16, ED_ = 1010; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP64 && (E) == 16 && (ED) == 1011) { \
+            if (tws) { typedef double T_; constexpr int E_ = 16, ED_ = 1011; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 16, ED_ = 1011; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP64 && (E) == 16 && (ED) == 1012) { \
+            if (tws) { typedef double T_; constexpr int E_ = 16, ED_ = 1012; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 16, ED_ = 1012; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP64 && (E) == 16 && (ED) == 1013) { \
+            if (tws) { typedef double T_; constexpr int E_ = 16, ED_ = 1013; constexpr bool W_ = true; CALL; } \
+            else { typedef double T_; constexpr int E_ = 16, ED_ = 1013; constexpr bool W_ = false; CALL; } \
+        } \
         else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1008) { \
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1008; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 1008; constexpr bool W_ = false; CALL; } \
@@ -234,7 +251,11 @@ static int generic_tpt(const FFTDesc &P)
     } while (0)
 
 static const int kFusedSets[][3] = {
-    {1, 16, 1008},  // compile-time power-of-two lengths 2^8 ... 2^13
+    {0, 16, 1010},  // FP64 compile-time power-of-two lengths 2^10 ... 2^13
+    {0, 16, 1011},
+    {0, 16, 1012},
+    {0, 16, 1013},
+    {1, 16, 1008},  // FP32 compile-time power-of-two lengths 2^8 ... 2^13
     {1, 16, 1009},
     {1, 16, 1010},
     {1, 16, 1011},
@@ -356,6 +377,7 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
     // compile-time lengths only for n = L/2 (their transforms prune the zero half and the crop)
     const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d, fused_pref == 1 && 2 * n == M) : 0;
     const bool fused = ed != 0;
+    if (p->prec == CONV_P_FP64 && E == 16 && ed < 1000) return false;  // no runtime FP64 E = 16 kernels
     if (ed >= 1000) {
         // the compile-time-length kernels: radix-16 stages, their launch bound
         if (!factorize(M, E, d, true)) return false;
@@ -475,7 +497,7 @@ conv_status select_transform(conv_plan_s *p)
     conv_status rc = device_limits(p, smem_optin, sms);
     if (rc != CONV_OK) return rc;
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
-    const int ncand = p->prec == CONV_P_FP64 ? 4 : 3;
+    const int ncand = p->prec == CONV_P_FP64 ? (int)(sizeof kElems64 / sizeof(int)) : (int)(sizeof kElems32 / sizeof(int));
     auto env = [](const char *k, int dflt) {
         const char *v = getenv(k);
         return v ? atoi(v) : dflt;
@@ -510,7 +532,7 @@ std::vector<std::vector<Candidate>> transform_families(conv_plan_s *p)
     int smem_optin = 0, sms = 0;
     if (device_limits(p, smem_optin, sms) != CONV_OK) return out;
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
-    const int ncand = p->prec == CONV_P_FP64 ? 4 : 3;
+    const int ncand = p->prec == CONV_P_FP64 ? (int)(sizeof kElems64 / sizeof(int)) : (int)(sizeof kElems32 / sizeof(int));
     conv_plan_s probe = *p;
     probe.tev_used.clear();
     probe.tev_free.clear();

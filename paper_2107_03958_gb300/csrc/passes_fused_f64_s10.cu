@@ -1,0 +1,11 @@
+// passes_fused_f64_s10.cu -- FP64, 16 elements per thread, transform length 2^10 fixed at compile time:
+// instantiations of the fused-transform pass kernels.
+#include "passes_fused.cuh"
+
+namespace wsc {
+template conv_status run_fused<double, 16, 1010>(conv_plan_s *, const void *, const void *, void *, int, double, double, double, void *, cudaStream_t);
+template conv_status set_attrs_fused<double, 16, 1010, true>(int);
+template int blocks_per_sm_fused<double, 16, 1010, true>(int, size_t);
+template conv_status set_attrs_fused<double, 16, 1010, false>(int);
+template int blocks_per_sm_fused<double, 16, 1010, false>(int, size_t);
+}  // namespace wsc

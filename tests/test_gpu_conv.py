@@ -259,9 +259,9 @@ def test_autotuned_plan_matches_oracle(name, io, prec):
 
 
 @pytest.mark.parametrize("io", ["r2r", "r2c", "c2c"])
-@pytest.mark.parametrize("n", [1024, 2048])
-def test_compile_time_lengths_match_oracle_and_runtime_stages(n, io, monkeypatch):
-    """FP32 compact embedding, L = 2n = 2^11, 2^12: the transforms whose stage structure is fixed at
+@pytest.mark.parametrize("n,prec", [(1024, "fp32"), (2048, "fp32"), (512, "fp64"), (1024, "fp64")])
+def test_compile_time_lengths_match_oracle_and_runtime_stages(n, prec, io, monkeypatch):
+    """Compact embedding, L = 2n = 2^10 ... 2^12: the transforms whose stage structure is fixed at
     compile time match the oracle and the runtime-descriptor transforms of the same plan."""
     kw = KERNELS["helm20" if io != "r2r" else "pow-1"]
     B = 2
@@ -272,7 +272,7 @@ def test_compile_time_lengths_match_oracle_and_runtime_stages(n, io, monkeypatch
     outs = []
     for fused in ("1", "2"):
         monkeypatch.setenv("WSCONV_FUSED", fused)
-        plan = ConvPlan(n=n, period=3, precision="fp32", io=io, batch_max=B, compact=True, **kw)
+        plan = ConvPlan(n=n, period=3, precision=prec, io=io, batch_max=B, compact=True, **kw)
         info = plan.info
         assert info.fused == 1 and info.static_log2 == (int(np.log2(2 * n)) if fused == "1" else 0)
         outs.append(plan.apply(torch.tensor(u, dtype=plan.in_dtype(), device="cuda")).cpu().numpy())
@@ -281,8 +281,8 @@ def test_compile_time_lengths_match_oracle_and_runtime_stages(n, io, monkeypatch
     if io == "r2r":
         ref = ref.real
     for i in range(B):
-        assert _relerr(ref[i], outs[0][i]) <= TOL["fp32"]
-        assert _relerr(outs[1][i], outs[0][i]) <= 1e-6
+        assert _relerr(ref[i], outs[0][i]) <= TOL[prec]
+        assert _relerr(outs[1][i], outs[0][i]) <= (1e-6 if prec == "fp32" else 1e-13)
 
 
 @pytest.mark.parametrize("io", ["r2r", "r2c"])
