@@ -200,6 +200,9 @@ const char *conv_last_error(void);
  * With an FP32 plan and opts->refine != 0 the solve is mixed precision: an outer FP64 residual
  * r = f - L x (FP64 matvec built internally), an inner FP32-matvec GMRES on L d = r to
  * opts->inner_tol, x += d, until ||r|| / ||f|| <= opts->tol.
+ * The first solve on a plan allocates its Krylov workspace ((restart + 1) n^2 complex128 and a few
+ * vectors) and keeps it with the plan, for later solves of the same n, until conv_destroy; a solve
+ * that starts while another uses it (another thread) allocates and frees its own.
  * Returns CONV_ENOTCONVERGED (with info filled) when max_iters is reached. */
 typedef struct {
     int restart;       /* Krylov dimension per cycle (default 50) */

@@ -12,6 +12,7 @@
 //   r = f - L64 x (FP64 operator),  solve L32 d = r to inner_tol by GMRES (FP32 matvec, FP64
 //   Arnoldi),  x += d,  until ||r|| / ||f|| <= tol.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "wsconv_internal.h"
@@ -235,6 +236,24 @@ struct LsWork {
     double *host_res = nullptr;  // pinned
 };
 
+static bool alloc_work(LsWork &W, long long N, int restart, bool mixed)
+{
+    bool ok = cudaMalloc(&W.V, (size_t)(restart + 1) * N * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&W.w, N * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&W.r, N * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&W.d, N * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&W.partial, (size_t)51 * LS_RED_BLOCKS * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&W.st, sizeof(GmresState)) == cudaSuccess &&
+              cudaMallocHost(&W.host_res, sizeof(double)) == cudaSuccess;
+    if (ok && mixed)
+        ok = cudaMalloc(&W.x64, N * sizeof(double2)) == cudaSuccess &&
+             cudaMalloc(&W.v32, N * sizeof(float2)) == cudaSuccess &&
+             cudaMalloc(&W.w32, N * sizeof(float2)) == cudaSuccess &&
+             cudaMalloc(&W.m32, N * sizeof(float)) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+}
+
 static void free_work(LsWork &W)
 {
     cudaFree(W.V);
@@ -248,6 +267,27 @@ static void free_work(LsWork &W)
     cudaFree(W.partial);
     cudaFree(W.st);
     if (W.host_res) cudaFreeHost(W.host_res);
+    W = LsWork();
+}
+
+// A plan's Krylov workspace, kept from one solve to the next (allocation and the device-wide sync
+// of cudaFree would otherwise cost each solve).  One solve at a time uses it; a solve that finds it
+// in use allocates its own.
+struct LsCache {
+    std::mutex mu;
+    LsWork W;
+    long long N = 0;
+    int restart = 0;
+    bool mixed = false;
+};
+static std::mutex g_ls_cache_mu;
+
+void destroy_ls_cache(conv_plan_s *p)
+{
+    if (!p->ls_cache) return;
+    free_work(p->ls_cache->W);
+    delete p->ls_cache;
+    p->ls_cache = nullptr;
 }
 
 struct Solver {
@@ -395,20 +435,32 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     S.grid_elem = (int)std::min<long long>((N + 255) / 256, (long long)sms * 8);
-    bool ok = cudaMalloc(&S.W.V, (size_t)(o.restart + 1) * N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&S.W.w, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&S.W.r, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&S.W.d, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&S.W.partial, (size_t)51 * LS_RED_BLOCKS * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&S.W.st, sizeof(GmresState)) == cudaSuccess &&
-              cudaMallocHost(&S.W.host_res, sizeof(double)) == cudaSuccess;
-    if (ok && p->prec == CONV_P_FP32)
-        ok = cudaMalloc(&S.W.x64, N * sizeof(double2)) == cudaSuccess &&
-             cudaMalloc(&S.W.v32, N * sizeof(float2)) == cudaSuccess &&
-             cudaMalloc(&S.W.w32, N * sizeof(float2)) == cudaSuccess &&
-             cudaMalloc(&S.W.m32, N * sizeof(float)) == cudaSuccess;
-    if (!ok) {
-        cudaGetLastError();
+    // workspace: the plan's cached one when free (reallocated if too small), else a private one
+    const bool mixed = p->prec == CONV_P_FP32;
+    LsCache *cache;
+    {
+        std::lock_guard<std::mutex> g(g_ls_cache_mu);
+        if (!p->ls_cache) p->ls_cache = new LsCache();
+        cache = p->ls_cache;
+    }
+    std::unique_lock<std::mutex> own(cache->mu, std::try_to_lock);
+    const bool cached = own.owns_lock();
+    if (cached) {
+        if (cache->W.V && (cache->N != N || cache->restart < o.restart || (mixed && !cache->mixed))) {
+            cudaStreamSynchronize(st);
+            free_work(cache->W);
+        }
+        if (!cache->W.V) {
+            if (!alloc_work(cache->W, N, o.restart, mixed)) {
+                free_work(cache->W);
+                return fail(CONV_ENOMEM, "ls_solve workspace allocation failed");
+            }
+            cache->N = N;
+            cache->restart = o.restart;
+            cache->mixed = mixed;
+        }
+        S.W = cache->W;
+    } else if (!alloc_work(S.W, N, o.restart, mixed)) {
         free_work(S.W);
         return fail(CONV_ENOMEM, "ls_solve workspace allocation failed");
     }
@@ -481,7 +533,7 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
         }
     }
     cudaError_t ce = cudaStreamSynchronize(st);
-    free_work(S.W);
+    if (!cached) free_work(S.W);
     if (info) {
         info->iters = iters;
         info->restarts = cycles;

@@ -190,6 +190,7 @@ void conv_destroy(conv_plan_t p)
 {
     if (!p) return;
     destroy_hostpipe(p);
+    destroy_ls_cache(p);
     if (p->ghat64 && p->ghat64 != p->ghat_paper) cudaFree(p->ghat64);
     if (p->ghat_paper) cudaFree(p->ghat_paper);
     if (p->ghat32) cudaFree(p->ghat32);
