@@ -279,13 +279,27 @@ struct LsCache {
     long long N = 0;
     int restart = 0;
     bool mixed = false;
+    double *m64 = nullptr;                 // the solve's contrast, copied in (the graphs read it here)
+    std::vector<cudaGraphExec_t> iter;     // iteration j of a cycle, captured on first use
+    cudaStream_t cap = nullptr;            // private stream the captures run on (any caller stream,
+                                           // the legacy one included, can launch the graphs)
 };
+
+static void drop_graphs(LsCache *c)
+{
+    for (auto &g : c->iter)
+        if (g) cudaGraphExecDestroy(g);
+    c->iter.clear();
+}
 static std::mutex g_ls_cache_mu;
 
 void destroy_ls_cache(conv_plan_s *p)
 {
     if (!p->ls_cache) return;
+    drop_graphs(p->ls_cache);
     free_work(p->ls_cache->W);
+    cudaFree(p->ls_cache->m64);
+    if (p->ls_cache->cap) cudaStreamDestroy(p->ls_cache->cap);
     delete p->ls_cache;
     p->ls_cache = nullptr;
 }
@@ -300,6 +314,8 @@ struct Solver {
     LsWork W;
     cudaStream_t st;
     int grid_elem;
+    std::vector<cudaGraphExec_t> *graphs = nullptr;  // the cached workspace's iteration graphs, or none
+    cudaStream_t cap_stream = nullptr;               // where those graphs are captured
 
     // w = L v with the Krylov plan (FP64 or FP32 matvec), v and w FP64.
     conv_status matvec(const double2 *v, double2 *w)
@@ -335,6 +351,61 @@ struct Solver {
         return *W.host_res;
     }
 
+    // Arnoldi step j of a cycle: v_{j+1} from L v_j by CGS2, the Givens update of the Hessenberg
+    // column, and the new residual estimate copied to the pinned host word (not yet waited for).
+    conv_status enqueue_iteration(int j, int ldh)
+    {
+        double2 *vj = W.V + (size_t)j * N, *vn = W.V + (size_t)(j + 1) * N;
+        conv_status rc = matvec(vj, W.w);
+        if (rc != CONV_OK) return rc;
+        // CGS with one re-orthogonalisation: h = V^H w; w -= V h; h2 = V^H w; w -= V h2
+        for (int pass = 0; pass < 2; ++pass) {
+            k_multidot<<<LS_RED_BLOCKS, LS_RED_THREADS, 0, st>>>(W.V, N, j + 1, W.w, N, W.partial);
+            k_finalize_dots<<<j + 1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, j + 1, W.st->hcol + 0, pass);
+            // subtract with this pass's coefficients only: recompute them into y scratch
+            k_finalize_dots<<<j + 1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, j + 1, W.st->y, 0);
+            k_sub_combination<<<grid_elem, 256, 0, st>>>(W.V, N, j + 1, W.st->y, W.w, N);
+        }
+        norm2(W.w);
+        k_scale_by_invnorm<<<grid_elem, 256, 0, st>>>(W.w, vn, &W.st->nrm2, N);
+        k_gmres_givens<<<1, 32, 0, st>>>(W.st, j, ldh);
+        WSC_CUDA(cudaMemcpyAsync(W.host_res, &W.st->res, sizeof(double), cudaMemcpyDeviceToHost, st));
+        return CONV_OK;
+    }
+
+    // Step j as one graph launch when the workspace is the plan's: the ~17 launches of a step are
+    // captured once and replayed, so the GPU does not wait on the host's launches after every
+    // residual check.  Every pointer the step uses belongs to the plan or its cached workspace.
+    conv_status run_iteration(int j, int ldh)
+    {
+        if (!graphs || p->timing) return enqueue_iteration(j, ldh);
+        if ((int)graphs->size() <= j) graphs->resize(j + 1, nullptr);
+        cudaGraphExec_t &ex = (*graphs)[j];
+        if (!ex) {
+            // capture on the private stream, after the work the caller's stream holds
+            cudaGraph_t g = nullptr;
+            WSC_CUDA(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaStream_t user = st;
+            st = cap_stream;
+            conv_status rc = enqueue_iteration(j, ldh);
+            st = user;
+            cudaError_t ce = cudaStreamEndCapture(cap_stream, &g);
+            if (rc != CONV_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ce, "capture of a GMRES step");
+            ce = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) {
+                ex = nullptr;
+                return cuda_fail(ce, "instantiation of a GMRES step");
+            }
+        }
+        WSC_CUDA(cudaGraphLaunch(ex, st));
+        return CONV_OK;
+    }
+
     // GMRES on L z = b from z (FP64 device vectors) to ||b - L z|| <= tol_abs (Arnoldi estimate,
     // confirmed by the residual of the Krylov operator at restarts).
     conv_status gmres(const double2 *b, double2 *z, double tol_abs, int maxit, bool z_is_zero,
@@ -362,22 +433,11 @@ struct Solver {
             ++cycles;
             int j = 0;
             for (; j < restart && iters < maxit; ++j) {
-                double2 *vj = W.V + (size_t)j * N, *vn = W.V + (size_t)(j + 1) * N;
-                conv_status rc = matvec(vj, W.w);
+                conv_status rc = run_iteration(j, ldh);
                 if (rc != CONV_OK) return rc;
-                // CGS with one re-orthogonalisation: h = V^H w; w -= V h; h2 = V^H w; w -= V h2
-                for (int pass = 0; pass < 2; ++pass) {
-                    k_multidot<<<LS_RED_BLOCKS, LS_RED_THREADS, 0, st>>>(W.V, N, j + 1, W.w, N, W.partial);
-                    k_finalize_dots<<<j + 1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, j + 1, W.st->hcol + 0, pass);
-                    // subtract with this pass's coefficients only: recompute them into y scratch
-                    k_finalize_dots<<<j + 1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, j + 1, W.st->y, 0);
-                    k_sub_combination<<<grid_elem, 256, 0, st>>>(W.V, N, j + 1, W.st->y, W.w, N);
-                }
-                norm2(W.w);
-                k_scale_by_invnorm<<<grid_elem, 256, 0, st>>>(W.w, vn, &W.st->nrm2, N);
-                k_gmres_givens<<<1, 32, 0, st>>>(W.st, j, ldh);
                 ++iters;
-                double res = read_scalar(&W.st->res);
+                WSC_CUDA(cudaStreamSynchronize(st));
+                double res = *W.host_res;
                 res_out = res;
                 if (!(res == res)) return fail(CONV_ENONFINITE, "GMRES residual is not finite");
                 if (res <= tol_abs) {
@@ -448,7 +508,10 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
     if (cached) {
         if (cache->W.V && (cache->N != N || cache->restart < o.restart || (mixed && !cache->mixed))) {
             cudaStreamSynchronize(st);
+            drop_graphs(cache);
             free_work(cache->W);
+            cudaFree(cache->m64);
+            cache->m64 = nullptr;
         }
         if (!cache->W.V) {
             if (!alloc_work(cache->W, N, o.restart, mixed)) {
@@ -460,6 +523,22 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
             cache->mixed = mixed;
         }
         S.W = cache->W;
+        if (!mixed) {  // the FP64 matvec reads the contrast from the plan's copy
+            if (!cache->m64 && cudaMalloc(&cache->m64, N * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(CONV_ENOMEM, "ls_solve contrast buffer");
+            }
+            WSC_CUDA(cudaMemcpyAsync(cache->m64, m, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            S.m64 = cache->m64;
+        }
+        if (!cache->cap && cudaStreamCreateWithFlags(&cache->cap, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            cache->cap = nullptr;
+        }
+        if (cache->cap) {
+            S.graphs = &cache->iter;
+            S.cap_stream = cache->cap;
+        }
     } else if (!alloc_work(S.W, N, o.restart, mixed)) {
         free_work(S.W);
         return fail(CONV_ENOMEM, "ls_solve workspace allocation failed");
