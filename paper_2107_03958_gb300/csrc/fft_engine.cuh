@@ -46,6 +46,7 @@ struct FFTDesc {
     int tws[WSC_MAX_STAGES];                  // L / (Ns R)
     int toff[WSC_MAX_STAGES];                 // offset of stage s's twiddle block in the table
     int tw_len;                               // complex entries of the whole table
+    int tw_full16;                            // radix-16 stages hold all fifteen powers (FP64)
     unsigned long long mag[WSC_MAX_STAGES];  // ceil(2^40 / Ns): j / Ns == (j * mag) >> 40 for j < 2^24, Ns < 2^16
 };
 
@@ -212,8 +213,9 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x
 }
 
 // ---------------------------------------------------------------- twiddles
-// x[q] *= w^{qk}, q = 1..R-1, from the stage's block tab = [w^k | w^{2k} | w^{4k} | w^{8k}] (k < Ns;
-// only the blocks the radix needs): powers 1, 2, 4 (and 8) are read; the others are products.
+// x[q] *= w^{qk}, q = 1..R-1, from the stage's blocks (k < Ns): radices 2..8, and radix 16 in FP32,
+// read [w^k | w^{2k} | w^{4k} (| w^{8k})] (the blocks they need) and form the other powers as
+// products; FP64 radix 16 reads all fifteen powers [w^k | w^{2k} | ... | w^{15k}].
 template <typename T, bool TWS>
 __device__ __forceinline__ typename cvec<T>::t tw_load(const typename cvec<T>::t *__restrict__ tw, int t)
 {
@@ -226,6 +228,17 @@ __device__ __forceinline__ void apply_twiddles(typename cvec<T>::t *x, const typ
                                                int Ns, int k)
 {
     typedef typename cvec<T>::t V;
+    if constexpr (R == 16 && sizeof(T) == 8) {
+        // FP64 radix 16 reads all fifteen powers (block q-1 holds w^{qk}): its FP64 units are the
+        // bound, and loads cost less than eleven complex products
+#pragma unroll
+        for (int q = 1; q < 16; ++q) {
+            V w = tw_load<T, TWS>(tab, (q - 1) * Ns + k);
+            if (INV) w.y = -w.y;
+            x[q] = cmul(x[q], w);
+        }
+        return;
+    }
     V w1 = tw_load<T, TWS>(tab, k);
     if (INV) w1.y = -w1.y;
     x[1] = cmul(x[1], w1);
@@ -246,7 +259,7 @@ __device__ __forceinline__ void apply_twiddles(typename cvec<T>::t *x, const typ
     x[6] = cmul(x[6], w6);
     x[7] = cmul(x[7], w7);
     if constexpr (R == 8) return;
-    // radix 16: a fourth block w^{8k}; powers 9..15 = (1..7) + 8
+    // FP32 radix 16: a fourth block w^{8k}; powers 9..15 = (1..7) + 8
     V w8 = tw_load<T, TWS>(tab, 3 * Ns + k);
     if (INV) w8.y = -w8.y;
     x[8] = cmul(x[8], w8);

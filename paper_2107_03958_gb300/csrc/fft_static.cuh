@@ -18,11 +18,11 @@
 
 namespace wsc {
 
-__host__ __device__ constexpr int tw_blocks_c(int R) { return R == 2 ? 1 : (R <= 4 ? 2 : (R <= 8 ? 3 : 4)); }
+__host__ __device__ constexpr int tw_blocks_c(int R, bool full16) { return R == 2 ? 1 : (R <= 4 ? 2 : (R <= 8 ? 3 : (full16 ? 15 : 4))); }
 
 // Stage structure of a length-2^L2 transform: radix-16 stages, then one radix-2^(L2 mod 4) stage
 // (the host's factorize with radix16 set gives the same sequence and twiddle table).
-template <int L2> struct Pow2Stages {
+template <int L2, bool FULL16 = false> struct Pow2Stages {
     static constexpr int L = 1 << L2;
     static constexpr int N16 = L2 / 4, REM = L2 % 4;
     static constexpr int NST = N16 + (REM ? 1 : 0);
@@ -37,7 +37,7 @@ template <int L2> struct Pow2Stages {
     __host__ __device__ static constexpr int toff(int s)
     {
         int o = 0;
-        for (int i = 0; i < s; ++i) o += tw_blocks_c(R(i)) << lNs(i);
+        for (int i = 0; i < s; ++i) o += tw_blocks_c(R(i), FULL16) << lNs(i);
         return o;
     }
 };
@@ -51,7 +51,7 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
                                        const Src &src, const Dst &dst)
 {
     typedef typename cvec<T>::t V;
-    typedef Pow2Stages<L2> P;
+    typedef Pow2Stages<L2, sizeof(T) == 8> P;  // FP64 tables hold all fifteen radix-16 powers
     constexpr int R = P::R(S), lNs = P::lNs(S), Ns = 1 << lNs, RN = R * Ns;
     constexpr int TPT = P::L / E, NB = E / R, NBF = NB * TPT;
     constexpr int PS = pad_shift<T>::v, PAD = 1 << PS;

@@ -87,14 +87,17 @@ static int max_threads(conv_precision prec, int E)
     } while (0)
 
 // Twiddle powers a radix-R butterfly reads from its stage's table: w^k (R = 2); w^k, w^2k (R = 3,
-// 4; w^3k is their product); w^k, w^2k, w^4k (R = 5, 8); w^k, w^2k, w^4k, w^8k (R = 16); the
-// other powers are products.
-static inline int tw_blocks(int R) { return R == 2 ? 1 : (R <= 4 ? 2 : (R <= 8 ? 3 : 4)); }
+// 4; w^3k is their product); w^k, w^2k, w^4k (R = 5, 8; the other powers are products); all of
+// w^k, w^2k, w^4k, w^8k (R = 16 in FP32) or all of w^k ... w^15k (R = 16 in FP64, whose FP64 units
+// are the bound).
+static inline int tw_blocks(int R, bool full16) { return R == 2 ? 1 : (R <= 4 ? 2 : (R <= 8 ? 3 : (full16 ? 15 : 4))); }
+// power of w^k that block m holds: 2^m, or m + 1 for radix 16 with all fifteen powers
+static inline long long tw_power(int R, bool full16, int m) { return R == 16 && full16 ? m + 1 : 1LL << m; }
 
 // Radix sequence for L = 2^p 3^q 5^r whose radices divide E (E = 0: any of 8, 4, 2, 3, 5):
 // power-of-two radices first (8s when allowed, else 4s), then 3s, then 5s.  radix16: a power of
 // two as radix-16 stages and one stage for the remainder (the compile-time-length transforms).
-static bool factorize(int L, int E, FFTDesc &d, bool radix16 = false)
+static bool factorize(int L, int E, FFTDesc &d, bool radix16 = false, bool full16 = false)
 {
     int rem = L, p2 = 0, p3 = 0, p5 = 0;
     while (rem % 2 == 0) { rem /= 2; ++p2; }
@@ -131,11 +134,12 @@ static bool factorize(int L, int E, FFTDesc &d, bool radix16 = false)
         d.Ns[s] = (int)Ns;
         d.tws[s] = (int)(L / (Ns * R[s]));
         d.toff[s] = off;
-        off += tw_blocks(R[s]) * (int)Ns;
+        off += tw_blocks(R[s], full16) * (int)Ns;
         d.mag[s] = ((1ULL << 40) + (unsigned long long)Ns - 1) / (unsigned long long)Ns;
         Ns *= R[s];
     }
     d.tw_len = off;
+    d.tw_full16 = full16 ? 1 : 0;
     return true;
 }
 
@@ -147,9 +151,9 @@ void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im)
     re_im.assign(2 * (size_t)d.tw_len, 0.0);
     for (int s = 0; s < d.nst; ++s) {
         const long long Ns = d.Ns[s], NR = Ns * d.R[s];
-        for (int m = 0; m < tw_blocks(d.R[s]); ++m)
+        for (int m = 0; m < tw_blocks(d.R[s], d.tw_full16); ++m)
             for (long long k = 0; k < Ns; ++k) {
-                const long long e = ((1LL << m) * k) % NR;
+                const long long e = (tw_power(d.R[s], d.tw_full16, m) * k) % NR;
                 const long double ang = 2.0L * PI_L * (long double)e / (long double)NR;
                 const size_t i = (size_t)d.toff[s] + (size_t)m * Ns + (size_t)k;
                 re_im[2 * i] = (double)cosl(ang);
@@ -380,7 +384,7 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
     if (p->prec == CONV_P_FP64 && E == 16 && ed < 1000) return false;  // no runtime FP64 E = 16 kernels
     if (ed >= 1000) {
         // the compile-time-length kernels: radix-16 stages, their launch bound
-        if (!factorize(M, E, d, true)) return false;
+        if (!factorize(M, E, d, true, p->prec == CONV_P_FP64)) return false;
         maxT = std::min(maxT, WSC_STATIC_MAXT);
         if (tpt > maxT) return false;
     }
