@@ -367,6 +367,52 @@ def ls_leg(n, kappa, repeats, stream):
             "repeats": repeats, **out}
 
 
+def group_leg(reps, stream):
+    """Mixed-size batching: the serving mix's grid sizes (n = 128 ... 2048, counts falling with n as
+    the mix's weights do, the sweep's five kernels in turn, FP32 compact plans) applied once per
+    step, either one conv_apply per size on one stream or as one ConvGroup graph launch."""
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import ConvGroup, ConvPlan
+    sizes = [(128, 16), (256, 16), (512, 8), (1024, 4), (2048, 1)]
+    items = []
+    for i, (n, b) in enumerate(sizes):
+        kern, kw = SWEEP[i % len(SWEEP)]
+        io = "r2c" if kern == "helmholtz" else "r2r"
+        p = ConvPlan(kern, n=n, period=3, precision="fp32", io=io, batch_max=b, compact=True, **kw)
+        u = torch.from_numpy(inputs.bump_sums(n, b, seed=900 + i)).float().cuda()
+        items.append((p, u, torch.empty((b, n, n), dtype=p.out_dtype(), device="cuda")))
+    g = ConvGroup(items)
+    convs = sum(b for _, b in sizes)
+
+    def seq():
+        for p, u, o in items:
+            p.apply(u, out=o, stream=stream)
+
+    def grp():
+        g.launch(stream)
+
+    out = {}
+    for name, fn in (("sequential", seq), ("group", grp)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"conv_per_s": convs / (ms * 1e-3), "ms_per_step": ms}
+    for p, _, _ in items:
+        p.device_status()
+    return {"sizes_batches": sizes, "convolutions_per_step": convs, "reps": reps,
+            "launches_per_step": {"sequential": 3 * len(sizes), "group": "1 graph of %d kernels" % (3 * len(sizes))},
+            "working_set": "about 0.2 GB of inputs, outputs and spectra, partly L2-resident", **out,
+            "speedup": out["sequential"]["ms_per_step"] / out["group"]["ms_per_step"]}
+
+
 def profile_case(args):
     """Small fixed case for ncu captures: one plan, warmup + steps applies, nothing else."""
     import torch
@@ -569,6 +615,8 @@ def main():
         extras["fp32_n%d" % n2] = {"value": ws * 5 * args.batch * args.steps / (l2_ms * 1e-3),
                                    "unit": "conv/s", "ms_per_step": l2_ms / args.steps}
         extras["ls"] = ls_leg(512, 40.0, 5, stream)
+        extras["ls_larger"] = [ls_leg(1024, 40.0, 3, stream), ls_leg(2048, 40.0, 3, stream)]
+        extras["mixed_group"] = group_leg(50, stream)
         extras["serving"] = serving_leg(80)
 
     if rank == 0:

@@ -149,6 +149,36 @@ conv_status conv_apply_host(conv_plan_t plan, const void *u_host, const void *ma
 conv_status conv_apply_noalloc(conv_plan_t plan, const void *u, const void *mask, void *out,
                                int batch, void *stream);
 
+/* Mixed-size batching (no counterpart in the paper; a serving aid for the convolutions of
+ * Sec. 2.1, eq. (An)).  A group is a fixed list of `count` applies,
+ *     out[i] = A_n(u[i] . mask[i])   on plans[i], batch[i] densities,
+ * whose plans may differ in n, kernel, period, precision and io.  conv_group_create captures the
+ * items' pass kernels into one CUDA graph and instantiates it; each conv_group_launch then runs
+ * every item with one graph launch on `stream`.
+ *   Items on different plans are concurrent branches of the graph, so the passes of small grids,
+ *   which do not fill the GPU alone, run side by side.  Items on one plan share its workspace
+ *   and run in list order on one branch.
+ *   plans, u, out, batch: arrays of `count` entries; u[i], out[i] as in conv_apply for plans[i];
+ *   mask: NULL, or an array of `count` entries each NULL or as conv_apply's mask;
+ *   batch[i] in [0, batch_max of plans[i]] (0 skips the item).
+ *   The pointers are fixed in the graph: every launch reads u[i] and writes out[i] as given at
+ *   creation (their contents may change between launches).  The plans and buffers must outlive
+ *   the group, and no other call on one of its plans may overlap a launch.
+ *   Every plan must be on the current device, with per-pass timing off.
+ *   A pass kernel's given-up bounded wait is reported in its plan's status word
+ *   (conv_device_status on that plan).
+ * Returns CONV_EINVAL for bad arguments: count < 1, an item conv_apply would reject, an out[i]
+ * equal to another item's u or out (ranges are not checked for partial overlap).  Returns
+ * CONV_ECUDA when capture or instantiation fails. */
+typedef struct conv_group_s *conv_group_t;
+conv_status conv_group_create(int count, const conv_plan_t *plans, const void *const *u, const void *const *mask,
+                              void *const *out, const int *batch, conv_group_t *group);
+/* One graph launch of every item, ordered on `stream` like conv_apply.  Returns CONV_EINVAL when
+ * the current device is not the group's. */
+conv_status conv_group_launch(conv_group_t group, void *stream);
+/* Frees the graph (the plans and buffers stay the caller's).  Call it with no launch in flight. */
+void conv_group_destroy(conv_group_t group);
+
 /* Generalised apply used by the Lippmann-Schwinger operator (Sec. 3.3, eq. (descretls)):
  *     out = beta * u + alpha * A_n(u . mask)
  * with complex alpha (alpha_re, alpha_im) and real beta; C2C/R2C plans only when beta != 0 needs a

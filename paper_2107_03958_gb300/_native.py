@@ -101,6 +101,12 @@ PROTOTYPES = {
                                 ctypes.POINTER(SrvResult)]),
     "srv_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SrvStats)]),
     "srv_destroy": (None, [ctypes.c_void_p]),
+    "conv_group_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "conv_group_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "conv_group_destroy": (None, [ctypes.c_void_p]),
     "conv_measure_peaks": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]),

@@ -176,6 +176,56 @@ class ConvPlan:
         return buf
 
 
+class ConvGroup:
+    """Several applies, on plans that may differ in n, kernel, precision and io, run as one CUDA
+    graph launch (items on different plans run concurrently; items on one plan in order).
+
+        g = ConvGroup([(plan_a, u_a, out_a), (plan_b, u_b, out_b, mask_b)])
+        g.launch()      # out_i = A_n(u_i * mask_i) for every item, one graph launch
+
+    The tensors are fixed at creation: launch() reads and writes the same storage every time
+    (its contents may change between launches); the group keeps the plans and tensors alive."""
+
+    def __init__(self, items):
+        self._lib = N.load()
+        plans, us, masks, outs, batches = [], [], [], [], []
+        for it in items:
+            plan, u, out = it[0], it[1], it[2]
+            mask = it[3] if len(it) > 3 else None
+            plan._check_grid(u, plan.in_dtype(), "u")
+            plan._check_grid(out, plan.out_dtype(), "out")
+            if out.shape != u.shape:
+                raise ValueError("out must have u's shape")
+            if mask is not None:
+                plan._check_grid(mask, plan.real_dtype, "mask")
+            plans.append(plan.handle.value)
+            us.append(u.data_ptr())
+            outs.append(out.data_ptr())
+            masks.append(mask.data_ptr() if mask is not None else None)
+            batches.append(1 if u.dim() == 2 else int(np.prod(u.shape[:-2])))
+        k = len(plans)
+        arr = ctypes.c_void_p * k
+        h = ctypes.c_void_p()
+        N.check(self._lib.conv_group_create(k, arr(*plans), arr(*us), arr(*masks), arr(*outs),
+                                            (ctypes.c_int * k)(*batches), ctypes.byref(h)))
+        self._h = h
+        self._keep = list(items)
+
+    def launch(self, stream=None):
+        N.check(self._lib.conv_group_launch(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.conv_group_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def ls_solve(plan, m, f, x=None, restart=50, max_iters=2000, tol=1e-10, refine=False,
              inner_tol=1e-5, stream=None):
     """Solve u + kappa^2 A_n(m u) = f (Sec. 3.3, eq. (descretls)) by restarted GMRES.

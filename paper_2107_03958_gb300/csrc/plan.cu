@@ -178,6 +178,35 @@ cudaEvent_t *timing_slot(conv_plan_s *p)
 
 static size_t elem_bytes(const conv_plan_s *p) { return p->prec == CONV_P_FP64 ? 16 : 8; }
 
+// Argument checks shared by every apply entry point; on success *ws is the workspace to use
+// (the caller's, or the plan's for batch <= batch_max).
+conv_status check_apply(conv_plan_s *p, const void *u, const void *mask, const void *out, int batch,
+                        double alpha_im, void *workspace, void **ws)
+{
+    if (!p) return fail(CONV_EINVAL, "plan is NULL");
+    if (batch < 0) return fail(CONV_EINVAL, "batch must be >= 0");
+    if (batch == 0) return CONV_OK;
+    if (!u || !out) return fail(CONV_EINVAL, "u and out must be device pointers");
+    if (u == out) return fail(CONV_EINVAL, "out must not alias u");
+    if (p->io == CONV_IO_R2R && alpha_im != 0.0)
+        return fail(CONV_EINVAL, "a real-to-real plan needs a real alpha");
+    if (batch > 65535) return fail(CONV_EINVAL, "batch must be <= 65535");
+    // element alignment of the caller's arrays; 16 bytes for a caller's workspace
+    const size_t rb = p->prec == CONV_P_FP64 ? 8 : 4;
+    auto al = [](const void *q, size_t m) { return (reinterpret_cast<uintptr_t>(q) % m) == 0; };
+    if (!al(u, p->io == CONV_IO_C2C ? 2 * rb : rb) || !al(out, p->io == CONV_IO_R2R ? rb : 2 * rb) ||
+        (mask && !al(mask, rb)))
+        return fail(CONV_EINVAL, "u, out and mask must be aligned to their element size");
+    if (workspace && !al(workspace, 16)) return fail(CONV_EINVAL, "the workspace must be 16-byte aligned");
+    *ws = workspace;
+    if (!workspace) {
+        if (batch > p->batch_max)
+            return fail(CONV_EINVAL, "batch exceeds the plan's batch_max; pass a workspace");
+        *ws = p->ws;
+    }
+    return CONV_OK;
+}
+
 }  // namespace wsc
 
 using namespace wsc;
@@ -352,27 +381,9 @@ conv_status conv_apply_axpby(conv_plan_t p, const void *u, const void *mask, voi
                              double alpha_re, double alpha_im, double beta, void *workspace,
                              void *stream)
 {
-    if (!p) return fail(CONV_EINVAL, "plan is NULL");
-    if (batch < 0) return fail(CONV_EINVAL, "batch must be >= 0");
-    if (batch == 0) return CONV_OK;
-    if (!u || !out) return fail(CONV_EINVAL, "u and out must be device pointers");
-    if (u == out) return fail(CONV_EINVAL, "out must not alias u");
-    if (p->io == CONV_IO_R2R && alpha_im != 0.0)
-        return fail(CONV_EINVAL, "a real-to-real plan needs a real alpha");
-    if (batch > 65535) return fail(CONV_EINVAL, "batch must be <= 65535");
-    // element alignment of the caller's arrays; 16 bytes for a caller's workspace
-    const size_t rb = p->prec == CONV_P_FP64 ? 8 : 4;
-    auto al = [](const void *q, size_t m) { return (reinterpret_cast<uintptr_t>(q) % m) == 0; };
-    if (!al(u, p->io == CONV_IO_C2C ? 2 * rb : rb) || !al(out, p->io == CONV_IO_R2R ? rb : 2 * rb) ||
-        (mask && !al(mask, rb)))
-        return fail(CONV_EINVAL, "u, out and mask must be aligned to their element size");
-    if (workspace && !al(workspace, 16)) return fail(CONV_EINVAL, "the workspace must be 16-byte aligned");
-    void *ws = workspace;
-    if (!ws) {
-        if (batch > p->batch_max)
-            return fail(CONV_EINVAL, "batch exceeds the plan's batch_max; pass a workspace");
-        ws = p->ws;
-    }
+    void *ws = nullptr;
+    conv_status rc = check_apply(p, u, mask, out, batch, alpha_im, workspace, &ws);
+    if (rc != CONV_OK || batch == 0) return rc;
     return launch_pipeline(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws,
                            reinterpret_cast<cudaStream_t>(stream));
 }

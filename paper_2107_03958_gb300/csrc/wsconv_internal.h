@@ -126,6 +126,9 @@ struct conv_plan_s {
 namespace wsc {
 // plan.cu: timing marks; returns the event set for this apply (nullptr when timing is off)
 cudaEvent_t *timing_slot(conv_plan_s *p);
+// plan.cu: the argument checks of every apply entry point
+conv_status check_apply(conv_plan_s *p, const void *u, const void *mask, const void *out, int batch,
+                        double alpha_im, void *workspace, void **ws);
 // passes.cu
 conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
                             double alpha_re, double alpha_im, double beta, void *ws,
