@@ -499,6 +499,41 @@ def serving_leg(count, seed=5):
             "plans_built": stats["plans_built"], "mix": "50% conv / 50% LS, Poisson 200/s"}
 
 
+def served_ls_burst(count, seed=5):
+    """The LS requests of the serving mix (n from the mix's sizes, kappa ~ U[5, 60], tolerance
+    1e-10), all submitted at once to a server whose plans are already resident (one untimed pass
+    first): saturated solves/s of the served mixed-precision path against the served all-FP64
+    path, with the final relative residual of each."""
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import Server
+    reqs = [r for r in inputs.serving_requests(count, rate=200.0, seed=seed) if r["kind"] == "ls"]
+    bufs = []
+    for r in reqs:
+        m = torch.tensor(inputs.lippmann_contrast(r["n"], "bump"), device="cuda")
+        f = torch.tensor(inputs.plane_wave(r["n"], r["kappa"]), device="cuda")
+        bufs.append((m, f, torch.zeros_like(f)))
+    out = {"solves": len(reqs), "sizes": sorted(set(r["n"] for r in reqs))}
+    for prec, name in (("fp32", "mixed"), ("fp64", "fp64")):
+        srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4, compact=True)
+        for timed in (False, True):
+            for b in bufs:
+                b[2].zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tickets = [srv.submit_ls(m, f, x, r["kappa"], precision=prec) for r, (m, f, x) in zip(reqs, bufs)]
+            res = [srv.wait(t, timeout_s=600) for t in tickets]
+            wall = time.perf_counter() - t0
+        srv.close()
+        lat = sorted(r["latency_s"] for r in res if r["status"] == "CONV_OK")
+        pct = lambda a, p: 1e3 * a[min(len(a) - 1, max(0, int(math.ceil(p * len(a))) - 1))] if a else None
+        out[name] = {"solves_per_s": len(lat) / wall, "wall_s": wall, "completed_ok": len(lat),
+                     "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
+                     "max_rel_residual": max(r["rel_residual"] for r in res)}
+    out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -618,6 +653,7 @@ def main():
         extras["ls_larger"] = [ls_leg(1024, 40.0, 3, stream), ls_leg(2048, 40.0, 3, stream)]
         extras["mixed_group"] = group_leg(50, stream)
         extras["serving"] = serving_leg(80)
+        extras["served_ls_burst"] = served_ls_burst(80)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "conv/s", "n_gpus": ws, "steps": args.steps,
