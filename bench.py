@@ -142,9 +142,18 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- traffic record
+# The files the pass kernels and their launches are built from: kernels, transforms and copies
+# (*.cuh), shared declarations (*.h), the launch configuration and instantiations (passes*.cu),
+# the multiplier tables (ghat.cu), the plan's sizes (plan.cu) and the TMA maps (tma.cu).  The
+# LS solver, serving runtime, host-buffer pipeline, graph groups, masks and peak probes are not.
+KERNEL_SOURCES = ("*.cuh", "*.h", "passes*.cu", "ghat.cu", "plan.cu", "tma.cu")
+
+
 def kernel_source_hash():
+    csrc = os.path.join(ROOT, "paper_2107_03958_gb300", "csrc")
+    files = sorted(set(f for pat in KERNEL_SOURCES for f in glob.glob(os.path.join(csrc, pat))))
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2107_03958_gb300", "csrc", "*"))):
+    for f in files:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

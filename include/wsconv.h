@@ -200,9 +200,11 @@ typedef struct {
     int elems;           /* complex elements per thread in the transform kernels (0: generic) */
     int smem_twiddles;   /* twiddle table staged in shared memory */
     int fused;           /* fused passes (global-memory first/last stages) */
-    int static_log2;     /* log2 of the transform length when its stage structure is fixed at
-                          * compile time (fused passes), else 0 */
+    int static_log2;     /* log2 of the transform length when it is a power of two whose stage
+                          * structure is fixed at compile time (fused passes), else 0 */
     int r2c_split;       /* R2C with complex ghat on the split pipeline (Re/Im ghat columns) */
+    int static_len;      /* the transform length when its stage structure is fixed at compile
+                          * time (2^l with n = L/2, or 3 2^l with n = L/3), else 0 */
 } conv_plan_info;
 
 conv_status conv_get_info(conv_plan_t plan, conv_plan_info *info);

@@ -123,6 +123,53 @@ template <bool INV, typename V> __device__ __forceinline__ void dft8(V *x) {
     x[7] = csub(e[3], o3);
 }
 
+// x w8^1 and x w8^3 (forward w8 = e^{-i pi/4}; inverse conjugate)
+template <bool INV, typename V> __device__ __forceinline__ V w8_1(V x)
+{
+    typedef decltype(V::x) T;
+    const T r2 = (T)0.7071067811865475244008443621048490;
+    return INV ? cmk<V>((x.x - x.y) * r2, (x.x + x.y) * r2) : cmk<V>((x.x + x.y) * r2, (x.y - x.x) * r2);
+}
+template <bool INV, typename V> __device__ __forceinline__ V w8_3(V x)
+{
+    typedef decltype(V::x) T;
+    const T r2 = (T)0.7071067811865475244008443621048490;
+    return INV ? cmk<V>((-x.x - x.y) * r2, (x.x - x.y) * r2) : cmk<V>((x.y - x.x) * r2, (-x.x - x.y) * r2);
+}
+
+// Radix-8 DFT of x0, x1, x2 with x3 ... x7 zero (the first stage of a length-3m transform whose
+// inputs beyond m are the zero extension): X_p = x0 + w^p x1 + w^2p x2.  The terms x0 + w^2p x2
+// repeat with period 4 and w^(p+4) = -w^p, so X_p and X_(p+4) share them.
+template <bool INV, typename V> __device__ __forceinline__ void dft8_in3(V *x)
+{
+    const V a = x[0], b = x[1], c = x[2], rc = rot<INV>(c);
+    const V e0 = cadd(a, c), e1 = cadd(a, rc), e2 = csub(a, c), e3 = csub(a, rc);
+    const V o1 = w8_1<INV>(b), o2 = rot<INV>(b), o3 = w8_3<INV>(b);
+    x[0] = cadd(e0, b);
+    x[4] = csub(e0, b);
+    x[1] = cadd(e1, o1);
+    x[5] = csub(e1, o1);
+    x[2] = cadd(e2, o2);
+    x[6] = csub(e2, o2);
+    x[3] = cadd(e3, o3);
+    x[7] = csub(e3, o3);
+}
+
+// Radix-8 DFT of x0, x1 with x2 ... x7 zero: X_p = x0 + w^p x1, X_(p+4) = x0 - w^p x1.
+template <bool INV, typename V> __device__ __forceinline__ void dft8_in2(V *x)
+{
+    const V a = x[0], b = x[1];
+    const V o1 = w8_1<INV>(b), o2 = rot<INV>(b), o3 = w8_3<INV>(b);
+    x[0] = cadd(a, b);
+    x[4] = csub(a, b);
+    x[1] = cadd(a, o1);
+    x[5] = csub(a, o1);
+    x[2] = cadd(a, o2);
+    x[6] = csub(a, o2);
+    x[3] = cadd(a, o3);
+    x[7] = csub(a, o3);
+}
+
 // x * (a + i b) for a constant unit root, conjugated for the inverse transform
 template <bool INV, typename V> __device__ __forceinline__ V cmulc(V x, decltype(V::x) a, decltype(V::x) b)
 {

@@ -1,7 +1,10 @@
 // fft_static.cuh -- the fused Stockham transform of fft_fused.cuh for a length fixed at compile
-// time, L = 2^L2, in radix-16 stages (and one radix-2, -4 or -8 stage for the remaining factor):
-// one shared-memory round trip per four bits, and no stage with Ns = 8, whose stride-8 stores
-// conflict in the padded layout.
+// time, in two families:
+//   ED = 1000 + l: L = 2^l in radix-16 stages (and one radix-2, -4 or -8 stage for the remaining
+//     factor): one shared-memory round trip per four bits, and no stage with Ns = 8, whose
+//     stride-8 stores conflict in the padded layout;
+//   ED = 2000 + l: L = 3 2^l (the period-3 grid, L = 3n) in radix-8 stages, one radix-4 or -2
+//     stage for l mod 3, and a last radix-3 stage.
 //
 // With R, Ns and the thread count known, every shared-memory, twiddle and global index of a
 // stage is a per-thread base plus a compile-time offset:
@@ -10,6 +13,8 @@
 //            part (jq0, k0) and a constant (cj, ck) of butterfly b, and pidx(o) = T0 + C(b) + C(p),
 //            T0 from (jq0, k0), the constants from the padding period PAD = 2^PS (tpt, and so
 //            b tpt, is a multiple of PAD).
+// This needs every stage's Ns to be a power of two, which holds in both families: the radix-3
+// stage, the one radix that is not a power of two, comes last.
 // The runtime path recomputes these per element (shifts, magic-number divisions, stage-table
 // loads); here each stage computes a handful of per-thread bases and the rest folds into the
 // load/store immediates.
@@ -20,18 +25,21 @@ namespace wsc {
 
 __host__ __device__ constexpr int tw_blocks_c(int R, bool full16) { return R == 2 ? 1 : (R <= 4 ? 2 : (R <= 8 ? 3 : (full16 ? 15 : 4))); }
 
-// Stage structure of a length-2^L2 transform: radix-16 stages, then one radix-2^(L2 mod 4) stage
-// (the host's factorize with radix16 set gives the same sequence and twiddle table).
-template <int L2, bool FULL16 = false> struct Pow2Stages {
-    static constexpr int L = 1 << L2;
-    static constexpr int N16 = L2 / 4, REM = L2 % 4;
-    static constexpr int NST = N16 + (REM ? 1 : 0);
-    __host__ __device__ static constexpr int lR(int s) { return s < N16 ? 4 : REM; }
-    __host__ __device__ static constexpr int R(int s) { return 1 << lR(s); }
+// Stage structure of compile-time length ED (the host's factorize gives the same sequence and
+// twiddle table: with radix16 set for ED = 1000 + l, with E = 24 for ED = 2000 + l).
+template <int ED, bool FULL16 = false> struct StaticStages {
+    static constexpr bool X3 = ED >= 2000;                     // L = 3 2^L2
+    static constexpr int L2 = X3 ? ED - 2000 : ED - 1000;      // log2 of the power-of-two factor
+    static constexpr int L = X3 ? 3 << L2 : 1 << L2;
+    static constexpr int LR = X3 ? 3 : 4;                      // log2 of the main radix
+    static constexpr int NMAIN = L2 / LR, REM = L2 % LR;
+    static constexpr int NST = NMAIN + (REM ? 1 : 0) + (X3 ? 1 : 0);
+    __host__ __device__ static constexpr int R(int s) { return s < NMAIN ? 1 << LR : (s == NMAIN && REM ? 1 << REM : 3); }
+    // log2 Ns of stage s: the radices before it are all powers of two
     __host__ __device__ static constexpr int lNs(int s)
     {
         int v = 0;
-        for (int i = 0; i < s; ++i) v += lR(i);
+        for (int i = 0; i < s; ++i) v += i < NMAIN ? LR : REM;
         return v;
     }
     __host__ __device__ static constexpr int toff(int s)
@@ -43,15 +51,16 @@ template <int L2, bool FULL16 = false> struct Pow2Stages {
 };
 
 // One radix-R stage S; every thread owns E/R butterflies j = lt + b tpt.
-// HIN: the transform's inputs e >= L/2 are zero (a zero-extended half): stage 0 loads only
-// q < R/2 and runs the half-input butterfly.  HOUT: only outputs o < L/2 are used (a cropped
-// half): the last stage stores only p < R/2, and the arithmetic feeding the rest drops out.
-template <typename T, int E, int L2, int S, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst>
+// HIN: the transform's inputs e >= n are zero (the zero extension; n = L/2 or L/3): stage 0 loads
+// only the inputs below n and runs a butterfly with the others fixed at zero.
+// HOUT: only outputs o < n are used (the crop): the last stage stores only p < R/2 (n = L/2) or
+// p = 0 (n = L/3, the last radix is 3), and the arithmetic feeding the rest drops out.
+template <typename T, int E, int ED, int S, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst>
 __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw, int lt,
                                        const Src &src, const Dst &dst)
 {
     typedef typename cvec<T>::t V;
-    typedef Pow2Stages<L2, sizeof(T) == 8> P;  // FP64 tables hold all fifteen radix-16 powers
+    typedef StaticStages<ED, sizeof(T) == 8> P;  // FP64 tables hold all fifteen radix-16 powers
     constexpr int R = P::R(S), lNs = P::lNs(S), Ns = 1 << lNs, RN = R * Ns;
     constexpr int TPT = P::L / E, NB = E / R, NBF = NB * TPT;
     constexpr int PS = pad_shift<T>::v, PAD = 1 << PS;
@@ -59,8 +68,15 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
     static_assert(TPT % PAD == 0, "threads per transform must be a multiple of the padding period");
     constexpr bool SRC_SMEM = std::is_same<Src, FromSmem>::value;
     constexpr bool DST_SMEM = writes_smem<Dst>::value;
-    constexpr bool half_in = HIN && S == 0, half_out = HOUT && S == P::NST - 1;
-    static_assert(!half_in || R == 16, "the half-input butterfly is radix 16");
+    constexpr bool pin = HIN && S == 0, pout = HOUT && S == P::NST - 1;
+    static_assert(!pin || R == (P::X3 ? 8 : 16), "the pruned-input butterflies are radix 16 (n = L/2) or 8 (n = L/3)");
+    static_assert(!pout || !P::X3 || R == 3, "the period-3 family ends in its radix-3 stage");
+    // input q of butterfly b (elements b tpt + q L/R + [0, tpt)) lies wholly below n or wholly
+    // above it: n = L/2 is a multiple of L/R; for n = L/3, tpt = L/24 and R = 8 make the bound
+    // 3q + b <= 7 an integer one
+    constexpr int NIN = P::X3 ? P::L / 3 : P::L / 2;
+    static_assert(!pin || !P::X3 || E == 24, "the period-3 input pruning assumes 24 elements per thread");
+    constexpr int NOUT = pout ? (P::X3 ? 1 : R / 2) : R;
     __builtin_assume(lt >= 0 && lt < TPT);
     // per-thread bases of this stage
     const int pl = lt + (lt >> PS);
@@ -88,7 +104,7 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int c = b * TPT + q * NBF;
-            if (half_in && q >= R / 2) v[b][q] = cmk<V>(0, 0);
+            if (pin && c >= NIN) v[b][q] = cmk<V>(0, 0);
             else if constexpr (SRC_SMEM) v[b][q] = buf[pl + c + (c >> PS)];
             else v[b][q] = src(lt + c);
         }
@@ -98,11 +114,14 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
     for (int b = 0; b < NB; ++b) {
         const int cb = b * TPT, ck = cb & (Ns - 1), cj = cb >> lNs;
         if constexpr (Ns > 1) apply_twiddles<T, R, INV, TWS>(v[b], tw + P::toff(S) + ck, Ns, k0);
-        if constexpr (half_in) dft16_half_in<INV>(v[b]);
-        else dftR<R, INV>(v[b]);
+        if constexpr (pin && !P::X3) dft16_half_in<INV>(v[b]);
+        else if constexpr (pin) {
+            if (b * TPT + 2 * NBF < NIN) dft8_in3<INV>(v[b]);
+            else dft8_in2<INV>(v[b]);
+        } else dftR<R, INV>(v[b]);
         const int Cb = RN <= PAD ? cj * RN + ((cj * RN) >> PS) : cj * (RN + RN / PAD) + ck + (ck >> PS);
 #pragma unroll
-        for (int p = 0; p < (half_out ? R / 2 : R); ++p) {
+        for (int p = 0; p < NOUT; ++p) {
             const int Cp = RN <= PAD ? p * Ns : (Ns < PAD ? p * Ns + ((p * Ns) >> PS) : p * (Ns + Ns / PAD));
             const int o = O0 + cj * RN + ck + p * Ns;
             if constexpr (std::is_same<Dst, ToSmem>::value) {
@@ -120,50 +139,50 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
     if constexpr (DST_SMEM) __syncthreads();
 }
 
-template <typename T, int E, int L2, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst, class After0, int S>
+template <typename T, int E, int ED, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst, class After0, int S>
 __device__ __forceinline__ void fft_static_from(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw,
                                                 int lt, const Src &src, const Dst &dst, const After0 &after0)
 {
-    constexpr int NST = Pow2Stages<L2>::NST;
+    constexpr int NST = StaticStages<ED>::NST;
     static_assert(NST >= 2, "at least two stages");
     // keep each stage's per-thread bases from being hoisted to the kernel start (register pressure)
     int lt_ = lt;
     asm volatile("" : "+r"(lt_));
     if constexpr (S == 0) {
-        sstage<T, E, L2, 0, INV, TWS, HIN, HOUT>(buf, tw, lt_, src, ToSmem{});
+        sstage<T, E, ED, 0, INV, TWS, HIN, HOUT>(buf, tw, lt_, src, ToSmem{});
         after0();
     } else if constexpr (S == NST - 1) {
-        sstage<T, E, L2, S, INV, TWS, HIN, HOUT>(buf, tw, lt_, FromSmem{}, dst);
+        sstage<T, E, ED, S, INV, TWS, HIN, HOUT>(buf, tw, lt_, FromSmem{}, dst);
     } else {
-        sstage<T, E, L2, S, INV, TWS, HIN, HOUT>(buf, tw, lt_, FromSmem{}, ToSmem{});
+        sstage<T, E, ED, S, INV, TWS, HIN, HOUT>(buf, tw, lt_, FromSmem{}, ToSmem{});
     }
     if constexpr (S + 1 < NST)
-        fft_static_from<T, E, L2, INV, TWS, HIN, HOUT, Src, Dst, After0, S + 1>(buf, tw, lt, src, dst, after0);
+        fft_static_from<T, E, ED, INV, TWS, HIN, HOUT, Src, Dst, After0, S + 1>(buf, tw, lt, src, dst, after0);
 }
 
-// Whole transform of length 2^L2; same contract as fft_fused.
-template <typename T, int E, int L2, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst, class After0>
+// Whole transform of compile-time length ED; same contract as fft_fused.
+template <typename T, int E, int ED, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst, class After0>
 __device__ __forceinline__ void fft_static(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw, int lt,
                                            const Src &src, const Dst &dst, const After0 &after0)
 {
-    fft_static_from<T, E, L2, INV, TWS, HIN, HOUT, Src, Dst, After0, 0>(buf, tw, lt, src, dst, after0);
+    fft_static_from<T, E, ED, INV, TWS, HIN, HOUT, Src, Dst, After0, 0>(buf, tw, lt, src, dst, after0);
 }
 
-// The pass kernels' transform: ED >= 1000 selects the static path for length 2^(ED - 1000)
-// (which the host picks only for n = L/2, so HIN and HOUT hold there: zero-extended inputs,
-// cropped outputs); otherwise the runtime-descriptor path of fft_fused with edge radices ED,
-// which reads and writes every element.
+// The pass kernels' transform: ED >= 1000 selects the static path for length 2^(ED - 1000) or
+// 3 2^(ED - 2000) (which the host picks only for n = L/2 or n = L/3 respectively, so HIN and HOUT
+// hold there: zero-extended inputs, cropped outputs); otherwise the runtime-descriptor path of
+// fft_fused with edge radices ED, which reads and writes every element.
 template <typename T, int E, int ED, bool INV, bool TWS, bool HIN = false, bool HOUT = false, class Src, class Dst,
           class After0 = NoHook>
 __device__ __forceinline__ void fft_any(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
                                         const typename cvec<T>::t *__restrict__ tw, int lt, int tpt, const Src &src,
                                         const Dst &dst, const After0 &after0 = After0{})
 {
-    if constexpr (ED >= 1000) fft_static<T, E, ED - 1000, INV, TWS, HIN, HOUT>(buf, tw, lt, src, dst, after0);
+    if constexpr (ED >= 1000) fft_static<T, E, ED, INV, TWS, HIN, HOUT>(buf, tw, lt, src, dst, after0);
     else fft_fused<T, E, ED, INV, TWS>(buf, P, tw, lt, tpt, src, dst, after0);
 }
 
 // Transform length of the compile-time path (0 for the runtime path).
-template <int ED> __host__ __device__ constexpr int static_len() { return ED >= 1000 ? 1 << (ED >= 1000 ? ED - 1000 : 0) : 0; }
+template <int ED> __host__ __device__ constexpr int static_len() { return ED >= 2000 ? 3 << (ED - 2000) : (ED >= 1000 ? 1 << (ED - 1000) : 0); }
 
 }  // namespace wsc

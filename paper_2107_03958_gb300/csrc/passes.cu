@@ -228,6 +228,30 @@ static int generic_tpt(const FFTDesc &P)
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1013; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 1013; constexpr bool W_ = false; CALL; } \
         } \
+        else if ((prec) == CONV_P_FP32 && (E) == 24 && (ED) == 2007) { \
+            if (tws) { typedef float T_; constexpr int E_ = 24, ED_ = 2007; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 24, ED_ = 2007; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 24 && (ED) == 2008) { \
+            if (tws) { typedef float T_; constexpr int E_ = 24, ED_ = 2008; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 24, ED_ = 2008; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 24 && (ED) == 2009) { \
+            if (tws) { typedef float T_; constexpr int E_ = 24, ED_ = 2009; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 24, ED_ = 2009; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 24 && (ED) == 2010) { \
+            if (tws) { typedef float T_; constexpr int E_ = 24, ED_ = 2010; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 24, ED_ = 2010; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 24 && (ED) == 2011) { \
+            if (tws) { typedef float T_; constexpr int E_ = 24, ED_ = 2011; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 24, ED_ = 2011; constexpr bool W_ = false; CALL; } \
+        } \
+        else if ((prec) == CONV_P_FP32 && (E) == 24 && (ED) == 2012) { \
+            if (tws) { typedef float T_; constexpr int E_ = 24, ED_ = 2012; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 24, ED_ = 2012; constexpr bool W_ = false; CALL; } \
+        } \
         else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 132) { \
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 132; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 132; constexpr bool W_ = false; CALL; } \
@@ -265,6 +289,12 @@ static const int kFusedSets[][3] = {
     {1, 16, 1011},
     {1, 16, 1012},
     {1, 16, 1013},
+    {1, 24, 2007},  // FP32 compile-time lengths 3 2^7 ... 3 2^12 (the period-3 grid, n = 128 ... 4096)
+    {1, 24, 2008},
+    {1, 24, 2009},
+    {1, 24, 2010},
+    {1, 24, 2011},
+    {1, 24, 2012},
     {1, 24, 131},
     {1, 16, 136},
     {1, 16, 130},
@@ -277,18 +307,29 @@ static const int kFusedSets[][3] = {
 };
 
 // Fused passes exist for these (precision, E, ED): ED = 16 first radix + last radix with the
-// stage structure read from the runtime descriptor, or ED = 1000 + log2 L with the whole stage
-// structure fixed at compile time (fft_static.cuh); everything else runs the plain passes.
-// static_pref = 0 skips the compile-time lengths.
-static int fused_edges(conv_precision prec, int E, const FFTDesc &d, int static_pref = 1)
+// stage structure read from the runtime descriptor, or the whole stage structure fixed at compile
+// time (fft_static.cuh): ED = 1000 + log2 L for L = 2^l, chosen only when n = L/2, or
+// ED = 2000 + log2(L/3) for L = 3 2^l, chosen only when n = L/3 (their transforms prune the zero
+// extension and the crop).  Everything else runs the plain passes.  static_n = 0 skips the
+// compile-time lengths.
+static int fused_edges(conv_precision prec, int E, const FFTDesc &d, int static_n = 0)
 {
     if (d.nst < 2) return 0;
-    // a power-of-two length with a compile-time instantiation: 1000 + log2 L
-    if (static_pref && (d.L & (d.L - 1)) == 0) {
-        int l2 = 0;
-        while ((1 << l2) < d.L) ++l2;
+    auto have = [&](int ed) {
         for (const auto &f : kFusedSets)
-            if ((f[0] == 1) == (prec == CONV_P_FP32) && f[1] == E && f[2] == 1000 + l2) return 1000 + l2;
+            if ((f[0] == 1) == (prec == CONV_P_FP32) && f[1] == E && f[2] == ed) return true;
+        return false;
+    };
+    auto log2_of = [](int x) {  // log2 x for a power of two, else -1
+        if (x <= 0 || (x & (x - 1))) return -1;
+        int l = 0;
+        while ((1 << l) < x) ++l;
+        return l;
+    };
+    if (static_n > 0) {
+        const int l2 = log2_of(d.L), l3 = d.L % 3 == 0 ? log2_of(d.L / 3) : -1;
+        if (l2 >= 0 && 2 * static_n == d.L && have(1000 + l2)) return 1000 + l2;
+        if (l3 >= 0 && 3 * static_n == d.L && have(2000 + l3)) return 2000 + l3;
     }
     const int ed = 16 * d.R[0] + d.R[d.nst - 1];
     for (const auto &f : kFusedSets)
@@ -378,13 +419,15 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         tpt = generic_tpt(d);
     }
     if (tpt > maxT) return false;
-    // compile-time lengths only for n = L/2 (their transforms prune the zero half and the crop)
-    const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d, fused_pref == 1 && 2 * n == M) : 0;
+    // compile-time lengths only for n = L/2 or n = L/3 (their transforms prune the zero
+    // extension and the crop)
+    const int ed = fused_pref != 0 ? fused_edges(p->prec, E, d, fused_pref == 1 ? n : 0) : 0;
     const bool fused = ed != 0;
     if (p->prec == CONV_P_FP64 && E == 16 && ed < 1000) return false;  // no runtime FP64 E = 16 kernels
     if (ed >= 1000) {
-        // the compile-time-length kernels: radix-16 stages, their launch bound
-        if (!factorize(M, E, d, true, p->prec == CONV_P_FP64)) return false;
+        // the compile-time-length kernels: radix-16 stages (L = 2^l; radix 8 and 3 for L = 3 2^l,
+        // as factorize gives already), their launch bound
+        if (ed < 2000 && !factorize(M, E, d, true, p->prec == CONV_P_FP64)) return false;
         maxT = std::min(maxT, WSC_STATIC_MAXT);
         if (tpt > maxT) return false;
     }

@@ -17,9 +17,10 @@ namespace wsc {
 
 #define WSC_LBF(T, E, ED) __launch_bounds__(maxt_fused<T, E, ED>::v, 1)
 
-// The compile-time-length kernels run only for n = L/2 (the host selects them so): their forward
-// transforms see zero-extended halves and their inverse transforms' outputs are cropped to a half.
-template <int ED> __device__ constexpr bool halved() { return ED >= 1000; }
+// The compile-time-length kernels run only for n = L/2 (ED = 1000 + log2 L) or n = L/3
+// (ED = 2000 + log2(L/3)), as the host selects them: their forward transforms see the zero
+// extension beyond n and their inverse transforms' outputs are cropped to the first n.
+template <int ED> __device__ constexpr bool pruned() { return ED >= 1000; }
 
 // ---------------------------------------------------------------------------- prefetch
 // With a.pf set, each thread group fetches the input of its next work item (unit + stride) into
@@ -151,7 +152,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const __grid_constant__ PassAr
             }
             return cmk<V>(x, y);
         };
-        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
         if (a.tma) {
             // the previous item's stores have to have read the pairs before they are rewritten
             if (lt == 0) bulk_wait_read();
@@ -224,14 +225,14 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const __grid_constant__ PassArgs<T
             return a.pf ? stg[i] : col[i];
         };
         auto mul = smem_hook([&](int o, V &x) {
-            const int Lm = halved<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
+            const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             x = cscale(x, __ldg(&gc[k1]));
         });
-        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -325,7 +326,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const __grid_constant__ PassAr
             oa[o] = ra;
             if (has2) oa[n + o] = rb;
         };
-        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -382,13 +383,13 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T
         };
         const V *gc = cg + (size_t)k2 * h;
         auto mul = smem_hook([&](int o, V &x) {
-            const int Lm = halved<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
+            const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             const V gk = __ldg(&gc[k1]);
             bim[pidx<T>(o)] = cscale(x, gk.y);
             x = cscale(x, gk.x);
         });
-        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(bre, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
-        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(bre, a.P, twp, lt, a.tpt, FromSmem{}, ToSmem{});
+        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(bre, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bre, a.P, twp, lt, a.tpt, FromSmem{}, ToSmem{});
         V *cout = reinterpret_cast<V *>(a.out) + 2 * co;
         auto dst = [&](int o, V xi) {
             if (!valid || o >= n) return;
@@ -402,7 +403,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T
             cout[2 * o] = xr;
             cout[2 * o + 1] = xi;
         };
-        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(bim, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bim, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -482,7 +483,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_rows_inv(const __grid_constant__ PassAr
             if (a.beta != (T)0) z.x += a.beta * ua[o];
             o_[o] = z;
         };
-        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -533,7 +534,7 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_rows_fwd(const __grid_constant__ PassAr
         auto dst = [&](int o, V z) {
             if (valid) Wb[(size_t)o * n + j1] = z;
         };
-        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
         __syncthreads();
     }
 }
@@ -575,15 +576,15 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_cols(const __grid_constant__ PassArgs<T
             return a.pf ? stg[i] : col[i];
         };
         auto mul = smem_hook([&](int o, V &x) {
-            const int Lm = halved<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
+            const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             if (CG) x = cmul(x, __ldg(reinterpret_cast<const V *>(a.ghat) + (size_t)k2q * h + k1));
             else x = cscale(x, __ldg(reinterpret_cast<const T *>(a.ghat) + (size_t)k2q * h + k1));
         });
-        fft_any<T, E, ED, false, TWS, halved<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -635,7 +636,7 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_rows_inv(const __grid_constant__ PassAr
             }
             o_[o] = z;
         };
-        fft_any<T, E, ED, true, TWS, false, halved<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();

@@ -405,7 +405,8 @@ conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
     info->elems = p->elems;
     info->smem_twiddles = p->tws ? 1 : 0;
     info->fused = p->fused ? 1 : 0;
-    info->static_log2 = p->fused && p->ed >= 1000 ? p->ed - 1000 : 0;
+    info->static_log2 = p->fused && p->ed >= 1000 && p->ed < 2000 ? p->ed - 1000 : 0;
+    info->static_len = !p->fused ? 0 : (p->ed >= 2000 ? 3 << (p->ed - 2000) : (p->ed >= 1000 ? 1 << (p->ed - 1000) : 0));
     info->r2c_split = p->r2c_split ? 1 : 0;
     info->period_num = p->pnum;
     info->period_den = p->pden;

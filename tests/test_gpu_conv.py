@@ -275,6 +275,7 @@ def test_compile_time_lengths_match_oracle_and_runtime_stages(n, prec, io, monke
         plan = ConvPlan(n=n, period=3, precision=prec, io=io, batch_max=B, compact=True, **kw)
         info = plan.info
         assert info.fused == 1 and info.static_log2 == (int(np.log2(2 * n)) if fused == "1" else 0)
+        assert info.static_len == (2 * n if fused == "1" else 0)
         outs.append(plan.apply(torch.tensor(u, dtype=plan.in_dtype(), device="cuda")).cpu().numpy())
         plan.device_status()
     ref = _oracle_conv(u, plan, kw)
@@ -283,6 +284,34 @@ def test_compile_time_lengths_match_oracle_and_runtime_stages(n, prec, io, monke
     for i in range(B):
         assert _relerr(ref[i], outs[0][i]) <= TOL[prec]
         assert _relerr(outs[1][i], outs[0][i]) <= (1e-6 if prec == "fp32" else 1e-13)
+
+
+@pytest.mark.parametrize("io", ["r2r", "r2c", "c2c"])
+@pytest.mark.parametrize("n", [128, 1024, 2048])
+def test_compile_time_period_3_lengths_match_oracle_and_runtime_stages(n, io, monkeypatch):
+    """The paper's period-3 grid, L = 3n = 3 2^l: FP32 transforms whose radix-8/radix-3 stage
+    structure is fixed at compile time (inputs beyond n pruned in the first stage, outputs beyond
+    n in the last) match the oracle and the runtime-descriptor transforms of the same plan."""
+    kw = KERNELS["helm20" if io != "r2r" else "log"]
+    B = 2
+    rng = np.random.default_rng(3 * n + len(io))
+    u = inputs.bump_sums(n, B, seed=n + 5)
+    if io == "c2c":
+        u = u + 1j * rng.standard_normal((B, n, n)) * 0.1
+    outs = []
+    for fused in ("1", "2"):
+        monkeypatch.setenv("WSCONV_FUSED", fused)
+        plan = ConvPlan(n=n, period=3, precision="fp32", io=io, batch_max=B, **kw)
+        info = plan.info
+        assert info.fused == 1 and info.static_len == (3 * n if fused == "1" else 0)
+        outs.append(plan.apply(torch.tensor(u, dtype=plan.in_dtype(), device="cuda")).cpu().numpy())
+        plan.device_status()
+    ref = _oracle_conv(u, plan, kw)
+    if io == "r2r":
+        ref = ref.real
+    for i in range(B):
+        assert _relerr(ref[i], outs[0][i]) <= TOL["fp32"]
+        assert _relerr(outs[1][i], outs[0][i]) <= 1e-6
 
 
 @pytest.mark.parametrize("io", ["r2r", "r2c"])
