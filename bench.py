@@ -301,43 +301,36 @@ def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, compact=
 
 
 def e2e_leg(n, batch, steps, warmup, compact=True):
-    """End to end through conv_apply_host (the call that takes HOST buffers): every step uploads
-    the batch of densities from pinned host memory for each of the five plans, runs the passes and
-    downloads every result into pinned host memory.  Each plan runs on its own stream, so one
-    plan's copies overlap another's passes; inside a plan the chunks overlap too.  Timed with CUDA
-    events from before the first upload to after the last download."""
+    """End to end through conv_apply_host_multi (the call that takes HOST buffers): every step
+    uploads the batch of densities from pinned host memory once, runs the five plans' passes on
+    each chunk and downloads every result into pinned host memory, each plan's result chunk
+    behind the next plan's passes.  Timed with CUDA events from before the first upload to after
+    the last download."""
     import torch
     from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import apply_host_multi
     plans = make_plans(n, batch, "fp32", compact)
     u_host = torch.from_numpy(inputs.bump_sums(n, batch)).to(torch.float32).pin_memory()
     outs = [torch.empty((batch, n, n), dtype=p.out_dtype()).pin_memory() for p in plans]
-    streams = [torch.cuda.Stream() for _ in plans]
     main = torch.cuda.current_stream()
 
     def step():
-        for p, o, s in zip(plans, outs, streams):
-            p.apply_host(u_host, out=o, stream=s)
+        apply_host_multi(plans, u_host, outs=outs, stream=main)
 
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(main)
-    for s in streams:
-        s.wait_event(e0)
     for _ in range(steps):
         step()
-    for s in streams:
-        ev = torch.cuda.Event()
-        ev.record(s)
-        main.wait_event(ev)
     e1.record(main)
     torch.cuda.synchronize()
     for p in plans:
         p.device_status()
     chunk = max(1, (batch + 3) // 4)
     return {"ms": e0.elapsed_time(e1), "launches": 3 * len(plans) * ((batch + chunk - 1) // chunk) * steps,
-            "h2d": len(plans) * u_host.numel() * u_host.element_size(),
+            "h2d": u_host.numel() * u_host.element_size(),
             "d2h": sum(o.numel() * o.element_size() for o in outs)}
 
 
@@ -622,7 +615,7 @@ def main():
     e2e_ms = max_over_ranks(ws, e2e_run["ms"])
     e2e = {"value": ws * 5 * args.batch * e2e_steps / (e2e_ms * 1e-3), "unit": "conv/s",
            "h2d_bytes_per_step": e2e_run["h2d"], "d2h_bytes_per_step": e2e_run["d2h"],
-           "api": "conv_apply_host (pinned host buffers; each plan on its own stream)"}
+           "api": "conv_apply_host_multi (pinned host buffers; one upload per chunk for the five plans)"}
 
     extras = {}
     if not args.no_extras:

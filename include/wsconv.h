@@ -131,6 +131,24 @@ conv_status conv_apply(conv_plan_t plan, const void *u, const void *mask, void *
 conv_status conv_apply_host(conv_plan_t plan, const void *u_host, const void *mask, void *out_host, int batch,
                             void *stream);
 
+/* conv_apply_host for several plans on ONE batch of host densities (no counterpart in the paper;
+ * e.g. the same densities convolved with several kernels of Sec. 2.2).  Each chunk of densities
+ * (ceil(min batch_max / 4)) is uploaded once; the plans' passes run on it in list order, each
+ * with its own workspace, and plan k's result chunk downloads while plan k+1's passes run.
+ *   plans:    `count` distinct plans with the same n, precision, device and input type (R2R and
+ *             R2C take real densities, C2C complex ones); per-pass timing off.
+ *   u_host:   batch x n x n densities, host memory, as conv_apply's u.
+ *   mask:     NULL or a DEVICE n x n array (plan precision) shared by every plan.
+ *   out_host: `count` host arrays, out_host[k] batch x n x n in plans[k]'s output layout.
+ * Host buffers should be page-locked.  Ordered on `stream` like conv_apply_host; returns without
+ * waiting.  The device slots (four chunks of densities, four of each plan's results) and three
+ * streams are created at the first call and kept on plans[0] until conv_destroy, or rebuilt when
+ * a later call's chunk or result sizes differ.  Calls on any of these plans must not overlap.
+ * Returns CONV_EINVAL for bad or mismatched arguments, CONV_ENOMEM when the slots cannot be
+ * allocated. */
+conv_status conv_apply_host_multi(int count, const conv_plan_t *plans, const void *u_host, const void *mask,
+                                  void *const *out_host, int batch, void *stream);
+
 /* conv_apply without any allocation (the paper has no counterpart; this is a deployment aid).
  * For callers that cannot call cudaMalloc when they run the convolution: code under a device
  * memory budget that forbids new allocations, real-time loops where an allocation may block, or

@@ -102,6 +102,9 @@ PROTOTYPES = {
                                 ctypes.POINTER(SrvResult)]),
     "srv_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SrvStats)]),
     "srv_destroy": (None, [ctypes.c_void_p]),
+    "conv_apply_host_multi": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                             ctypes.c_void_p]),
     "conv_group_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),

@@ -176,6 +176,36 @@ class ConvPlan:
         return buf
 
 
+def apply_host_multi(plans, u, outs=None, mask=None, stream=None):
+    """A_n(u * mask) with every plan in `plans` for one batch of host densities `u` (a CPU tensor;
+    pinned for overlap): each chunk is uploaded once and the plans run on it in turn.  The plans
+    share n, precision and input type.  Returns the list of host results (pinned CPU tensors
+    unless `outs` is given), ordered on `stream`; synchronise it before reading them."""
+    plans = list(plans)
+    if not plans:
+        raise ValueError("at least one plan")
+    p0 = plans[0]
+    if u.device.type != "cpu" or u.dtype != p0.in_dtype() or tuple(u.shape[-2:]) != (p0.n, p0.n) or not u.is_contiguous():
+        raise ValueError("u must be a contiguous (..., n, n) %s host tensor" % p0.in_dtype())
+    batch = 1 if u.dim() == 2 else int(np.prod(u.shape[:-2]))
+    if outs is None:
+        outs = [torch.empty(u.shape, dtype=p.out_dtype()).pin_memory() for p in plans]
+    if len(outs) != len(plans):
+        raise ValueError("one output per plan")
+    for p, o in zip(plans, outs):
+        if o.device.type != "cpu" or o.dtype != p.out_dtype() or o.shape != u.shape or not o.is_contiguous():
+            raise ValueError("each output must be a contiguous host tensor of u's shape and its plan's dtype")
+    if mask is not None:
+        p0._check_grid(mask, p0.real_dtype, "mask")
+    k = len(plans)
+    arr = ctypes.c_void_p * k
+    N.check(p0._lib.conv_apply_host_multi(
+        k, arr(*[p.handle.value for p in plans]), ctypes.c_void_p(u.data_ptr()),
+        ctypes.c_void_p(mask.data_ptr()) if mask is not None else None,
+        arr(*[o.data_ptr() for o in outs]), batch, _stream_ptr(stream)))
+    return outs
+
+
 class ConvGroup:
     """Several applies, on plans that may differ in n, kernel, precision and io, run as one CUDA
     graph launch (items on different plans run concurrently; items on one plan in order).

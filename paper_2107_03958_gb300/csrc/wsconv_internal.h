@@ -119,6 +119,7 @@ struct conv_plan_s {
     std::vector<std::array<cudaEvent_t, 4>> tev_used, tev_free;
     // host-buffer pipeline (host_io.cu), created by the first conv_apply_host
     struct HostPipe *hostpipe = nullptr;
+    struct HostMulti *hostmulti = nullptr;  // conv_apply_host_multi's slots (on its first plan)
     // Krylov workspace of ls_solve (ls.cu), created by the first solve
     wsc::LsCache *ls_cache = nullptr;
 };
@@ -137,6 +138,6 @@ conv_status select_transform(conv_plan_s *p);
 // ghat.cu
 conv_status build_ghat(conv_plan_s *p);
 size_t spectrum_elems(const conv_plan_s *p);  // complex elements of the workspace per density
-void destroy_hostpipe(conv_plan_s *p);          // host_io.cu
+void destroy_hostpipe(conv_plan_s *p);          // host_io.cu (both host pipelines)
 void destroy_ls_cache(conv_plan_s *p);          // ls.cu
 }  // namespace wsc

@@ -240,6 +240,35 @@ def test_host_buffer_apply_equals_device_apply(name, io, prec):
     plan.device_status()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_multi_plan_host_apply_equals_device_apply(prec):
+    """conv_apply_host_multi (one upload per chunk, the plans' passes in turn, each result chunk
+    downloaded behind the next plan): every plan's result is bitwise its device-buffer apply, for
+    the kernel sweep's mix of R2R and R2C plans, a ragged last chunk and a mask."""
+    from paper_2107_03958_gb300.api import apply_host_multi
+    n, B = 128, 7
+    plans = [ConvPlan(n=n, period=3, precision=prec, io="r2c" if k == "helm20" else "r2r",
+                      batch_max=5 + i, compact=i % 2 == 0, **KERNELS[k]) for i, k in enumerate(KERNELS)]
+    u = inputs.bump_sums(n, B, seed=21)
+    u_host = torch.tensor(u, dtype=plans[0].real_dtype).pin_memory()
+    mask = torch.tensor(np.random.default_rng(3).uniform(0, 1, (n, n)), dtype=plans[0].real_dtype, device="cuda")
+    ud = u_host.cuda()
+    refs = []
+    for p in plans:
+        ws = torch.empty(p.workspace_bytes(B), dtype=torch.uint8, device="cuda")
+        refs.append(p.apply(ud, mask=mask, workspace=ws).cpu())
+    s = torch.cuda.Stream()
+    for _ in range(2):  # the second call reuses the slots kept on the first plan
+        outs = apply_host_multi(plans, u_host, mask=mask, stream=s)
+        s.synchronize()
+        for o, r in zip(outs, refs):
+            assert torch.equal(o, r)
+    for p in plans:
+        p.device_status()
+    with pytest.raises(Exception):
+        apply_host_multi([plans[0], plans[0]], u_host)
+
+
 @pytest.mark.parametrize("name,io", [("log", "r2r"), ("helm20", "r2c")])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_autotuned_plan_matches_oracle(name, io, prec):
