@@ -244,9 +244,10 @@ def test_host_buffer_apply_equals_device_apply(name, io, prec):
 def test_multi_plan_host_apply_equals_device_apply(prec):
     """conv_apply_host_multi (one upload per chunk, the plans' passes in turn, each result chunk
     downloaded behind the next plan): every plan's result is bitwise its device-buffer apply, for
-    the kernel sweep's mix of R2R and R2C plans, a ragged last chunk and a mask."""
+    the kernel sweep's mix of R2R and R2C plans, more chunks than device slots, a ragged last
+    chunk and a mask."""
     from paper_2107_03958_gb300.api import apply_host_multi
-    n, B = 128, 7
+    n, B = 128, 11
     plans = [ConvPlan(n=n, period=3, precision=prec, io="r2c" if k == "helm20" else "r2r",
                       batch_max=5 + i, compact=i % 2 == 0, **KERNELS[k]) for i, k in enumerate(KERNELS)]
     u = inputs.bump_sums(n, B, seed=21)
