@@ -20,6 +20,7 @@
 
 #include <array>
 #include <cstdlib>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -519,11 +520,16 @@ static conv_status device_limits(conv_plan_s *p, int &smem_optin, int &sms)
     const int dev = p->device;
     WSC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     WSC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // once per device; plans may be created from several threads (the serving runtime's)
+    static std::mutex mu;
     static bool attrs_set[64] = {false};
-    if (dev >= 0 && dev < 64 && !attrs_set[dev]) {
-        conv_status rc = set_all_attrs(smem_optin);
-        if (rc != CONV_OK) return rc;
-        attrs_set[dev] = true;
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attrs_set[dev]) {
+            conv_status rc = set_all_attrs(smem_optin);
+            if (rc != CONV_OK) return rc;
+            attrs_set[dev] = true;
+        }
     }
     const int M = p->M;
     const size_t esz = p->prec == CONV_P_FP64 ? 16 : 8;
