@@ -22,38 +22,77 @@ namespace wsc {
 #define LS_RED_BLOCKS 296  // 2 x 148..152 SMs: fixed partition for deterministic reductions
 #define LS_RED_THREADS 256
 
-// partial[i * nb + blk] = sum_{t in blk's slice} conj(V_i[t]) w[t], i < cnt
+// Dot products of NV basis vectors V_i0 ... V_i0+NV-1 with w over this block's slice [lo, hi):
+// one sweep that reads w once for the NV of them.  Each thread issues the loads of four elements
+// (and of every vector) before it uses them, so enough reads are in flight to keep HBM busy;
+// the sums still run over t in the order of a plain loop, so the result is the same bit for bit.
+template <int NV>
+__device__ __forceinline__ void dots_sweep(const double2 *__restrict__ V, size_t ldv, int i0,
+                                           const double2 *__restrict__ w, long long lo, long long hi,
+                                           double2 (*red)[LS_RED_THREADS / 32], double2 *__restrict__ partial)
+{
+    const long long S = blockDim.x;
+    double sr[NV], si[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sr[k] = si[k] = 0.0;
+    long long t = lo + threadIdx.x;
+    for (; t + 3 * S < hi; t += 4 * S) {
+        double2 b[4], a[NV][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = w[t + u * S];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[k][u] = V[(size_t)(i0 + k) * ldv + t + u * S];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                sr[k] += a[k][u].x * b[u].x + a[k][u].y * b[u].y;
+                si[k] += a[k][u].x * b[u].y - a[k][u].y * b[u].x;
+            }
+    }
+    for (; t < hi; t += S) {
+        const double2 b = w[t];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double2 a = V[(size_t)(i0 + k) * ldv + t];
+            sr[k] += a.x * b.x + a.y * b.y;
+            si[k] += a.x * b.y - a.y * b.x;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            sr[k] += __shfl_down_sync(0xffffffffu, sr[k], o);
+            si[k] += __shfl_down_sync(0xffffffffu, si[k], o);
+        }
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = make_double2(sr[k], si[k]);
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int k = threadIdx.x;
+        double ar = 0, ai = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            ar += red[k][q].x;
+            ai += red[k][q].y;
+        }
+        partial[(size_t)(i0 + k) * gridDim.x + blockIdx.x] = make_double2(ar, ai);
+    }
+    __syncthreads();
+}
+
+// partial[i * nb + blk] = sum_{t in blk's slice} conj(V_i[t]) w[t], i < cnt; two vectors per sweep
 __global__ void __launch_bounds__(LS_RED_THREADS) k_multidot(const double2 *__restrict__ V, size_t ldv, int cnt,
                                                              const double2 *__restrict__ w, long long N,
                                                              double2 *__restrict__ partial)
 {
-    __shared__ double2 red[LS_RED_THREADS / 32];
+    __shared__ double2 red[2][LS_RED_THREADS / 32];
     const long long chunk = (N + gridDim.x - 1) / gridDim.x;
     const long long lo = blockIdx.x * chunk, hi = min(N, lo + chunk);
-    for (int i = 0; i < cnt; ++i) {
-        const double2 *vi = V + (size_t)i * ldv;
-        double sr = 0.0, si = 0.0;
-        for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-            double2 a = vi[t], b = w[t];
-            sr += a.x * b.x + a.y * b.y;
-            si += a.x * b.y - a.y * b.x;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_down_sync(0xffffffffu, sr, o);
-            si += __shfl_down_sync(0xffffffffu, si, o);
-        }
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(sr, si);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double ar = 0, ai = 0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-                ar += red[q].x;
-                ai += red[q].y;
-            }
-            partial[(size_t)i * gridDim.x + blockIdx.x] = make_double2(ar, ai);
-        }
-        __syncthreads();
-    }
+    int i = 0;
+    for (; i + 2 <= cnt; i += 2) dots_sweep<2>(V, ldv, i, w, lo, hi, red, partial);
+    if (i < cnt) dots_sweep<1>(V, ldv, i, w, lo, hi, red, partial);
 }
 
 // out[i] = sum_blk partial[i * nb + blk] (+= if accumulate); one warp per i, fixed order.
@@ -88,7 +127,20 @@ __global__ void k_sub_combination(const double2 *__restrict__ V, size_t ldv, int
     __syncthreads();
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
         double2 acc = w[t];
-        for (int i = 0; i < cnt; ++i) {
+        int i = 0;
+        // four vectors' loads issued before their uses (same subtraction order as one at a time)
+        for (; i + 4 <= cnt; i += 4) {
+            double2 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = V[(size_t)(i + k) * ldv + t];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double2 c = hs[i + k];
+                acc.x -= v[k].x * c.x - v[k].y * c.y;
+                acc.y -= v[k].x * c.y + v[k].y * c.x;
+            }
+        }
+        for (; i < cnt; ++i) {
             double2 v = V[(size_t)i * ldv + t], c = hs[i];
             acc.x -= v.x * c.x - v.y * c.y;
             acc.y -= v.x * c.y + v.y * c.x;
@@ -106,7 +158,19 @@ __global__ void k_add_combination(const double2 *__restrict__ V, size_t ldv, int
     __syncthreads();
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
         double2 acc = x[t];
-        for (int i = 0; i < cnt; ++i) {
+        int i = 0;
+        for (; i + 4 <= cnt; i += 4) {
+            double2 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = V[(size_t)(i + k) * ldv + t];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double2 c = ys[i + k];
+                acc.x += v[k].x * c.x - v[k].y * c.y;
+                acc.y += v[k].x * c.y + v[k].y * c.x;
+            }
+        }
+        for (; i < cnt; ++i) {
             double2 v = V[(size_t)i * ldv + t], c = ys[i];
             acc.x += v.x * c.x - v.y * c.y;
             acc.y += v.x * c.y + v.y * c.x;
