@@ -415,6 +415,46 @@ def group_leg(reps, stream):
             "speedup": out["sequential"]["ms_per_step"] / out["group"]["ms_per_step"]}
 
 
+def ls_multi_leg(n, kappa, K, repeats, stream):
+    """K incident directions (angles 2 pi s / K) on the bump scatterer: one stacked solve
+    (ls_solve_multi, batched matvecs) against K single solves, both to 1e-10 per system."""
+    import numpy as np
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import ConvPlan, ls_solve, ls_solve_multi
+    m = torch.tensor(inputs.lippmann_contrast(n, "bump"), device="cuda")
+    F = torch.tensor(np.stack([inputs.plane_wave(n, kappa, 2 * math.pi * s / K) for s in range(K)]), device="cuda")
+    out = {"n": n, "kappa": kappa, "rhs": K, "tol": 1e-10, "repeats": repeats}
+    for mode in ("mixed", "fp64"):
+        plan = ConvPlan("helmholtz", n=n, period=3, precision="fp64" if mode == "fp64" else "fp32",
+                        io="c2c", kappa=kappa, compact=True)
+        refine = mode == "mixed"
+
+        def single():
+            return [ls_solve(plan, m, F[s], refine=refine, stream=stream)[1] for s in range(K)]
+
+        def multi():
+            return ls_solve_multi(plan, m, F, refine=refine, stream=stream)[1]
+
+        res = {}
+        for name, fn in (("single", single), ("stacked", multi)):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(repeats):
+                infos = fn()
+            torch.cuda.synchronize()
+            wall = (time.perf_counter() - t0) / repeats
+            res[name] = {"solves_per_s": K / wall, "ms_per_batch": 1e3 * wall,
+                         "iters": [i["iters"] for i in infos][:1] if name == "stacked" else [i["iters"] for i in infos],
+                         "max_rel_residual": max(i["rel_residual"] for i in infos)}
+        res["speedup"] = res["single"]["ms_per_batch"] / res["stacked"]["ms_per_batch"]
+        out[mode] = res
+        del plan
+        torch.cuda.empty_cache()
+    return out
+
+
 def profile_case(args):
     """Small fixed case for ncu captures: one plan, warmup + steps applies, nothing else."""
     import torch
@@ -653,6 +693,7 @@ def main():
                                    "unit": "conv/s", "ms_per_step": l2_ms / args.steps}
         extras["ls"] = ls_leg(512, 40.0, 5, stream)
         extras["ls_larger"] = [ls_leg(1024, 40.0, 3, stream), ls_leg(2048, 40.0, 3, stream)]
+        extras["ls_multi_rhs"] = ls_multi_leg(512, 40.0, 8, 3, stream)
         extras["mixed_group"] = group_leg(50, stream)
         extras["serving"] = serving_leg(80)
         extras["served_ls_burst"] = served_ls_burst(80)

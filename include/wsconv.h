@@ -273,6 +273,20 @@ typedef struct {
 conv_status ls_solve(conv_plan_t plan, const double *m, const void *f, void *x, const ls_opts *opts,
                      ls_info *info, void *stream);
 
+/* ls_solve for `count` right-hand sides with one operator (the same plan, contrast m and kappa;
+ * e.g. several incident plane waves on one scatterer, Sec. 3.3).
+ *   f, x: count x n x n complex128, contiguous (x: initial guesses unless opts->zero_guess; on
+ *         return the solutions).  info: NULL or `count` entries.
+ * GMRES runs on the stacked block-diagonal system with each f_s scaled to unit norm, so every
+ * matvec is one batched apply of `count` densities.  The stacked target tol / sqrt(count) bounds
+ * each system's relative residual by tol; info[s].rel_residual is system s's own, from the FP64
+ * operator, and iters / restarts / refinements are the shared iteration's.
+ * Workspace: the Krylov basis grows with count ((restart + 1) x count x n^2 complex128), kept with
+ * the plan like ls_solve's; matvec workspaces for count beyond the plans' batch_max are allocated
+ * with it.  Returns as ls_solve, CONV_EINVAL also for count < 1 or > 65535. */
+conv_status ls_solve_multi(conv_plan_t plan, int count, const double *m, const void *f, void *x,
+                           const ls_opts *opts, ls_info *info, void *stream);
+
 /* Fourier-smoothed indicator mask for discontinuous densities (Sec. 2.4, eq. (tfs)):
  *     mask_j = Re chi^n_Omega(x_j) * psi(x_j),  x_j = j/n,
  *     chi^n_Omega(x) = sum_{k in F_n} chihat_b(k) e^{2 pi i k.x/b},

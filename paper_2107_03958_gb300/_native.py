@@ -86,6 +86,9 @@ PROTOTYPES = {
     "conv_last_error": (ctypes.c_char_p, []),
     "ls_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.POINTER(LsOpts), ctypes.POINTER(LsInfo), ctypes.c_void_p]),
+    "ls_solve_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.POINTER(LsOpts), ctypes.POINTER(LsInfo),
+                                      ctypes.c_void_p]),
     "conv_fs_mask": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "conv_device_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),

@@ -280,6 +280,35 @@ def ls_solve(plan, m, f, x=None, restart=50, max_iters=2000, tol=1e-10, refine=F
     return x, info
 
 
+def ls_solve_multi(plan, m, F, X=None, restart=50, max_iters=2000, tol=1e-10, refine=False,
+                   inner_tol=1e-5, stream=None):
+    """Solve u_s + kappa^2 A_n(m u_s) = f_s for every right-hand side F[s] (one operator, one
+    contrast m) as one stacked GMRES whose matvecs are batched applies.
+    F: (K, n, n) complex128 CUDA tensor; returns (X, [info per system])."""
+    if plan.io != "c2c" or plan.kernel not in ("helmholtz", "helm"):
+        raise ValueError("ls_solve_multi needs a C2C Helmholtz plan")
+    plan._check_grid(m, torch.float64, "m")
+    plan._check_grid(F, torch.complex128, "F")
+    if F.dim() != 3:
+        raise ValueError("F must be (K, n, n)")
+    K = int(F.shape[0])
+    zero = X is None
+    if X is None:
+        X = torch.zeros_like(F)
+    plan._check_grid(X, torch.complex128, "X")
+    if X.shape != F.shape:
+        raise ValueError("X must have F's shape")
+    o = N.LsOpts(int(restart), int(max_iters), float(tol), int(bool(refine)), float(inner_tol), int(zero))
+    infs = (N.LsInfo * K)()
+    st = plan._lib.ls_solve_multi(plan.handle, K, ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(F.data_ptr()),
+                                  ctypes.c_void_p(X.data_ptr()), ctypes.byref(o), infs, _stream_ptr(stream))
+    status = N.STATUS.get(st, st)
+    if st not in (0, 6):
+        N.check(st)
+    return X, [{"iters": i.iters, "restarts": i.restarts, "refinements": i.refinements,
+                "rel_residual": i.rel_residual, "status": status} for i in infs]
+
+
 class Server:
     """Continuous-batching request loop (C++ runtime in the library; see srv_* in wsconv.h).
 

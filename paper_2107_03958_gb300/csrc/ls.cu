@@ -192,6 +192,15 @@ __global__ void k_scale_by_invnorm(const double2 *__restrict__ src, double2 *__r
 }
 
 // r = f - r (r holds L x on entry)
+// x *= a (a real)
+__global__ void k_scale_real(double2 *__restrict__ x, double a, long long N)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+        const double2 v = x[t];
+        x[t] = make_double2(v.x * a, v.y * a);
+    }
+}
+
 __global__ void k_rsub(const double2 *__restrict__ f, double2 *__restrict__ r, long long N)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
@@ -298,9 +307,16 @@ struct LsWork {
     double2 *partial = nullptr;
     GmresState *st = nullptr;
     double *host_res = nullptr;  // pinned
+    // several right-hand sides: their normalised copies, and the matvecs' spectrum workspaces
+    // when the batch exceeds the plans' own
+    double2 *fsc = nullptr;
+    void *cws = nullptr, *cws64 = nullptr;
 };
 
-static bool alloc_work(LsWork &W, long long N, int restart, bool mixed)
+// N: the (stacked) Krylov vector length, NN = n^2 (the contrast), batch: right-hand sides, with
+// cws/cws64 bytes of matvec workspace (0: the plans' own suffices).
+static bool alloc_work(LsWork &W, long long N, long long NN, int batch, size_t cws, size_t cws64, int restart,
+                       bool mixed)
 {
     bool ok = cudaMalloc(&W.V, (size_t)(restart + 1) * N * sizeof(double2)) == cudaSuccess &&
               cudaMalloc(&W.w, N * sizeof(double2)) == cudaSuccess &&
@@ -313,7 +329,10 @@ static bool alloc_work(LsWork &W, long long N, int restart, bool mixed)
         ok = cudaMalloc(&W.x64, N * sizeof(double2)) == cudaSuccess &&
              cudaMalloc(&W.v32, N * sizeof(float2)) == cudaSuccess &&
              cudaMalloc(&W.w32, N * sizeof(float2)) == cudaSuccess &&
-             cudaMalloc(&W.m32, N * sizeof(float)) == cudaSuccess;
+             cudaMalloc(&W.m32, NN * sizeof(float)) == cudaSuccess;
+    if (ok && batch > 1) ok = cudaMalloc(&W.fsc, N * sizeof(double2)) == cudaSuccess;
+    if (ok && cws) ok = cudaMalloc(&W.cws, cws) == cudaSuccess;
+    if (ok && cws64) ok = cudaMalloc(&W.cws64, cws64) == cudaSuccess;
     if (!ok) cudaGetLastError();
     return ok;
 }
@@ -328,6 +347,9 @@ static void free_work(LsWork &W)
     cudaFree(W.v32);
     cudaFree(W.w32);
     cudaFree(W.m32);
+    cudaFree(W.fsc);
+    cudaFree(W.cws);
+    cudaFree(W.cws64);
     cudaFree(W.partial);
     cudaFree(W.st);
     if (W.host_res) cudaFreeHost(W.host_res);
@@ -340,7 +362,8 @@ static void free_work(LsWork &W)
 struct LsCache {
     std::mutex mu;
     LsWork W;
-    long long N = 0;
+    long long N = 0;                       // Krylov vector length (batch n^2)
+    int batch = 0;
     int restart = 0;
     bool mixed = false;
     double *m64 = nullptr;                 // the solve's contrast, copied in (the graphs read it here)
@@ -373,7 +396,8 @@ struct Solver {
     conv_plan_s *p64;      // FP64 operator for true residuals
     const double *m64;
     double kappa2;
-    long long N;
+    long long N;           // Krylov vector length: batch x n^2
+    int batch;             // right-hand sides stacked in one vector (one batched matvec)
     int restart;
     LsWork W;
     cudaStream_t st;
@@ -385,9 +409,9 @@ struct Solver {
     conv_status matvec(const double2 *v, double2 *w)
     {
         if (p->prec == CONV_P_FP64)
-            return conv_apply_axpby(p, v, m64, w, 1, kappa2, 0.0, 1.0, nullptr, st);
+            return conv_apply_axpby(p, v, m64, w, batch, kappa2, 0.0, 1.0, W.cws, st);
         k_d2f<<<grid_elem, 256, 0, st>>>(reinterpret_cast<const double *>(v), reinterpret_cast<float *>(W.v32), 2 * N);
-        conv_status rc = conv_apply_axpby(p, W.v32, W.m32, W.w32, 1, kappa2, 0.0, 1.0, nullptr, st);
+        conv_status rc = conv_apply_axpby(p, W.v32, W.m32, W.w32, batch, kappa2, 0.0, 1.0, W.cws, st);
         if (rc != CONV_OK) return rc;
         k_f2d<<<grid_elem, 256, 0, st>>>(reinterpret_cast<const float *>(W.w32), reinterpret_cast<double *>(w), 2 * N);
         return CONV_OK;
@@ -395,17 +419,25 @@ struct Solver {
 
     conv_status true_residual(const double2 *f, const double2 *x, double2 *r)
     {
-        conv_status rc = conv_apply_axpby(p64, x, m64, r, 1, kappa2, 0.0, 1.0, nullptr, st);
+        conv_status rc = conv_apply_axpby(p64, x, m64, r, batch, kappa2, 0.0, 1.0, p64 == p ? W.cws : W.cws64, st);
         if (rc != CONV_OK) return rc;
         k_rsub<<<grid_elem, 256, 0, st>>>(f, r, N);
         return CONV_OK;
     }
 
-    // squared norm of v into st->nrm2
-    void norm2(const double2 *v)
+    // squared norm of v (len elements, default the Krylov length) into st->nrm2
+    void norm2(const double2 *v, long long len = -1)
     {
-        k_multidot<<<LS_RED_BLOCKS, LS_RED_THREADS, 0, st>>>(v, 0, 1, v, N, W.partial);
+        k_multidot<<<LS_RED_BLOCKS, LS_RED_THREADS, 0, st>>>(v, 0, 1, v, len < 0 ? N : len, W.partial);
         k_finalize_dots<<<1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, 1, &W.st->nrm2, 0);
+    }
+
+    // ||v|| of len elements, waited for
+    double norm_of(const double2 *v, long long len)
+    {
+        norm2(v, len);
+        k_gmres_init<<<1, 32, 0, st>>>(W.st);
+        return read_scalar(&W.st->res);
     }
 
     double read_scalar(const double *dptr)
@@ -520,10 +552,16 @@ struct Solver {
 
 using namespace wsc;
 
-extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, void *x,
-                                const ls_opts *opts_in, ls_info *info, void *stream)
+// K right-hand sides with one operator (same plan and contrast): GMRES on the stacked system
+// diag(L, ..., L) [x_1; ...; x_K] = [f_1; ...; f_K] / scales, each f_s scaled to unit norm, so
+// that one stacked residual ||r|| <= tol / sqrt(K) ||[f]|| = tol bounds every system's relative
+// residual ||r_s|| / ||f_s|| by tol.  Every matvec is one batched apply of K densities; the
+// Krylov vectors are K n^2 long.  K = 1 is the plain solve.
+static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, void *x, int K,
+                                 const ls_opts *opts_in, ls_info *info, void *stream)
 {
     if (!p || !m || !f || !x) return fail(CONV_EINVAL, "bad argument");
+    if (K < 1) return fail(CONV_EINVAL, "count must be >= 1");
     if (p->kern.family != CONV_K_HELMHOLTZ || p->io != CONV_IO_C2C)
         return fail(CONV_EINVAL, "ls_solve needs a C2C Helmholtz plan");
     ls_opts o = {50, 2000, 1e-10, 0, 1e-5, 1};
@@ -532,8 +570,9 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
     if (o.max_iters < 1) return fail(CONV_EINVAL, "max_iters must be >= 1");
     if (!(o.tol > 0)) return fail(CONV_EINVAL, "tol must be > 0");
     if (o.refine && !(o.inner_tol > 0 && o.inner_tol < 1)) return fail(CONV_EINVAL, "inner_tol must be in (0, 1)");
+    if (K > 65535) return fail(CONV_EINVAL, "count must be <= 65535");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const long long N = (long long)p->n * p->n;
+    const long long NN = (long long)p->n * p->n, N = NN * K;
 
     // FP64 operator for true residuals
     conv_plan_s *p64 = p;
@@ -547,6 +586,10 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
         }
         p64 = p->fp64_twin;
     }
+    // matvec workspaces for a batch beyond the plans' own
+    size_t cws = 0, cws64 = 0;
+    if (K > p->batch_max) conv_workspace_size(p, K, &cws);
+    if (p64 != p && K > p64->batch_max) conv_workspace_size(p64, K, &cws64);
 
     Solver S;
     S.p = p;
@@ -554,12 +597,14 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
     S.m64 = m;
     S.kappa2 = p->kern.kappa * p->kern.kappa;
     S.N = N;
+    S.batch = K;
     S.restart = o.restart;
     S.st = st;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     S.grid_elem = (int)std::min<long long>((N + 255) / 256, (long long)sms * 8);
-    // workspace: the plan's cached one when free (reallocated if too small), else a private one
+    // workspace: the plan's cached one when free (reallocated if it does not match), else a
+    // private one
     const bool mixed = p->prec == CONV_P_FP32;
     LsCache *cache;
     {
@@ -570,7 +615,7 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
     std::unique_lock<std::mutex> own(cache->mu, std::try_to_lock);
     const bool cached = own.owns_lock();
     if (cached) {
-        if (cache->W.V && (cache->N != N || cache->restart < o.restart || (mixed && !cache->mixed))) {
+        if (cache->W.V && (cache->N != N || cache->batch != K || cache->restart < o.restart || (mixed && !cache->mixed))) {
             cudaStreamSynchronize(st);
             drop_graphs(cache);
             free_work(cache->W);
@@ -578,21 +623,22 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
             cache->m64 = nullptr;
         }
         if (!cache->W.V) {
-            if (!alloc_work(cache->W, N, o.restart, mixed)) {
+            if (!alloc_work(cache->W, N, NN, K, cws, cws64, o.restart, mixed)) {
                 free_work(cache->W);
                 return fail(CONV_ENOMEM, "ls_solve workspace allocation failed");
             }
             cache->N = N;
+            cache->batch = K;
             cache->restart = o.restart;
             cache->mixed = mixed;
         }
         S.W = cache->W;
         if (!mixed) {  // the FP64 matvec reads the contrast from the plan's copy
-            if (!cache->m64 && cudaMalloc(&cache->m64, N * sizeof(double)) != cudaSuccess) {
+            if (!cache->m64 && cudaMalloc(&cache->m64, NN * sizeof(double)) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(CONV_ENOMEM, "ls_solve contrast buffer");
             }
-            WSC_CUDA(cudaMemcpyAsync(cache->m64, m, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            WSC_CUDA(cudaMemcpyAsync(cache->m64, m, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
             S.m64 = cache->m64;
         }
         if (!cache->cap && cudaStreamCreateWithFlags(&cache->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -603,15 +649,29 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
             S.graphs = &cache->iter;
             S.cap_stream = cache->cap;
         }
-    } else if (!alloc_work(S.W, N, o.restart, mixed)) {
+    } else if (!alloc_work(S.W, N, NN, K, cws, cws64, o.restart, mixed)) {
         free_work(S.W);
         return fail(CONV_ENOMEM, "ls_solve workspace allocation failed");
     }
-    if (p->prec == CONV_P_FP32) k_d2f<<<S.grid_elem, 256, 0, st>>>(m, S.W.m32, N);
+    if (p->prec == CONV_P_FP32) k_d2f<<<S.grid_elem, 256, 0, st>>>(m, S.W.m32, NN);
 
     const double2 *fb = reinterpret_cast<const double2 *>(f);
     double2 *xb = reinterpret_cast<double2 *>(x);
     if (o.zero_guess) cudaMemsetAsync(xb, 0, N * sizeof(double2), st);
+    // several right-hand sides: unit-norm copies, the initial guesses scaled alike
+    std::vector<double> scale(K, 1.0);
+    double tol = o.tol;
+    if (K > 1) {
+        WSC_CUDA(cudaMemcpyAsync(S.W.fsc, fb, N * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        for (int k = 0; k < K; ++k) {
+            const double nk = S.norm_of(fb + (size_t)k * NN, NN);
+            scale[k] = nk > 0 ? nk : 1.0;
+            k_scale_real<<<S.grid_elem, 256, 0, st>>>(S.W.fsc + (size_t)k * NN, 1.0 / scale[k], NN);
+            if (!o.zero_guess) k_scale_real<<<S.grid_elem, 256, 0, st>>>(xb + (size_t)k * NN, 1.0 / scale[k], NN);
+        }
+        fb = S.W.fsc;
+        tol = o.tol / std::sqrt((double)K);
+    }
     S.norm2(fb);
     k_gmres_init<<<1, 32, 0, st>>>(S.W.st);
     double fn = S.read_scalar(&S.W.st->res);
@@ -621,7 +681,7 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
     double res = 0;
     conv_status rc = CONV_OK;
     if (!o.refine || p->prec == CONV_P_FP64) {
-        rc = S.gmres(fb, xb, o.tol * fn, o.max_iters, o.zero_guess != 0, iters, cycles, res);
+        rc = S.gmres(fb, xb, tol * fn, o.max_iters, o.zero_guess != 0, iters, cycles, res);
     } else {
         // FP64 iterative refinement around an FP32-matvec GMRES
         bool first = o.zero_guess != 0;
@@ -640,7 +700,7 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
                 rc = fail(CONV_ENONFINITE, "residual is not finite");
                 break;
             }
-            if (rn <= o.tol * fn) break;
+            if (rn <= tol * fn) break;
             if (iters >= o.max_iters) {
                 rc = fail(CONV_ENOTCONVERGED, "GMRES-IR reached its iteration limit");
                 break;
@@ -648,7 +708,7 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
             // inner solve L32 c = r from c = 0 to inner_tol relative (never tighter than the outer
             // target needs), then x += c
             cudaMemsetAsync(S.W.x64, 0, N * sizeof(double2), st);
-            double inner_abs = std::max(o.inner_tol * rn, 0.5 * o.tol * fn);
+            double inner_abs = std::max(o.inner_tol * rn, 0.5 * tol * fn);
             int it_before = iters;
             double inner_res = 0;
             conv_status irc = S.gmres(S.W.d, S.W.x64, inner_abs, o.max_iters, true, iters, cycles, inner_res);
@@ -666,25 +726,45 @@ extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, v
             }
         }
     }
-    // final true residual with the FP64 operator
+    // final true residual with the FP64 operator, per right-hand side
+    std::vector<double> rel(K, 0.0);
     if (rc == CONV_OK || rc == CONV_ENOTCONVERGED) {
         conv_status r2 = S.true_residual(fb, xb, S.W.r);
         if (r2 == CONV_OK) {
-            S.norm2(S.W.r);
-            k_gmres_init<<<1, 32, 0, st>>>(S.W.st);
-            res = S.read_scalar(&S.W.st->res);
+            if (K == 1) {
+                S.norm2(S.W.r);
+                k_gmres_init<<<1, 32, 0, st>>>(S.W.st);
+                rel[0] = S.read_scalar(&S.W.st->res) / fn;
+            } else {
+                for (int k = 0; k < K; ++k) rel[k] = S.norm_of(S.W.r + (size_t)k * NN, NN);  // ||f_s|| = 1
+            }
         }
     }
+    if (K > 1)
+        for (int k = 0; k < K; ++k) k_scale_real<<<S.grid_elem, 256, 0, st>>>(xb + (size_t)k * NN, scale[k], NN);
     cudaError_t ce = cudaStreamSynchronize(st);
     if (!cached) free_work(S.W);
-    if (info) {
-        info->iters = iters;
-        info->restarts = cycles;
-        info->refinements = refinements;
-        info->rel_residual = res / fn;
-    }
+    if (info)
+        for (int k = 0; k < K; ++k) {
+            info[k].iters = iters;
+            info[k].restarts = cycles;
+            info[k].refinements = refinements;
+            info[k].rel_residual = rel[k];
+        }
     if (ce != cudaSuccess) return cuda_fail(ce, "ls_solve");
     // a pass kernel that gave up on a bounded wait leaves the solve's matvecs incomplete
     const conv_status ds = conv_device_status(p, stream);
     return ds != CONV_OK ? ds : rc;
+}
+
+extern "C" conv_status ls_solve(conv_plan_t p, const double *m, const void *f, void *x, const ls_opts *opts,
+                                ls_info *info, void *stream)
+{
+    return ls_solve_impl(p, m, f, x, 1, opts, info, stream);
+}
+
+extern "C" conv_status ls_solve_multi(conv_plan_t p, int count, const double *m, const void *f, void *x,
+                                      const ls_opts *opts, ls_info *info, void *stream)
+{
+    return ls_solve_impl(p, m, f, x, count, opts, info, stream);
 }

@@ -140,10 +140,12 @@ def lippmann_contrast(n, kind="bump"):
     raise ValueError(kind)
 
 
-def plane_wave(n, kappa):
-    """u_inc(x) = exp(i kappa x1) on the grid."""
-    X1, _ = grid(n)
-    return np.exp(1j * kappa * X1)
+def plane_wave(n, kappa, angle=0.0):
+    """u_inc(x) = exp(i kappa (x1 cos angle + x2 sin angle)) on the grid (angle 0: exp(i kappa x1))."""
+    X1, X2 = grid(n)
+    if angle == 0.0:
+        return np.exp(1j * kappa * X1)
+    return np.exp(1j * kappa * (X1 * np.cos(angle) + X2 * np.sin(angle)))
 
 
 SERVING_SIZES = (128, 256, 512, 1024, 2048)
