@@ -343,6 +343,23 @@ def r2r_bytes(plan, batch):
     return batch * 2 * h * n * esz + h * h * (esz // 2)
 
 
+def cols_roofline(run, batch, peak_tflops, hbm, peak_source):
+    """Column-pass rooflines of the R2R plans of a timed sweep: the ALU view (5 L log2 L flops per
+    transform, two transforms per column, h = L/2 + 1 columns per density) and the HBM view
+    (algorithmic bytes of r2r_bytes)."""
+    r = [(p, t) for p, t in zip(run["plans"], run["passes"]) if p.io == "r2r"]
+    ms = sum(t[0][1] for _, t in r) / sum(t[1] for _, t in r)
+    plan = r[0][0]
+    L = plan.info.transform_len
+    flops = 5.0 * L * math.log2(L) * 2 * (L // 2 + 1) * batch
+    byts = r2r_bytes(plan, batch)
+    tf = flops / (ms * 1e-3) / 1e12
+    gbs = byts / (ms * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": tf, "peak": peak_tflops, "unit": "TFLOP/s", "frac": tf / peak_tflops,
+            "peak_source": peak_source, "avg_launch_ms": ms, "transform_len": L,
+            "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}}
+
+
 def ls_leg(n, kappa, repeats, stream):
     import torch
     from paper_2107_03958_gb300 import inputs
@@ -689,8 +706,18 @@ def main():
         n2 = args.n // 2
         l2 = sweep_leg(n2, args.batch, "fp32", args.steps, args.warmup, stream)
         l2_ms = max_over_ranks(ws, l2["ms"])
+        l2t = sweep_leg(n2, args.batch, "fp32", 3, 1, stream, timing=True)
         extras["fp32_n%d" % n2] = {"value": ws * 5 * args.batch * args.steps / (l2_ms * 1e-3),
-                                   "unit": "conv/s", "ms_per_step": l2_ms / args.steps}
+                                   "unit": "conv/s", "ms_per_step": l2_ms / args.steps,
+                                   "roofline_cols": cols_roofline(l2t, args.batch, FP32_SM_PEAK_TFLOPS, hbm,
+                                                                  "FP32 FMA unit count x 2070 MHz")}
+        k64b = max(2, args.steps // 3)
+        f64b = sweep_leg(n2, args.batch, "fp64", k64b, 1, stream, timing=True)
+        f64b_ms = max_over_ranks(ws, f64b["ms"])
+        extras["fp64_n%d" % n2] = {"value": ws * 5 * args.batch * k64b / (f64b_ms * 1e-3), "unit": "conv/s",
+                                   "ms_per_step": f64b_ms / k64b, "steps": k64b,
+                                   "roofline_cols": cols_roofline(f64b, args.batch, peaks["fp64_tflops"], hbm,
+                                                                  "measured FP64 FMA microbenchmark")}
         extras["ls"] = ls_leg(512, 40.0, 5, stream)
         extras["ls_larger"] = [ls_leg(1024, 40.0, 3, stream), ls_leg(2048, 40.0, 3, stream)]
         extras["ls_multi_rhs"] = ls_multi_leg(512, 40.0, 8, 3, stream)

@@ -420,3 +420,16 @@ def test_fourier_smoothed_convolution(prec):
     om = O.fs_mask(n, 3.0, "disk", (0.5, 0.5, 0.3), 0.15)
     ref = O.conv(ut * om, plan.M, O.ghat_full("pow", plan.M, 3.0, plan.a, gamma=-1.0)).real
     assert _relerr(ref, out) <= TOL[prec]
+
+
+def test_lines_beyond_one_cta_are_reported_unsupported():
+    """A line of a transform lives in one CTA's shared memory, the plan's FP64 line transforms
+    included: n = 8192 (FP64 passes at L = 16384, the compact weights' FP64 lines of 3n and 2n,
+    FP32 period-3 lines of 24576 at more than 1024 threads) is refused with CONV_EUNSUPPORTED, and
+    n = 4096 builds in both precisions."""
+    from paper_2107_03958_gb300._native import ConvError
+    for prec, compact in (("fp64", True), ("fp32", True), ("fp32", False), ("fp64", False)):
+        with pytest.raises(ConvError, match="CONV_EUNSUPPORTED"):
+            ConvPlan("log", n=8192, period=3, precision=prec, io="r2r", compact=compact)
+    for prec in ("fp32", "fp64"):
+        assert ConvPlan("log", n=4096, period=3, precision=prec, io="r2r", compact=True).info.transform_len == 8192
