@@ -162,6 +162,42 @@ static void gauss_legendre(int n, double *x, double *w)
 
 conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, double *g2_out, cudaStream_t st);
 
+// The FP64 tables of plan src (same kernel, period, n, radius and embedding) copied into p, then
+// p's FP32 multiplier from them if p is FP32.
+conv_status copy_ghat(conv_plan_s *p, const conv_plan_s *src)
+{
+    cudaStream_t st = p->setup_stream;
+    p->ghat_bytes = src->ghat_bytes;
+    if (cudaMalloc(&p->ghat_paper, p->ghat_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CONV_ENOMEM, "cudaMalloc of the moment table failed");
+    }
+    WSC_CUDA(cudaMemcpyAsync(p->ghat_paper, src->ghat_paper, p->ghat_bytes, cudaMemcpyDeviceToDevice, st));
+    if (p->compact) {
+        p->table_bytes = src->table_bytes;
+        if (cudaMalloc(&p->ghat64, p->table_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CONV_ENOMEM, "cudaMalloc of the compact multiplier failed");
+        }
+        WSC_CUDA(cudaMemcpyAsync(p->ghat64, src->ghat64, p->table_bytes, cudaMemcpyDeviceToDevice, st));
+    } else {
+        p->ghat64 = p->ghat_paper;
+        p->table_bytes = p->ghat_bytes;
+    }
+    if (p->prec == CONV_P_FP32) {
+        const long long NT = (long long)(p->table_bytes / sizeof(double));
+        if (cudaMalloc(&p->ghat32, (size_t)NT * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CONV_ENOMEM, "cudaMalloc of the FP32 multiplier failed");
+        }
+        const int b2 = (int)std::min<long long>((NT + 255) / 256, 152LL * 16);
+        k_to_f32<<<b2, 256, 0, st>>>(p->ghat64, reinterpret_cast<float *>(p->ghat32), NT);
+        WSC_CUDA(cudaGetLastError());
+    }
+    WSC_CUDA(cudaStreamSynchronize(st));
+    return CONV_OK;
+}
+
 conv_status build_ghat(conv_plan_s *p)
 {
     double gx[GL_NODES], gw[GL_NODES];

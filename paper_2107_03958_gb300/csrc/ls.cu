@@ -579,8 +579,7 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
     if (p->prec != CONV_P_FP64) {
         if (!p->fp64_twin) {
             conv_plan_t twin = nullptr;
-            conv_status rc = conv_plan_ex(&p->kern, p->pnum, p->pden, p->n, p->a, CONV_P_FP64, CONV_IO_C2C, 1,
-                                          p->compact ? CONV_PLAN_COMPACT : 0, &twin);
+            conv_status rc = conv_plan_twin(p, &twin);
             if (rc != CONV_OK) return rc;
             p->fp64_twin = twin;
         }

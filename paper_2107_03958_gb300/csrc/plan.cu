@@ -241,9 +241,12 @@ conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den,
     return conv_plan_ex(kernel, period_num, period_den, n, trunc_a, precision, io, batch_max, 0, plan);
 }
 
-conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_den, int n,
-                         double trunc_a, conv_precision precision, conv_io io, int batch_max, int flags,
-                         conv_plan_t *plan)
+// The plan constructor behind conv_plan_ex.  share: NULL, or a plan with the same kernel, period,
+// n, truncation radius and embedding whose FP64 tables (moments, compact multiplier) are copied
+// instead of computed again (the FP64 twin of an FP32 plan).
+static conv_status plan_create(const conv_kernel *kernel, int period_num, int period_den, int n, double trunc_a,
+                               conv_precision precision, conv_io io, int batch_max, int flags, const conv_plan_s *share,
+                               conv_plan_t *plan)
 {
     g_last_error.clear();
     if (!plan) return fail(CONV_EINVAL, "plan output pointer is NULL");
@@ -331,7 +334,7 @@ conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_d
         }
     }
     if (rc == CONV_OK) rc = upload_twiddles(p);
-    if (rc == CONV_OK) rc = build_ghat(p);
+    if (rc == CONV_OK) rc = share ? copy_ghat(p, share) : build_ghat(p);
     if (rc == CONV_OK) {
         p->ws_bytes = spectrum_elems(p) * elem_bytes(p) * (size_t)batch_max;
         if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) {
@@ -350,6 +353,13 @@ conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_d
     }
     *plan = p;
     return CONV_OK;
+}
+
+conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_den, int n,
+                         double trunc_a, conv_precision precision, conv_io io, int batch_max, int flags,
+                         conv_plan_t *plan)
+{
+    return plan_create(kernel, period_num, period_den, n, trunc_a, precision, io, batch_max, flags, nullptr, plan);
 }
 
 conv_status conv_device_status(conv_plan_t p, void *stream)
@@ -460,3 +470,13 @@ conv_status conv_timing_read(conv_plan_t p, double ms_out[3], long long *applies
 }
 
 }  // extern "C"
+
+namespace wsc {
+// The FP64 C2C operator of an FP32 plan, for refinement residuals: same kernel, period, n, radius
+// and embedding, batch 1, its FP64 tables copied from the FP32 plan's.
+conv_status conv_plan_twin(const conv_plan_s *p, conv_plan_s **twin)
+{
+    return plan_create(&p->kern, p->pnum, p->pden, p->n, p->a, CONV_P_FP64, CONV_IO_C2C, 1,
+                       p->compact ? CONV_PLAN_COMPACT : 0, p, twin);
+}
+}  // namespace wsc

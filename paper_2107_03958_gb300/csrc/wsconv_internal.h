@@ -137,6 +137,9 @@ conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, voi
 conv_status select_transform(conv_plan_s *p);
 // ghat.cu
 conv_status build_ghat(conv_plan_s *p);
+conv_status copy_ghat(conv_plan_s *p, const conv_plan_s *src);  // src's FP64 tables, no recomputation
+// plan.cu: the FP64 C2C twin of an FP32 plan (refinement residuals), tables copied from it
+conv_status conv_plan_twin(const conv_plan_s *p, conv_plan_s **twin);
 size_t spectrum_elems(const conv_plan_s *p);  // complex elements of the workspace per density
 void destroy_hostpipe(conv_plan_s *p);          // host_io.cu (both host pipelines)
 void destroy_ls_cache(conv_plan_s *p);          // ls.cu
