@@ -111,8 +111,32 @@ static PlanKey key_of(const srv_request &r)
     return k;
 }
 
+// Bytes of one LS solve's Krylov basis and vectors.
+static size_t request_bytes(const srv_request &r)
+{
+    if (r.kind != SRV_LS) return 0;
+    const size_t N = (size_t)r.n * r.n;
+    const int restart = r.restart > 0 ? r.restart : 50;
+    return N * 16 * (restart + 5) + N * 8 * 4;
+}
+
+// What an LS plan keeps after its first solve, for as long as it stays cached: the Krylov
+// workspace (ls_solve keeps one with the plan) and, in mixed precision, the FP64 twin (its copies
+// of the moment and compact tables and its workspace).
+static size_t ls_resident_bytes(const srv_request &r, int flags)
+{
+    if (r.kind != SRV_LS) return 0;
+    const long long n = r.n, Mb = n * r.period_num / r.period_den;
+    const long long M = (flags & CONV_PLAN_COMPACT) ? 2 * n : Mb, h = M / 2 + 1, hb = Mb / 2 + 1;
+    size_t twin = 0;
+    if (r.precision == CONV_P_FP32)
+        twin = (size_t)hb * hb * 16 + ((flags & CONV_PLAN_COMPACT) ? (size_t)h * h * 16 : 0) + (size_t)M * n * 16;
+    return request_bytes(r) + twin;
+}
+
 // Device bytes of a plan (moment table, twiddles, workspace) plus, for conv plans, the staging
-// buffers of one batch; estimated from the sizes before the plan exists.
+// buffers of one batch, and for LS plans what ls_resident_bytes counts; estimated from the sizes
+// before the plan exists.
 static size_t plan_bytes_estimate(const srv_request &r, int batch_max, int flags)
 {
     const long long n = r.n, Mb = n * r.period_num / r.period_den;
@@ -132,18 +156,7 @@ static size_t plan_bytes_estimate(const srv_request &r, int batch_max, int flags
         const size_t out_b = (size_t)n * n * (r.io == CONV_IO_R2R ? cz / 2 : cz);
         stage = (in_b + out_b) * batch_max;
     }
-    size_t twin = 0;
-    if (r.kind == SRV_LS && r.precision == CONV_P_FP32) twin = (size_t)h * h * 16 + (size_t)M * n * 16;
-    return ghat + ws + stage + twin + (size_t)M * cz * 4;
-}
-
-// Per-request bytes beyond the plan: the LS solver's Krylov basis and vectors.
-static size_t request_bytes(const srv_request &r)
-{
-    if (r.kind != SRV_LS) return 0;
-    const size_t N = (size_t)r.n * r.n;
-    const int restart = r.restart > 0 ? r.restart : 50;
-    return N * 16 * (restart + 5) + N * 8 * 4;
+    return ghat + ws + stage + ls_resident_bytes(r, flags) + (size_t)M * cz * 4;
 }
 
 static void finish(srv_t s, const std::shared_ptr<Req> &q, int status, double t_done)
@@ -196,7 +209,8 @@ static std::shared_ptr<CachedPlan> get_plan(srv_t s, const srv_request &r, int &
     cudaStreamCreateWithFlags(&cp->stream, cudaStreamNonBlocking);
     conv_plan_info inf;
     conv_get_info(cp->plan, &inf);
-    cp->bytes = inf.ghat_bytes + inf.workspace_bytes + (inf.precision == CONV_P_FP32 ? inf.ghat_bytes / 2 : 0);
+    cp->bytes = inf.ghat_bytes + inf.workspace_bytes + (inf.precision == CONV_P_FP32 ? inf.ghat_bytes / 2 : 0) +
+                ls_resident_bytes(r, s->plan_flags);
     if (r.kind == SRV_CONV) {
         const size_t cz = 2 * elem_bytes_of(r.precision);
         const size_t in_b = (size_t)r.n * r.n * (io == CONV_IO_C2C ? cz : cz / 2);
@@ -273,8 +287,12 @@ static void dispatcher_loop(srv_t s)
             auto q = *it;
             if (s->inflight_reqs >= s->max_inflight) break;
             PlanKey k = key_of(q->r);
-            const bool have = s->plans.count(k) != 0;
-            const size_t need = request_bytes(q->r) + (have ? 0 : plan_bytes_estimate(q->r, s->batch_max, s->plan_flags));
+            const auto pit = s->plans.find(k);
+            const bool have = pit != s->plans.end();
+            // an LS solve on an idle plan uses the Krylov workspace the plan keeps (counted in its
+            // bytes); one beside another solve on the same plan allocates its own
+            const size_t extra = (have && pit->second->users > 0) ? request_bytes(q->r) : 0;
+            const size_t need = extra + (have ? 0 : plan_bytes_estimate(q->r, s->batch_max, s->plan_flags));
             if (need > s->budget) {  // can never fit
                 it = s->pending.erase(it);
                 s->inflight_reqs++;
@@ -298,8 +316,8 @@ static void dispatcher_loop(srv_t s)
                 continue;
             }
             q->cp = cp;
+            q->need = cp->users > 0 ? request_bytes(q->r) : 0;
             cp->users++;
-            q->need = request_bytes(q->r);
             s->in_use += q->need;
             admitted.push_back(q);
         }

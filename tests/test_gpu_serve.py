@@ -89,3 +89,23 @@ def test_budget_admission_and_rejection():
     r = srv.wait(srv.submit_conv(big, bo, kernel="log", precision="fp64"), timeout_s=60)
     assert r["status"] == "CONV_ENOMEM"
     srv.close()
+
+
+def test_cached_ls_plans_count_their_krylov_workspace():
+    """An LS plan keeps its Krylov workspace (and its FP64 twin) after the solve, for as long as the
+    server caches it: the budget counts them, and a second LS plan that would not fit beside the
+    first evicts it instead of exceeding the budget."""
+    n = 256
+    basis = n * n * 16 * 51
+    budget = int(1.6 * basis)
+    srv = Server(mem_budget_bytes=budget, max_inflight=4, conv_batch_max=4, ls_workers=1, compact=True)
+    m = torch.tensor(inputs.lippmann_contrast(n, "bump"), device="cuda")
+    for i, kappa in enumerate((11.0, 23.0)):
+        f = torch.tensor(inputs.plane_wave(n, kappa), device="cuda")
+        x = torch.zeros_like(f)
+        r = srv.wait(srv.submit_ls(m, f, x, kappa, precision="fp32"), timeout_s=120)
+        assert r["status"] == "CONV_OK" and r["rel_residual"] <= 1.05e-10, r
+        st = srv.stats()
+        assert basis <= st["bytes_in_use"] <= budget, st
+        assert st["plans_evicted"] == i, st
+    srv.close()
