@@ -360,6 +360,47 @@ def cols_roofline(run, batch, peak_tflops, hbm, peak_source):
             "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}}
 
 
+def n8192_leg(steps, stream, hbm):
+    """The largest grid of the discontinuous-density sweep: n = 8192, batch 8, log kernel, FP32 R2R
+    on the compact grid (L = 16384, runtime stage structure at 1024 threads per line)."""
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import ConvPlan
+    n, B = 8192, 8
+    t0 = time.perf_counter()
+    plan = ConvPlan("log", n=n, period=3, precision="fp32", io="r2r", batch_max=B, compact=True)
+    plan_s = time.perf_counter() - t0
+    u = torch.from_numpy(inputs.bump_sums(n, B, seed=81)).float().cuda()
+    out = torch.empty_like(u)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            plan.apply(u, out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.apply(u, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plan.timing(True)
+    for _ in range(2):
+        plan.apply(u, out=out, stream=stream)
+    t, cnt = plan.timing_read()
+    plan.timing(False)
+    plan.device_status()
+    col_ms = t[1] / cnt
+    L = plan.info.transform_len
+    flops = 5.0 * L * math.log2(L) * 2 * (L // 2 + 1) * B
+    byts = r2r_bytes(plan, B)
+    return {"value": B / (ms * 1e-3), "unit": "conv/s", "batch": B, "ms_per_batch": ms, "transform_len": L,
+            "plan_build_s": plan_s, "pass_ms": [x / cnt for x in t],
+            "roofline_cols": {"bound": "alu", "achieved": flops / (col_ms * 1e-3) / 1e12, "peak": FP32_SM_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": flops / (col_ms * 1e-3) / 1e12 / FP32_SM_PEAK_TFLOPS,
+                              "hbm": {"achieved": byts / (col_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                      "frac": byts / (col_ms * 1e-3) / 1e9 / hbm}}}
+
+
 def ls_leg(n, kappa, repeats, stream):
     import torch
     from paper_2107_03958_gb300 import inputs
@@ -718,6 +759,7 @@ def main():
                                    "ms_per_step": f64b_ms / k64b, "steps": k64b,
                                    "roofline_cols": cols_roofline(f64b, args.batch, peaks["fp64_tflops"], hbm,
                                                                   "measured FP64 FMA microbenchmark")}
+        extras["fp32_n8192"] = n8192_leg(5, stream, hbm)
         extras["ls"] = ls_leg(512, 40.0, 5, stream)
         extras["ls_larger"] = [ls_leg(1024, 40.0, 3, stream), ls_leg(2048, 40.0, 3, stream)]
         extras["ls_multi_rhs"] = ls_multi_leg(512, 40.0, 8, 3, stream)

@@ -24,6 +24,8 @@
 //   DFT cropped to the n x n quadrant of w (w is even in each index), then an L x L forward DFT whose
 //   (n+1) x (n+1) quadrant is kept (G2 is even as well).
 #include <cmath>
+#include <cstdlib>
+#include <string>
 #include <vector>
 
 #include "passes.cuh"
@@ -115,6 +117,64 @@ __global__ void __launch_bounds__(512, 1) k_lines(LineGen G, double2 *__restrict
     }
 }
 
+// Lines longer than one CTA holds: DFT_L = DFT_L2 after twiddles after DFT_L1 (L = L1 L2, the
+// four-step split).  X[k1 + L1 k2] = sum_{n2} W_L2^{n2 k2} W_L^{n2 k1} sum_{n1} W_L1^{n1 k1} x[L2 n1 + n2]
+// (W_N = e^{-+2 pi i/N}).  Step 1: per (line, n2), the length-L1 transform over n1, times the
+// twiddle, into T[line][k1][n2]; step 2: per (line, k1), the length-L2 transform over n2, outputs
+// k = k1 + L1 k2 < keep.  T lives in global memory (plan time only).
+template <bool INV>
+__global__ void __launch_bounds__(512, 1) k_lines_split1(LineGen G, double2 *__restrict__ T, int nlines, int L1, int L2,
+                                                         const FFTDesc *__restrict__ P, const double2 *__restrict__ tw,
+                                                         int tpt)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *buf = reinterpret_cast<double2 *>(smem_raw);
+    const int lt = threadIdx.x;
+    const long long L = (long long)L1 * L2, subs = (long long)nlines * L2;
+    for (long long sidx = blockIdx.x; sidx < subs; sidx += gridDim.x) {
+        const int line = (int)(sidx / L2), n2 = (int)(sidx - (long long)line * L2);
+        for (int e = lt; e < L1; e += tpt) buf[pidx<double>(e)] = line_value(G, line, e * L2 + n2);
+        __syncthreads();
+        fft_smem<double, 0, INV, false>(buf, P, tw, lt, tpt);
+        for (int k1 = lt; k1 < L1; k1 += tpt) {
+            const double2 v = buf[pidx<double>(k1)];
+            double sn, cs;
+            // W_L^{n2 k1} = e^{-+2 pi i n2 k1 / L}: sincospi of 2 (n2 k1 mod L) / L
+            sincospi(2.0 * (double)(((long long)n2 * k1) % L) / (double)L, &sn, &cs);
+            if (!INV) sn = -sn;
+            T[((size_t)line * L1 + k1) * L2 + n2] = make_double2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+        }
+        __syncthreads();
+    }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(512, 1) k_lines_split2(const double2 *__restrict__ T, double2 *__restrict__ out,
+                                                         int nlines, int L1, int L2, int keep, long long ol,
+                                                         long long oe, double scale, const FFTDesc *__restrict__ P,
+                                                         const double2 *__restrict__ tw, int tpt)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *buf = reinterpret_cast<double2 *>(smem_raw);
+    const int lt = threadIdx.x;
+    const long long subs = (long long)nlines * L1;
+    for (long long sidx = blockIdx.x; sidx < subs; sidx += gridDim.x) {
+        const int line = (int)(sidx / L1), k1 = (int)(sidx - (long long)line * L1);
+        const double2 *src = T + ((size_t)line * L1 + k1) * L2;
+        for (int e = lt; e < L2; e += tpt) buf[pidx<double>(e)] = src[e];
+        __syncthreads();
+        fft_smem<double, 0, INV, false>(buf, P, tw, lt, tpt);
+        for (int k2 = lt; k2 < L2; k2 += tpt) {
+            const long long k = k1 + (long long)L1 * k2;
+            if (k < keep) {
+                const double2 v = buf[pidx<double>(k2)];
+                out[line * ol + k * oe] = make_double2(scale * v.x, scale * v.y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __device__ double varkappa(double t)
 {
     if (t <= 0.0) return 1.0;
@@ -157,7 +217,9 @@ int generic_threads(const FFTDesc &P);
 bool factorize_any(int L, FFTDesc &d);
 void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im);
 
-// Device-side FFT set-up of one line length (descriptor, twiddles, launch shape).
+// Device-side FFT set-up of one line length (descriptor, twiddles, launch shape).  A line that one
+// CTA cannot hold (or any line with WSCONV_LINE_SPLIT=1, for tests) runs as the four-step split
+// L = L1 L2 into two shorter line transforms with a global-memory buffer between them.
 struct LineFFT {
     FFTDesc d;
     FFTDesc *dd = nullptr;
@@ -165,13 +227,54 @@ struct LineFFT {
     int tpt = 0;
     size_t smem = 0;
     std::vector<double> twh;
+    int L = 0, L1 = 0, L2 = 0;                 // L1 > 0: the split path
+    LineFFT *f1 = nullptr, *f2 = nullptr;      // its two line lengths
     ~LineFFT()
     {
         cudaFree(dd);
         cudaFree(tw);
+        delete f1;
+        delete f2;
     }
-    conv_status init(int L, cudaStream_t st)
+    static bool fits(int L, int &tpt_out)
     {
+        FFTDesc d;
+        if (!factorize_any(L, d)) return false;
+        const int tpt = generic_threads(d);
+        int optin = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        tpt_out = tpt;
+        return (size_t)padded_len<double>(L) * sizeof(double2) <= (size_t)optin && tpt <= 512;
+    }
+    conv_status init(int Lin, cudaStream_t st)
+    {
+        L = Lin;
+        int t = 0;
+        const char *force = getenv("WSCONV_LINE_SPLIT");
+        const bool split = !fits(L, t) || (force && atoi(force) == 1 && L >= 16);
+        if (split) {
+            // the most balanced factor pair whose parts both fit (L1 <= L2)
+            for (int a = (int)std::sqrt((double)L); a >= 2 && !L1; --a) {
+                if (L % a) continue;
+                int t1 = 0, t2 = 0;
+                if (fits(a, t1) && fits(L / a, t2)) {
+                    L1 = a;
+                    L2 = L / a;
+                }
+            }
+            if (!L1) return fail(CONV_EUNSUPPORTED, "FP64 line length " + std::to_string(L) + " has no four-step split");
+            f1 = new LineFFT();
+            f2 = new LineFFT();
+            conv_status rc = f1->init_direct(L1, st);
+            if (rc == CONV_OK) rc = f2->init_direct(L2, st);
+            return rc;
+        }
+        return init_direct(L, st);
+    }
+    conv_status init_direct(int Lin, cudaStream_t st)
+    {
+        L = Lin;
         if (!factorize_any(L, d)) return fail(CONV_EUNSUPPORTED, "line length not 2^a 3^b 5^c");
         tpt = generic_threads(d);
         smem = (size_t)padded_len<double>(L) * sizeof(double2);
@@ -189,13 +292,32 @@ struct LineFFT {
         // the opt-in maximum, so line transforms of any length can follow each other
         WSC_CUDA(cudaFuncSetAttribute(k_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         WSC_CUDA(cudaFuncSetAttribute(k_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        WSC_CUDA(cudaFuncSetAttribute(k_lines_split1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        WSC_CUDA(cudaFuncSetAttribute(k_lines_split1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        WSC_CUDA(cudaFuncSetAttribute(k_lines_split2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        WSC_CUDA(cudaFuncSetAttribute(k_lines_split2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         return CONV_OK;
     }
     template <bool INV>
-    void run(const LineGen &G, double2 *out, int nlines, int keep, long long ol, long long oe, double scale,
-             int sms, cudaStream_t st) const
+    conv_status run(const LineGen &G, double2 *out, int nlines, int keep, long long ol, long long oe, double scale,
+                    int sms, cudaStream_t st) const
     {
-        k_lines<INV><<<std::min(nlines, sms * 2), tpt, smem, st>>>(G, out, nlines, keep, ol, oe, scale, dd, tw, tpt);
+        if (!L1) {
+            k_lines<INV><<<std::min(nlines, sms * 2), tpt, smem, st>>>(G, out, nlines, keep, ol, oe, scale, dd, tw, tpt);
+            return CONV_OK;
+        }
+        double2 *T = nullptr;
+        if (cudaMallocAsync(&T, (size_t)nlines * L * sizeof(double2), st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CONV_ENOMEM, "four-step line buffer");
+        }
+        const long long s1 = (long long)nlines * L2, s2 = (long long)nlines * L1;
+        k_lines_split1<INV><<<(int)std::min<long long>(s1, sms * 2LL), f1->tpt, f1->smem, st>>>(G, T, nlines, L1, L2,
+                                                                                             f1->dd, f1->tw, f1->tpt);
+        k_lines_split2<INV><<<(int)std::min<long long>(s2, sms * 2LL), f2->tpt, f2->smem, st>>>(
+            T, out, nlines, L1, L2, keep, ol, oe, scale, f2->dd, f2->tw, f2->tpt);
+        WSC_CUDA(cudaFreeAsync(T, st));
+        return CONV_OK;
     }
 };
 
@@ -236,33 +358,35 @@ conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, dou
     G.L = M;
     G.quad = ghat;
     G.h = h;
-    fm.run<true>(G, t1, M, n, n, 1, 1.0, sms, st);
+    if (rc == CONV_OK) rc = fm.run<true>(G, t1, M, n, n, 1, 1.0, sms, st);
     // rows d1: along k2, keep d2 < n -> w[d1][d2]
     G.mode = 5;
     G.src = t1;
     G.sl = 1;
     G.se = n;
-    fm.run<true>(G, w, n, n, n, 1, 1.0 / ((double)M * (double)M), sms, st);
+    if (rc == CONV_OK) rc = fm.run<true>(G, w, n, n, n, 1, 1.0 / ((double)M * (double)M), sms, st);
     // G2 = DFT_L x L (w on the L-periodic lattice): rows e1 along e2, keep k2 <= n -> t2[k2][e1]
     G.mode = 4;
     G.L = L;
     G.src = w;
     G.n = n;
-    fl.run<false>(G, t2, L, n + 1, 1, L, 1.0, sms, st);
+    if (rc == CONV_OK) rc = fl.run<false>(G, t2, L, n + 1, 1, L, 1.0, sms, st);
     // columns k2 along e1, keep k1 <= n -> g2[k2][k1]
     G.mode = 5;
     G.src = t2;
     G.sl = L;
     G.se = 1;
-    fl.run<false>(G, g2, n + 1, n + 1, n + 1, 1, 1.0, sms, st);
+    if (rc == CONV_OK) rc = fl.run<false>(G, g2, n + 1, n + 1, n + 1, 1, 1.0, sms, st);
     const long long NQ = (long long)n1 * n1;
-    k_take_quadrant<<<(int)std::min<long long>((NQ + 255) / 256, sms * 8LL), 256, 0, st>>>(g2, g2_out, NQ, cplx ? 1 : 0);
+    if (rc == CONV_OK)
+        k_take_quadrant<<<(int)std::min<long long>((NQ + 255) / 256, sms * 8LL), 256, 0, st>>>(g2, g2_out, NQ, cplx ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(t1);
     cudaFree(w);
     cudaFree(t2);
     cudaFree(g2);
+    if (rc != CONV_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "compact-embedding table");
     return CONV_OK;
 }
@@ -294,14 +418,20 @@ extern "C" conv_status conv_fs_mask(conv_plan_t p, int shape, const double *geom
     G.b = p->b;
     for (int i = 0; i < (shape == 0 ? 3 : 4); ++i) G.g[i] = geom[i];
     // columns k2 (lines) of chihat along k1, keep j1 < n -> W[k2][j1]
-    f.run<true>(G, W, M, n, n, 1, 1.0, sms, st);
+    if (rc == CONV_OK) rc = f.run<true>(G, W, M, n, n, 1, 1.0, sms, st);
     // rows j1: along k2, keep j2 < n -> chi[j1][j2]
     G.mode = 5;
     G.src = W;
     G.sl = 1;
     G.se = n;
-    f.run<true>(G, chi, n, n, n, 1, 1.0, sms, st);
+    if (rc == CONV_OK) rc = f.run<true>(G, chi, n, n, n, 1, 1.0, sms, st);
     const int blocks = (int)std::min<long long>(((long long)n * n + 255) / 256, (long long)sms * 8);
+    if (rc != CONV_OK) {
+        cudaStreamSynchronize(st);
+        cudaFree(W);
+        cudaFree(chi);
+        return rc;
+    }
     if (p->prec == CONV_P_FP64)
         k_fs_finish<double><<<blocks, 256, 0, st>>>(chi, reinterpret_cast<double *>(mask), n, delta);
     else

@@ -423,13 +423,46 @@ def test_fourier_smoothed_convolution(prec):
 
 
 def test_lines_beyond_one_cta_are_reported_unsupported():
-    """A line of a transform lives in one CTA's shared memory, the plan's FP64 line transforms
-    included: n = 8192 (FP64 passes at L = 16384, the compact weights' FP64 lines of 3n and 2n,
-    FP32 period-3 lines of 24576 at more than 1024 threads) is refused with CONV_EUNSUPPORTED, and
-    n = 4096 builds in both precisions."""
+    """A pass holds a whole line of the transform in one CTA's shared memory: FP64 passes at
+    L = 16384 (n = 8192 compact) and the FP32 period-3 lines of 24576 at n = 8192 are refused with
+    CONV_EUNSUPPORTED, as is FP64 on the period-3 grid there."""
     from paper_2107_03958_gb300._native import ConvError
-    for prec, compact in (("fp64", True), ("fp32", True), ("fp32", False), ("fp64", False)):
+    for prec, compact in (("fp64", True), ("fp32", False), ("fp64", False)):
         with pytest.raises(ConvError, match="CONV_EUNSUPPORTED"):
             ConvPlan("log", n=8192, period=3, precision=prec, io="r2r", compact=compact)
-    for prec in ("fp32", "fp64"):
-        assert ConvPlan("log", n=4096, period=3, precision=prec, io="r2r", compact=True).info.transform_len == 8192
+
+
+@pytest.mark.parametrize("io", ["r2r", "c2c"])
+def test_split_plan_time_lines_equal_direct(io, monkeypatch):
+    """The plan's FP64 line transforms split four-step (forced here at n = 64, where one CTA holds
+    a line) give the same compact multiplier and FS mask as the direct transforms, to rounding."""
+    n = 64
+    kw = KERNELS["log"] if io == "r2r" else KERNELS["helm20"]
+    u = inputs.bump_sums(n, 2, seed=31)
+    if io == "c2c":
+        u = u + 0.5j * inputs.bump_sums(n, 2, seed=32)
+    outs, masks = [], []
+    for split in ("0", "1"):
+        monkeypatch.setenv("WSCONV_LINE_SPLIT", split)
+        plan = ConvPlan(n=n, period=3, precision="fp64", io=io, compact=True, batch_max=2, **kw)
+        outs.append(plan.apply(torch.tensor(u, dtype=plan.in_dtype(), device="cuda")).cpu().numpy())
+        masks.append(plan.fs_mask("disk", (0.5, 0.5, 0.3)).cpu().numpy())
+    assert _relerr(outs[0], outs[1]) <= 1e-13
+    assert np.max(np.abs(masks[0] - masks[1])) <= 1e-13
+
+
+def test_n8192_fp32_compact_matches_the_analytic_potential():
+    """n = 8192, FP32 passes on the compact grid (L = 16384; the plan's FP64 lines of 24576 and
+    16384 split four-step): the log potential of the Laplacian of a Gaussian sum (the setting of
+    Table 7, alpha = 250) is minus the Gaussian sum.  FP32 rounding of 16384-point transforms sets
+    the error, measured against that closed form."""
+    n = 8192
+    centres = [(0.6, 0.6), (0.5, 0.5), (0.35, 0.6)]
+    f = inputs.gaussian_sum_laplacian(n, 250.0, centres)
+    ex = -inputs.gaussian_sum(n, 250.0, centres)
+    plan = ConvPlan("log", n=n, period=3, precision="fp32", io="r2r", compact=True, scale=-INV2PI)
+    assert plan.info.transform_len == 16384
+    out = plan.apply(torch.tensor(f, dtype=torch.float32, device="cuda")).cpu().numpy()
+    plan.device_status()
+    err = _relerr(ex, out)
+    assert err <= 2e-5, err
