@@ -229,10 +229,11 @@ struct LineFFT {
     std::vector<double> twh;
     int L = 0, L1 = 0, L2 = 0;                 // L1 > 0: the split path
     LineFFT *f1 = nullptr, *f2 = nullptr;      // its two line lengths
+    cudaStream_t st_ = nullptr;                // the tables are allocated and freed in its order
     ~LineFFT()
     {
-        cudaFree(dd);
-        cudaFree(tw);
+        if (dd) cudaFreeAsync(dd, st_);
+        if (tw) cudaFreeAsync(tw, st_);
         delete f1;
         delete f2;
     }
@@ -275,6 +276,7 @@ struct LineFFT {
     conv_status init_direct(int Lin, cudaStream_t st)
     {
         L = Lin;
+        st_ = st;
         if (!factorize_any(L, d)) return fail(CONV_EUNSUPPORTED, "line length not 2^a 3^b 5^c");
         tpt = generic_threads(d);
         smem = (size_t)padded_len<double>(L) * sizeof(double2);
@@ -283,7 +285,8 @@ struct LineFFT {
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (smem > (size_t)optin || tpt > 512) return fail(CONV_EUNSUPPORTED, "FP64 line transform does not fit one CTA");
         stage_twiddles(d, twh);
-        if (cudaMalloc(&dd, sizeof(FFTDesc)) != cudaSuccess || cudaMalloc(&tw, twh.size() * sizeof(double)) != cudaSuccess) {
+        if (cudaMallocAsync(&dd, sizeof(FFTDesc), st) != cudaSuccess ||
+            cudaMallocAsync(&tw, twh.size() * sizeof(double), st) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "line transform tables");
         }
@@ -340,16 +343,19 @@ conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, dou
     if (rc != CONV_OK) return rc;
     double2 *t1 = nullptr, *w = nullptr, *t2 = nullptr, *g2 = nullptr;
     const size_t n1 = (size_t)n + 1;
-    bool ok = cudaMalloc(&t1, (size_t)M * n * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&w, (size_t)n * n * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&t2, n1 * L * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&g2, n1 * n1 * sizeof(double2)) == cudaSuccess;
+    // scratch in stream order: freeing it does not wait for other work on the device (a serving
+    // process builds plans while other requests run)
+    auto release = [&] {
+        for (double2 *q : {t1, w, t2, g2})
+            if (q) cudaFreeAsync(q, st);
+    };
+    bool ok = cudaMallocAsync(&t1, (size_t)M * n * sizeof(double2), st) == cudaSuccess &&
+              cudaMallocAsync(&w, (size_t)n * n * sizeof(double2), st) == cudaSuccess &&
+              cudaMallocAsync(&t2, n1 * L * sizeof(double2), st) == cudaSuccess &&
+              cudaMallocAsync(&g2, n1 * n1 * sizeof(double2), st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        cudaFree(t1);
-        cudaFree(w);
-        cudaFree(t2);
-        cudaFree(g2);
+        release();
         return fail(CONV_ENOMEM, "compact-embedding buffers");
     }
     LineGen G{};
@@ -381,11 +387,8 @@ conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, dou
     if (rc == CONV_OK)
         k_take_quadrant<<<(int)std::min<long long>((NQ + 255) / 256, sms * 8LL), 256, 0, st>>>(g2, g2_out, NQ, cplx ? 1 : 0);
     cudaError_t e = cudaGetLastError();
+    release();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(t1);
-    cudaFree(w);
-    cudaFree(t2);
-    cudaFree(g2);
     if (rc != CONV_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "compact-embedding table");
     return CONV_OK;
@@ -406,10 +409,10 @@ extern "C" conv_status conv_fs_mask(conv_plan_t p, int shape, const double *geom
     conv_status rc = f.init(M, st);
     if (rc != CONV_OK) return rc;
     double2 *W = nullptr, *chi = nullptr;
-    if (cudaMalloc(&W, (size_t)M * n * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&chi, (size_t)n * n * sizeof(double2)) != cudaSuccess) {
+    if (cudaMallocAsync(&W, (size_t)M * n * sizeof(double2), st) != cudaSuccess ||
+        cudaMallocAsync(&chi, (size_t)n * n * sizeof(double2), st) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(W);
+        if (W) cudaFreeAsync(W, st);
         return fail(CONV_ENOMEM, "FS mask buffers");
     }
     LineGen G{};
@@ -427,9 +430,9 @@ extern "C" conv_status conv_fs_mask(conv_plan_t p, int shape, const double *geom
     if (rc == CONV_OK) rc = f.run<true>(G, chi, n, n, n, 1, 1.0, sms, st);
     const int blocks = (int)std::min<long long>(((long long)n * n + 255) / 256, (long long)sms * 8);
     if (rc != CONV_OK) {
+        cudaFreeAsync(W, st);
+        cudaFreeAsync(chi, st);
         cudaStreamSynchronize(st);
-        cudaFree(W);
-        cudaFree(chi);
         return rc;
     }
     if (p->prec == CONV_P_FP64)
@@ -437,9 +440,9 @@ extern "C" conv_status conv_fs_mask(conv_plan_t p, int shape, const double *geom
     else
         k_fs_finish<float><<<blocks, 256, 0, st>>>(chi, reinterpret_cast<float *>(mask), n, delta);
     cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(W, st);
+    cudaFreeAsync(chi, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(W);
-    cudaFree(chi);
     if (e != cudaSuccess) return cuda_fail(e, "conv_fs_mask");
     return CONV_OK;
 }

@@ -235,7 +235,7 @@ conv_status build_ghat(conv_plan_s *p)
                 e[3] = ::y0(arg);
             }
         hnodes = P * GL_NODES;
-        if (cudaMalloc(&htab, tab.size() * sizeof(double)) != cudaSuccess) {
+        if (cudaMallocAsync(&htab, tab.size() * sizeof(double), st) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the Helmholtz quadrature table failed");
         }
@@ -244,11 +244,7 @@ conv_status build_ghat(conv_plan_s *p)
     int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
     k_ghat<<<blocks, 256, 0, st>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, hb,
                                    p->ghat_paper, hka, htab, hnodes);
-    if (htab) {
-        cudaError_t e = cudaStreamSynchronize(st);
-        cudaFree(htab);
-        if (e != cudaSuccess) return cuda_fail(e, "moment table kernel");
-    }
+    if (htab) cudaFreeAsync(htab, st);  // in stream order, after the kernel that reads it
     WSC_CUDA(cudaGetLastError());
     // the passes' multiplier: the moments themselves, or the compact-embedding table built from them
     if (p->compact) {
