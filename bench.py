@@ -362,7 +362,7 @@ def cols_roofline(run, batch, peak_tflops, hbm, peak_source):
 
 def n8192_leg(steps, stream, hbm):
     """The largest grid of the discontinuous-density sweep: n = 8192, batch 8, log kernel, FP32 R2R
-    on the compact grid (L = 16384, runtime stage structure at 1024 threads per line)."""
+    on the compact grid (L = 16384, compile-time stages, 1024 threads per line)."""
     import torch
     from paper_2107_03958_gb300 import inputs
     from paper_2107_03958_gb300.api import ConvPlan

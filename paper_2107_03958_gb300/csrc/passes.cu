@@ -253,6 +253,10 @@ static int generic_tpt(const FFTDesc &P)
             if (tws) { typedef float T_; constexpr int E_ = 24, ED_ = 2012; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 24, ED_ = 2012; constexpr bool W_ = false; CALL; } \
         } \
+        else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 1014) { \
+            if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 1014; constexpr bool W_ = true; CALL; } \
+            else { typedef float T_; constexpr int E_ = 16, ED_ = 1014; constexpr bool W_ = false; CALL; } \
+        } \
         else if ((prec) == CONV_P_FP32 && (E) == 16 && (ED) == 132) { \
             if (tws) { typedef float T_; constexpr int E_ = 16, ED_ = 132; constexpr bool W_ = true; CALL; } \
             else { typedef float T_; constexpr int E_ = 16, ED_ = 132; constexpr bool W_ = false; CALL; } \
@@ -284,12 +288,13 @@ static const int kFusedSets[][3] = {
     {0, 16, 1011},
     {0, 16, 1012},
     {0, 16, 1013},
-    {1, 16, 1008},  // FP32 compile-time power-of-two lengths 2^8 ... 2^13
+    {1, 16, 1008},  // FP32 compile-time power-of-two lengths 2^8 ... 2^14
     {1, 16, 1009},
     {1, 16, 1010},
     {1, 16, 1011},
     {1, 16, 1012},
     {1, 16, 1013},
+    {1, 16, 1014},
     {1, 24, 2007},  // FP32 compile-time lengths 3 2^7 ... 3 2^12 (the period-3 grid, n = 128 ... 4096)
     {1, 24, 2008},
     {1, 24, 2009},
@@ -429,7 +434,7 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         // the compile-time-length kernels: radix-16 stages (L = 2^l; radix 8 and 3 for L = 3 2^l,
         // as factorize gives already), their launch bound
         if (ed < 2000 && !factorize(M, E, d, true, p->prec == CONV_P_FP64)) return false;
-        maxT = std::min(maxT, WSC_STATIC_MAXT);
+        maxT = std::min(maxT, static_max_threads(ed));
         if (tpt > maxT) return false;
     }
     const size_t twb = (size_t)d.tw_len * esz;

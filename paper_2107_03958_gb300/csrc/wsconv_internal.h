@@ -32,10 +32,12 @@ conv_status cuda_fail(cudaError_t e, const char *what);
 // guarded stages): keeps the E values in registers.
 template <typename T, int E> struct maxt { static const int v = (E == 0 || (int)(2 * sizeof(T) * E) > 160) ? 512 : 1024; };
 // Fused passes: the compile-time-length transforms (ED >= 1000) unroll every stage into straight-
-// line code and get 128 registers per thread (at most 512 threads per CTA).
+// line code, one transform of L/E threads per CTA: at most 512 threads (128 registers each), except
+// L = 2^14 at 16 elements per thread, whose 1024 threads get 64 registers.
 #define WSC_STATIC_MAXT 512
+__host__ __device__ constexpr int static_max_threads(int ed) { return ed == 1014 ? 1024 : WSC_STATIC_MAXT; }
 template <typename T, int E, int ED> struct maxt_fused {
-    static const int v = ED >= 1000 ? WSC_STATIC_MAXT : maxt<T, E>::v;
+    static const int v = ED >= 1000 ? static_max_threads(ED) : maxt<T, E>::v;
 };
 
 template <typename T, int E, bool TWS>

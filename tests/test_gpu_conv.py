@@ -270,6 +270,21 @@ def test_multi_plan_host_apply_equals_device_apply(prec):
         apply_host_multi([plans[0], plans[0]], u_host)
 
 
+def test_multi_plan_host_apply_rejects_mismatched_plans():
+    """conv_apply_host_multi needs one n, precision and input type across its plans."""
+    from paper_2107_03958_gb300.api import apply_host_multi
+    from paper_2107_03958_gb300._native import ConvError
+    a = ConvPlan("log", n=64, period=3, precision="fp32", io="r2r")
+    b = ConvPlan("log", n=32, period=3, precision="fp32", io="r2r")
+    c = ConvPlan("log", n=64, period=3, precision="fp64", io="r2r")
+    d = ConvPlan("helmholtz", n=64, period=3, precision="fp32", io="c2c", kappa=5.0)
+    u = torch.zeros((1, 64, 64), dtype=torch.float32).pin_memory()
+    outs = [torch.empty((1, 64, 64), dtype=p.out_dtype()).pin_memory() for p in (a, a)]
+    for other in (b, c, d):
+        with pytest.raises((ConvError, ValueError)):
+            apply_host_multi([a, other], u, outs=[outs[0], torch.empty((1, 64, 64), dtype=other.out_dtype()).pin_memory()])
+
+
 @pytest.mark.parametrize("name,io", [("log", "r2r"), ("helm20", "r2c")])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_autotuned_plan_matches_oracle(name, io, prec):
@@ -451,18 +466,28 @@ def test_split_plan_time_lines_equal_direct(io, monkeypatch):
     assert np.max(np.abs(masks[0] - masks[1])) <= 1e-13
 
 
-def test_n8192_fp32_compact_matches_the_analytic_potential():
-    """n = 8192, FP32 passes on the compact grid (L = 16384; the plan's FP64 lines of 24576 and
-    16384 split four-step): the log potential of the Laplacian of a Gaussian sum (the setting of
-    Table 7, alpha = 250) is minus the Gaussian sum.  FP32 rounding of 16384-point transforms sets
-    the error, measured against that closed form."""
+def test_n8192_fp32_compact_matches_the_analytic_potential(monkeypatch):
+    """n = 8192, FP32 passes on the compact grid (L = 16384: the compile-time transform at 1024
+    threads, and the runtime stage structure; the plan's FP64 lines of 24576 and 16384 split
+    four-step): the log potential of the Laplacian of a Gaussian sum (the setting of Table 7,
+    alpha = 250) is minus the Gaussian sum.  FP32 rounding of 16384-point transforms sets the
+    error, measured against that closed form; the two stage structures agree to it."""
     n = 8192
     centres = [(0.6, 0.6), (0.5, 0.5), (0.35, 0.6)]
     f = inputs.gaussian_sum_laplacian(n, 250.0, centres)
     ex = -inputs.gaussian_sum(n, 250.0, centres)
-    plan = ConvPlan("log", n=n, period=3, precision="fp32", io="r2r", compact=True, scale=-INV2PI)
-    assert plan.info.transform_len == 16384
-    out = plan.apply(torch.tensor(f, dtype=torch.float32, device="cuda")).cpu().numpy()
-    plan.device_status()
-    err = _relerr(ex, out)
-    assert err <= 2e-5, err
+    ft = torch.tensor(f, dtype=torch.float32, device="cuda")
+    outs = []
+    for fused in ("1", "2"):
+        monkeypatch.setenv("WSCONV_FUSED", fused)
+        plan = ConvPlan("log", n=n, period=3, precision="fp32", io="r2r", compact=True, scale=-INV2PI)
+        assert plan.info.transform_len == 16384
+        assert plan.info.static_len == (16384 if fused == "1" else 0)
+        outs.append(plan.apply(ft).cpu().numpy())
+        plan.device_status()
+        del plan
+        torch.cuda.empty_cache()
+    for out in outs:
+        err = _relerr(ex, out)
+        assert err <= 2e-5, err
+    assert _relerr(outs[1], outs[0]) <= 2e-6

@@ -119,3 +119,20 @@ def test_group_rejects_bad_items():
     assert _create(lib, [p], [u], [out], [2]) == 1            # timing events cannot be captured
     p.timing(False)
     assert _create(lib, [p, q], [u, u64], [out, out64], [0, 1]) == 0  # a zero batch skips its item
+
+
+def test_group_of_empty_items_launches_nothing():
+    """Every item with batch 0: the group holds no graph and a launch is a no-op (outputs untouched)."""
+    lib = N.load()
+    p = ConvPlan("log", n=32, period=3, precision="fp32", io="r2r", batch_max=1, scale=-INV2PI)
+    u = _u(p, 1, 5)
+    out = torch.full_like(u, 7.0)
+    k = 1
+    arr = ctypes.c_void_p * k
+    h = ctypes.c_void_p()
+    assert lib.conv_group_create(k, arr(p.handle.value), arr(u.data_ptr()), None, arr(out.data_ptr()),
+                                 (ctypes.c_int * k)(0), ctypes.byref(h)) == 0
+    assert lib.conv_group_launch(h, None) == 0
+    torch.cuda.synchronize()
+    assert torch.all(out == 7.0)
+    lib.conv_group_destroy(h)

@@ -93,3 +93,15 @@ def test_ls_solve_multi_matches_oracle_per_right_hand_side(mode):
     for s in range(3):
         assert _true_residual(g, M, kappa, m, F[s], X2g[s]) <= 1.05e-10
     assert infos2[0]["iters"] < infos[0]["iters"]
+
+
+def test_ls_solve_multi_with_one_right_hand_side_is_ls_solve():
+    """count = 1 runs the plain solve: bitwise the same solution and residual."""
+    n, kappa = 32, 10.0
+    _, m, f, _ = _oracle(n, kappa, "bump")
+    plan = ConvPlan("helmholtz", n=n, period=3, precision="fp32", io="c2c", kappa=kappa)
+    mt, ft = torch.tensor(m, device="cuda"), torch.tensor(f, device="cuda")
+    x1, i1 = ls_solve(plan, mt, ft, refine=True)
+    X, infos = ls_solve_multi(plan, mt, ft[None].contiguous(), refine=True)
+    assert torch.equal(X[0], x1)
+    assert infos[0]["rel_residual"] == i1["rel_residual"] and infos[0]["iters"] == i1["iters"]
