@@ -679,8 +679,14 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
     int iters = 0, cycles = 0, refinements = 0;
     double res = 0;
     conv_status rc = CONV_OK;
+    // the buffer holding f - L64 x for the current x, when the iteration has just formed it with the
+    // FP64 operator (the final residual below is then that one, not a recomputation)
+    const double2 *last_r = nullptr;
     if (!o.refine || p->prec == CONV_P_FP64) {
         rc = S.gmres(fb, xb, tol * fn, o.max_iters, o.zero_guess != 0, iters, cycles, res);
+        // GMRES ends right after forming b - L z for its final z (its restart check); with the FP64
+        // plan that is the true residual
+        if (p->prec == CONV_P_FP64 && (rc == CONV_OK || rc == CONV_ENOTCONVERGED)) last_r = S.W.r;
     } else {
         // FP64 iterative refinement around an FP32-matvec GMRES
         bool first = o.zero_guess != 0;
@@ -691,6 +697,7 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
                 if (rc != CONV_OK) break;
             }
             first = false;
+            last_r = S.W.d;
             S.norm2(S.W.d);
             k_gmres_init<<<1, 32, 0, st>>>(S.W.st);
             double rn = S.read_scalar(&S.W.st->res);
@@ -713,6 +720,7 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
             conv_status irc = S.gmres(S.W.d, S.W.x64, inner_abs, o.max_iters, true, iters, cycles, inner_res);
             if (irc == CONV_OK || irc == CONV_ENOTCONVERGED) {
                 k_axpy_real<<<S.grid_elem, 256, 0, st>>>(xb, S.W.x64, N);
+                last_r = nullptr;  // x moved on
                 ++refinements;
             }
             if (irc != CONV_OK && irc != CONV_ENOTCONVERGED) {
@@ -728,14 +736,19 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
     // final true residual with the FP64 operator, per right-hand side
     std::vector<double> rel(K, 0.0);
     if (rc == CONV_OK || rc == CONV_ENOTCONVERGED) {
-        conv_status r2 = S.true_residual(fb, xb, S.W.r);
+        conv_status r2 = CONV_OK;
+        const double2 *r = last_r;
+        if (!r) {
+            r2 = S.true_residual(fb, xb, S.W.r);
+            r = S.W.r;
+        }
         if (r2 == CONV_OK) {
             if (K == 1) {
-                S.norm2(S.W.r);
+                S.norm2(r);
                 k_gmres_init<<<1, 32, 0, st>>>(S.W.st);
                 rel[0] = S.read_scalar(&S.W.st->res) / fn;
             } else {
-                for (int k = 0; k < K; ++k) rel[k] = S.norm_of(S.W.r + (size_t)k * NN, NN);  // ||f_s|| = 1
+                for (int k = 0; k < K; ++k) rel[k] = S.norm_of(r + (size_t)k * NN, NN);  // ||f_s|| = 1
             }
         }
     }
