@@ -504,8 +504,10 @@ struct Solver {
 
     // GMRES on L z = b from z (FP64 device vectors) to ||b - L z|| <= tol_abs (Arnoldi estimate,
     // confirmed by the residual of the Krylov operator at restarts).
+    // trust_estimate: return once the Arnoldi residual estimate reaches tol_abs, without forming
+    // b - L z again (the inner solves of the refinement, whose outer FP64 residual checks them)
     conv_status gmres(const double2 *b, double2 *z, double tol_abs, int maxit, bool z_is_zero,
-                      int &iters, int &cycles, double &res_out)
+                      int &iters, int &cycles, double &res_out, bool trust_estimate = false)
     {
         const int ldh = 50;
         while (true) {
@@ -528,6 +530,7 @@ struct Solver {
             k_scale_by_invnorm<<<grid_elem, 256, 0, st>>>(W.r, W.V, &W.st->nrm2, N);
             ++cycles;
             int j = 0;
+            bool reached = false;
             for (; j < restart && iters < maxit; ++j) {
                 conv_status rc = run_iteration(j, ldh);
                 if (rc != CONV_OK) return rc;
@@ -538,12 +541,14 @@ struct Solver {
                 if (!(res == res)) return fail(CONV_ENONFINITE, "GMRES residual is not finite");
                 if (res <= tol_abs) {
                     ++j;
+                    reached = true;
                     break;
                 }
             }
             k_gmres_solve<<<1, 32, 0, st>>>(W.st, j, ldh);
             k_add_combination<<<grid_elem, 256, 0, st>>>(W.V, N, j, W.st->y, z, N);
             WSC_CUDA(cudaGetLastError());
+            if (reached && trust_estimate) return CONV_OK;
         }
     }
 };
@@ -717,7 +722,7 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
             double inner_abs = std::max(o.inner_tol * rn, 0.5 * tol * fn);
             int it_before = iters;
             double inner_res = 0;
-            conv_status irc = S.gmres(S.W.d, S.W.x64, inner_abs, o.max_iters, true, iters, cycles, inner_res);
+            conv_status irc = S.gmres(S.W.d, S.W.x64, inner_abs, o.max_iters, true, iters, cycles, inner_res, true);
             if (irc == CONV_OK || irc == CONV_ENOTCONVERGED) {
                 k_axpy_real<<<S.grid_elem, 256, 0, st>>>(xb, S.W.x64, N);
                 last_r = nullptr;  // x moved on
