@@ -1,0 +1,57 @@
+"""Host-side logic that needs no GPU: the benchmark's traffic record lookup and the input
+generators the multi-right-hand-side solves use."""
+import os
+import shutil
+
+import numpy as np
+
+from conftest import ROOT
+
+
+def test_traffic_record_is_used_only_for_the_kernel_sources_it_was_taken_on(tmp_path, monkeypatch):
+    """bench.py reports a committed ncu traffic figure only while the pass kernels' sources hash to
+    the value recorded beside it; a record for other sources reads as missing."""
+    import bench
+    src = os.path.join(ROOT, "profiles", "kf_r2r_cols_fp32_compact_n4096.txt")
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    shutil.copytree(os.path.join(ROOT, "paper_2107_03958_gb300", "csrc"), root / "paper_2107_03958_gb300" / "csrc")
+    shutil.copy(src, root / "profiles" / "rec.txt")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    text = open(src).read()
+    recorded = float(next(l.split(":", 1)[1] for l in text.splitlines() if l.startswith("traffic_bytes_per_launch")))
+    current = bench.kernel_source_hash()
+    # the copy hashes like the repository's sources
+    (root / "profiles" / "rec.txt").write_text(
+        "\n".join(("kernel_source_hash: " + current) if l.startswith("kernel_source_hash") else l
+                  for l in text.splitlines()))
+    assert bench.recorded_traffic("rec.txt") == recorded
+    # a changed pass-kernel source voids it
+    with open(root / "paper_2107_03958_gb300" / "csrc" / "fft_engine.cuh", "a") as f:
+        f.write("\n// changed\n")
+    assert bench.kernel_source_hash() != current
+    assert bench.recorded_traffic("rec.txt") is None
+    # a host-only source (the LS solver) does not
+    with open(root / "paper_2107_03958_gb300" / "csrc" / "fft_engine.cuh", "w") as f:
+        f.write(open(os.path.join(ROOT, "paper_2107_03958_gb300", "csrc", "fft_engine.cuh")).read())
+    with open(root / "paper_2107_03958_gb300" / "csrc" / "ls.cu", "a") as f:
+        f.write("\n// changed\n")
+    assert bench.kernel_source_hash() == current
+    assert bench.recorded_traffic("rec.txt") == recorded
+    assert bench.recorded_traffic("absent.txt") is None
+
+
+def test_plane_wave_directions():
+    from paper_2107_03958_gb300 import inputs
+    n, kappa = 32, 7.0
+    X1, X2 = inputs.grid(n)
+    w0 = inputs.plane_wave(n, kappa)
+    assert np.allclose(w0, np.exp(1j * kappa * X1))
+    assert np.allclose(inputs.plane_wave(n, kappa, 0.0), w0)
+    w90 = inputs.plane_wave(n, kappa, np.pi / 2)
+    assert np.allclose(w90, np.exp(1j * kappa * X2), atol=1e-12)
+    w = inputs.plane_wave(n, kappa, 0.7)
+    assert np.allclose(np.abs(w), 1.0)
+    # the phase advances by kappa along the unit direction (cos 0.7, sin 0.7)
+    h = 1.0 / n
+    assert np.allclose(w[1:, :] / w[:-1, :], np.exp(1j * kappa * h * np.cos(0.7)))
