@@ -88,13 +88,16 @@ __global__ void k_ghat(int family, double gamma, double kappa, double scale, dou
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
          idx += (long long)gridDim.x * blockDim.x) {
         const int k2 = (int)(idx / h), k1 = (int)(idx - (long long)k2 * h);
+        // ghat depends on |k| only: each entry with k1 >= k2 also fills its mirror [k1][k2]
+        if (k1 < k2) continue;
+        const long long mirror = (long long)k1 * h + k2;
         const double km = hypot((double)k1, (double)k2);
         const double s = 2.0 * M_PI * km / b, z = s * a;
         if (family == CONV_K_LOG) {
             double G;
             if (km == 0.0) G = 0.25 * a * a * (1.0 - 2.0 * log(a));
             else G = -a * log(a) * j1(z) / s + (1.0 - j0(z)) / (s * s);
-            out[idx] = -2.0 * M_PI * scale * G;
+            out[idx] = out[mirror] = -2.0 * M_PI * scale * G;
         } else if (family == CONV_K_POW) {
             double v;
             if (km == 0.0) v = pow(a, 2.0 + gamma) / (2.0 + gamma);
@@ -105,7 +108,7 @@ __global__ void k_ghat(int family, double gamma, double kappa, double scale, dou
                                     j1(z) * lommel_S_large(1.0 + gamma, 0.0, z));
                 v = pow(s, -2.0 - gamma) * I;
             }
-            out[idx] = 2.0 * M_PI * scale * v;
+            out[idx] = out[mirror] = 2.0 * M_PI * scale * v;
         } else {
             const double ka = kappa * a;
             double2 r;
@@ -124,8 +127,8 @@ __global__ void k_ghat(int family, double gamma, double kappa, double scale, dou
                 double d = 0.5 * M_PI / (s * s - kappa * kappa);
                 r = make_double2(-ni * d, nr * d);
             }
-            out[2 * idx] = scale * r.x;
-            out[2 * idx + 1] = scale * r.y;
+            out[2 * idx] = out[2 * mirror] = scale * r.x;
+            out[2 * idx + 1] = out[2 * mirror + 1] = scale * r.y;
         }
     }
 }
