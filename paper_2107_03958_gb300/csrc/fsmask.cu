@@ -34,14 +34,15 @@ namespace wsc {
 
 struct LineGen {
     int mode;             // 0 disk chihat, 1 rect chihat, 2 real quadrant, 3 complex quadrant,
-                          // 4 mirrored n x n table on the L-periodic lattice, 5 strided read
+                          // 4 mirrored n x n table on the L-periodic lattice, 5 strided read,
+                          // 6 strided read of an even line stored for e <= L/2 only
     int L;                // line length
     double b, g[4];       // modes 0, 1
     const double *quad;   // modes 2, 3: quadrant [k2][k1] of a table of period L, h = L/2 + 1 per row
     int h;
     const double2 *src;   // modes 4, 5
     int n;                // mode 4: table side
-    long long sl, se;     // mode 5: src[line * sl + e * se]
+    long long sl, se;     // modes 5, 6: src[line * sl + e * se] (6: e folded to L - e above L/2)
 };
 
 __device__ double2 chihat(int shape, const double *g, double b, int M, int q1, int q2)
@@ -90,6 +91,10 @@ __device__ __forceinline__ double2 line_value(const LineGen &G, int line, int e)
         const int d2 = e < G.n ? e : (e > G.L - G.n ? G.L - e : -1);
         if (d1 < 0 || d2 < 0) return make_double2(0.0, 0.0);
         return G.src[(size_t)d1 * G.n + d2];
+    }
+    case 6: {
+        const int f = e <= G.L / 2 ? e : G.L - e;
+        return G.src[line * G.sl + f * G.se];
     }
     default: return G.src[line * G.sl + e * G.se];
     }
@@ -349,7 +354,11 @@ conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, dou
         for (double2 *q : {t1, w, t2, g2})
             if (q) cudaFreeAsync(q, st);
     };
-    bool ok = cudaMallocAsync(&t1, (size_t)M * n * sizeof(double2), st) == cudaSuccess &&
+    // ghat is even in k2 and w in d1: the lines k2 and M - k2 of the first transform, and e1 and
+    // L - e1 of the third, are the same, so only the first half of each is formed and the next
+    // transform reads the other half folded back (mode 6)
+    const int hM = M / 2 + 1, hL = L / 2 + 1;
+    bool ok = cudaMallocAsync(&t1, (size_t)hM * n * sizeof(double2), st) == cudaSuccess &&
               cudaMallocAsync(&w, (size_t)n * n * sizeof(double2), st) == cudaSuccess &&
               cudaMallocAsync(&t2, n1 * L * sizeof(double2), st) == cudaSuccess &&
               cudaMallocAsync(&g2, n1 * n1 * sizeof(double2), st) == cudaSuccess;
@@ -364,9 +373,9 @@ conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, dou
     G.L = M;
     G.quad = ghat;
     G.h = h;
-    if (rc == CONV_OK) rc = fm.run<true>(G, t1, M, n, n, 1, 1.0, sms, st);
-    // rows d1: along k2, keep d2 < n -> w[d1][d2]
-    G.mode = 5;
+    if (rc == CONV_OK) rc = fm.run<true>(G, t1, hM, n, n, 1, 1.0, sms, st);
+    // rows d1: along k2 (lines k2 > M/2 folded back), keep d2 < n -> w[d1][d2]
+    G.mode = 6;
     G.src = t1;
     G.sl = 1;
     G.se = n;
@@ -376,9 +385,9 @@ conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, dou
     G.L = L;
     G.src = w;
     G.n = n;
-    if (rc == CONV_OK) rc = fl.run<false>(G, t2, L, n + 1, 1, L, 1.0, sms, st);
-    // columns k2 along e1, keep k1 <= n -> g2[k2][k1]
-    G.mode = 5;
+    if (rc == CONV_OK) rc = fl.run<false>(G, t2, hL, n + 1, 1, L, 1.0, sms, st);
+    // columns k2 along e1 (lines e1 > L/2 folded back), keep k1 <= n -> g2[k2][k1]
+    G.mode = 6;
     G.src = t2;
     G.sl = L;
     G.se = 1;
