@@ -561,7 +561,7 @@ def serving_leg(count, seed=5):
             cplx = r["kernel"] == "helmholtz"
             out = torch.empty((n, n), dtype=torch.complex64 if cplx else torch.float32, device="cuda")
             bufs.append((u, out))
-    srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4, compact=True)
+    srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=8, compact=True)
     tickets = [None] * len(reqs)
     t0 = time.perf_counter()
 
@@ -615,7 +615,7 @@ def served_ls_burst(count, seed=5):
         bufs.append((m, f, torch.zeros_like(f)))
     out = {"solves": len(reqs), "sizes": sorted(set(r["n"] for r in reqs))}
     for prec, name in (("fp32", "mixed"), ("fp64", "fp64")):
-        srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=4, compact=True)
+        srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=16, ls_workers=8, compact=True)
         for timed in (False, True):
             for b in bufs:
                 b[2].zero_()
