@@ -37,7 +37,8 @@ typedef enum {
     CONV_ECUDA = 4,           /* a CUDA call or kernel launch failed */
     CONV_ETIMEOUT = 5,        /* a bounded device-side wait gave up */
     CONV_ENOTCONVERGED = 6,   /* GMRES hit its iteration limit */
-    CONV_ENONFINITE = 7       /* NaN/Inf detected */
+    CONV_ENONFINITE = 7,      /* NaN/Inf detected */
+    CONV_ECANCELLED = 8       /* a serving request was cancelled before it ran (srv_cancel) */
 } conv_status;
 
 /* Kernel families (Sec. 2.2).  g(x) = scale * log|x|, scale * |x|^gamma (gamma > -2, 2 gamma an
@@ -154,16 +155,21 @@ conv_status conv_apply_host_multi(int count, const conv_plan_t *plans, const voi
  * memory budget that forbids new allocations, real-time loops where an allocation may block, or
  * host frameworks that own all device memory and pass this library only inputs and outputs.
  * The plan must exist already (conv_plan allocates its tables once); this call uses neither the
- * plan's workspace nor a caller's, but a fixed 32 MiB device array inside the library, which every
- * GPU that loads the library holds until the process exits.
- *   Same arguments and result as conv_apply (workspace and stream aside).
- *   Returns CONV_EINVAL, with a message giving both sizes, when the plan and batch need more than
- *   32 MiB of workspace (conv_workspace_size), or when per-pass timing is enabled on the plan.
- *   The first call on each device looks up the array's device address (cudaGetSymbolAddress); make
- *   that first call before any stream capture.
+ * plan's workspace nor a caller's, but a fixed 32 MiB device array inside the library.  The array
+ * is placed on a device when the first plan is built there (conv_plan looks up its device address
+ * and keeps it in the plan) and stays until the process exits; this call looks nothing up, loads
+ * nothing and allocates nothing.
+ *   Same arguments, argument checks and result as conv_apply (workspace and stream aside); the
+ *   batch is limited by the array's size, not by the plan's batch_max.
+ *   Returns CONV_EINVAL for whatever conv_apply rejects (NULL or aliased pointers, u, out or mask
+ *   not aligned to its element size), with a message giving both sizes when the plan and batch
+ *   need more than 32 MiB of workspace (conv_workspace_size), and when per-pass timing is enabled
+ *   on the plan.  Returns CONV_ECUDA when the array's address could not be looked up at plan
+ *   creation.
  *   All calls share the one array: calls that overlap on the GPU (other streams, other threads)
- *   race and corrupt each other's results; serialise them.  Nothing in the array needs to start at
- *   zero: each call writes every element it later reads. */
+ *   race and corrupt each other's results; serialise them.  The array keeps the last call's
+ *   contents; nothing in it needs to start at zero, since each call writes every element it
+ *   later reads. */
 conv_status conv_apply_noalloc(conv_plan_t plan, const void *u, const void *mask, void *out,
                                int batch, void *stream);
 
@@ -376,6 +382,30 @@ conv_status srv_wait(srv_t server, long long ticket, double timeout_s, srv_resul
 conv_status srv_get_stats(srv_t server, srv_stats *stats);
 /* Stops admitting, finishes what is on the GPU, frees every cached plan. */
 void srv_destroy(srv_t server);
+
+/* Cancel a request that has not been admitted yet (still waiting for memory or a slot, or lost
+ * by an injected CONV_FAULT_DROP).  Its result then reads status CONV_ECANCELLED; srv_wait on the
+ * ticket returns at once and releases it.  CONV_EINVAL for an unknown ticket or a request that
+ * already runs (wait for it instead). */
+conv_status srv_cancel(srv_t server, long long ticket);
+
+/* ------------------------------------------------------------------------------------------
+ * Host-side fault injection (no counterpart in the paper; a test aid for the failure paths).
+ * Nothing here faults, traps or hangs a GPU.  Each call arms `count` occurrences of one fault
+ * (count 0 disarms it); the environment variable CONV_FAULT="alloc:N,wait:N,drop:N" arms the same
+ * when the library loads.
+ *   CONV_FAULT_ALLOC: the next plan builds fail their workspace allocation (CONV_ENOMEM), after
+ *                     the plan's tables were allocated, so the clean-up path runs.
+ *   CONV_FAULT_WAIT:  in the next applies, every pass kernel that prefetches its work items treats
+ *                     its first bounded wait as given up: it records CONV_ETIMEOUT in the plan's
+ *                     status word, waits (bounded) for the copy it issued to land, and leaves.
+ *                     The applies' results are incomplete; conv_device_status reports it.
+ *                     Plans whose passes do not prefetch never wait, so nothing is recorded.
+ *   CONV_FAULT_DROP:  the next srv_submit calls return a ticket but the request is lost before
+ *                     the dispatcher sees it (srv_wait with a limit times out; srv_cancel ends it).
+ * Returns CONV_EINVAL for an unknown kind or a negative count. */
+typedef enum { CONV_FAULT_ALLOC = 1, CONV_FAULT_WAIT = 2, CONV_FAULT_DROP = 3 } conv_fault_kind;
+conv_status conv_fault_inject(int kind, int count);
 
 /* ------------------------------------------------------------------------------------------
  * Roofline denominators measured on the running GPU (no counterpart in the paper):

@@ -105,6 +105,8 @@ PROTOTYPES = {
                                 ctypes.POINTER(SrvResult)]),
     "srv_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SrvStats)]),
     "srv_destroy": (None, [ctypes.c_void_p]),
+    "srv_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
+    "conv_fault_inject": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "conv_apply_host_multi": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                              ctypes.c_void_p]),
@@ -120,7 +122,9 @@ PROTOTYPES = {
 }
 
 STATUS = {0: "CONV_OK", 1: "CONV_EINVAL", 2: "CONV_EUNSUPPORTED", 3: "CONV_ENOMEM", 4: "CONV_ECUDA",
-          5: "CONV_ETIMEOUT", 6: "CONV_ENOTCONVERGED", 7: "CONV_ENONFINITE"}
+          5: "CONV_ETIMEOUT", 6: "CONV_ENOTCONVERGED", 7: "CONV_ENONFINITE", 8: "CONV_ECANCELLED"}
+
+FAULT = {"alloc": 1, "wait": 2, "drop": 3}
 
 
 class ConvError(RuntimeError):

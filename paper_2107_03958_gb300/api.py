@@ -358,6 +358,10 @@ class Server:
                 "iters": res.iters, "rel_residual": res.rel_residual,
                 "latency_s": res.t_done - res.t_submit}
 
+    def cancel(self, ticket):
+        """Cancel a request that has not been admitted yet; its wait then reports CONV_ECANCELLED."""
+        N.check(self._lib.srv_cancel(self._h, int(ticket)))
+
     def stats(self):
         st = N.SrvStats()
         N.check(self._lib.srv_get_stats(self._h, ctypes.byref(st)))
@@ -382,6 +386,12 @@ def measure_peaks(nbytes=1 << 30):
     c, d, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     N.check(lib.conv_measure_peaks(int(nbytes), ctypes.byref(c), ctypes.byref(d), ctypes.byref(s)))
     return {"copy_gbs": c.value, "fp64_tflops": d.value, "fp32_tflops": s.value}
+
+
+def fault_inject(kind, count=1):
+    """Arm `count` host-side injected faults of one kind ('alloc', 'wait' or 'drop'; see
+    conv_fault_inject in wsconv.h); count 0 disarms it."""
+    N.check(N.load().conv_fault_inject(N.FAULT[kind], int(count)))
 
 
 def default_scale(kernel):

@@ -28,6 +28,7 @@ template <typename T> struct PassArgs {
     V alpha;               // pass 3 scale (already times 1/M^2)
     T beta;                // pass 3: out = beta u + alpha (.)
     int *err;              // the plan's device status word (CONV_ETIMEOUT: a bounded wait gave up)
+    int give_up;           // injected fault (CONV_FAULT_WAIT): treat the first bounded wait as given up
     int stage_len;         // fused passes: elements V of each group's staging area (0: none)
     int pf;                // fused passes: this launch prefetches work items into the staging areas
     int vec;               // R2C pass 2: the output pairs may be stored as 16-byte vectors

@@ -43,7 +43,9 @@ template <typename T>
 __device__ __forceinline__ bool await_bulk(const PassArgs<T> &a, unsigned long long *bar, unsigned &par,
                                            bool valid)
 {
-    const bool ok = !valid || mbar_wait(bar, par);
+    // with a.give_up (an injected fault) the wait is not even polled: the CTA abandons its first
+    // item, draining the copy it issued with the ordinary bounded wait
+    const bool ok = !valid || (!a.give_up && mbar_wait(bar, par));
     if (__syncthreads_or(!ok)) {
         abandon(a.err, bar, par, !ok);
         return false;
@@ -681,6 +683,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
     const double sc = 1.0 / ((double)M * (double)M);
     PassArgs<T> a{};
     a.err = p->dev_err;
+    a.give_up = fault_take(CONV_FAULT_WAIT) ? 1 : 0;
     a.mask = reinterpret_cast<const T *>(mask);
     a.ghat = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
     a.u = u;

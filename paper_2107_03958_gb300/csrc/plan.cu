@@ -1,5 +1,6 @@
 // plan.cu -- conv_plan / conv_apply and the rest of the C ABI's host side (Sec. 2.1, eq. (io), (An)).
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -12,6 +13,38 @@
 namespace wsc {
 
 static thread_local std::string g_last_error;
+
+// Armed host-side faults (conv_fault_inject), by kind.
+static std::atomic<int> g_fault[4];
+
+bool fault_take(int kind)
+{
+    if (kind < 1 || kind > 3) return false;
+    int c = g_fault[kind].load();
+    while (c > 0)
+        if (g_fault[kind].compare_exchange_weak(c, c - 1)) return true;
+    return false;
+}
+
+// CONV_FAULT="alloc:N,wait:N,drop:N" arms faults when the library loads.
+[[maybe_unused]] static const bool g_fault_env = [] {
+    const char *v = getenv("CONV_FAULT");
+    if (!v) return false;
+    std::string s(v);
+    size_t i = 0;
+    while (i < s.size()) {
+        size_t j = s.find(',', i);
+        if (j == std::string::npos) j = s.size();
+        const std::string item = s.substr(i, j - i);
+        const size_t c = item.find(':');
+        const std::string k = item.substr(0, c);
+        const int cnt = c == std::string::npos ? 1 : atoi(item.c_str() + c + 1);
+        const int kind = k == "alloc" ? CONV_FAULT_ALLOC : k == "wait" ? CONV_FAULT_WAIT : k == "drop" ? CONV_FAULT_DROP : 0;
+        if (kind && cnt >= 0) g_fault[kind].store(cnt);
+        i = j + 1;
+    }
+    return true;
+}();
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -337,7 +370,9 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
     if (rc == CONV_OK) rc = share ? copy_ghat(p, share) : build_ghat(p);
     if (rc == CONV_OK) {
         p->ws_bytes = spectrum_elems(p) * elem_bytes(p) * (size_t)batch_max;
-        if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) {
+        if (fault_take(CONV_FAULT_ALLOC)) {
+            rc = fail(CONV_ENOMEM, "cudaMalloc of the workspace failed (injected fault)");
+        } else if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(CONV_ENOMEM, "cudaMalloc of the workspace failed");
         }
@@ -347,6 +382,7 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
         if (e != cudaSuccess) rc = cuda_fail(e, "plan setup");
     }
     if (rc == CONV_OK && (flags & CONV_PLAN_AUTOTUNE)) rc = autotune(p);
+    if (rc == CONV_OK) noalloc_lookup(p);
     if (rc != CONV_OK) {
         conv_destroy(p);
         return rc;
@@ -377,6 +413,14 @@ conv_status conv_device_status(conv_plan_t p, void *stream)
                                        "results of the applies since the last check are incomplete");
     }
     if (p->fp64_twin) return conv_device_status(p->fp64_twin, stream);
+    return CONV_OK;
+}
+
+conv_status conv_fault_inject(int kind, int count)
+{
+    if (kind < CONV_FAULT_ALLOC || kind > CONV_FAULT_DROP || count < 0)
+        return fail(CONV_EINVAL, "unknown fault kind or negative count");
+    g_fault[kind].store(count);
     return CONV_OK;
 }
 

@@ -59,6 +59,7 @@ struct Req {
     srv_result res;
     size_t need = 0;     // bytes reserved while admitted (beyond the plan)
     bool done = false;
+    bool admitted = false;  // taken off the pending queue by the dispatcher
     std::shared_ptr<CachedPlan> cp;
 };
 
@@ -295,6 +296,7 @@ static void dispatcher_loop(srv_t s)
             const size_t need = extra + (have ? 0 : plan_bytes_estimate(q->r, s->batch_max, s->plan_flags));
             if (need > s->budget) {  // can never fit
                 it = s->pending.erase(it);
+                q->admitted = true;
                 s->inflight_reqs++;
                 q->need = 0;
                 finish(s, q, fail(CONV_ENOMEM, "request exceeds the serving memory budget"), now_s());
@@ -308,6 +310,7 @@ static void dispatcher_loop(srv_t s)
             int status = CONV_OK;
             auto cp = get_plan(s, q->r, status);
             it = s->pending.erase(it);
+            q->admitted = true;
             s->inflight_reqs++;
             if (!cp) {
                 q->need = 0;
@@ -468,7 +471,8 @@ conv_status srv_submit(srv_t s, const srv_request *r, long long *ticket)
         if (s->stop) return fail(CONV_EINVAL, "server is shutting down");
         q->ticket = s->next_ticket++;
         q->res.t_submit = now_s();
-        s->pending.push_back(q);
+        // an injected CONV_FAULT_DROP loses the request here: it has a ticket but never queues
+        if (!fault_take(CONV_FAULT_DROP)) s->pending.push_back(q);
         s->all[q->ticket] = q;
         s->stats.submitted++;
         *ticket = q->ticket;
@@ -493,6 +497,30 @@ conv_status srv_wait(srv_t s, long long ticket, double timeout_s, srv_result *re
     }
     if (res) *res = q->res;
     s->all.erase(ticket);
+    return CONV_OK;
+}
+
+conv_status srv_cancel(srv_t s, long long ticket)
+{
+    if (!s) return fail(CONV_EINVAL, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) return fail(CONV_EINVAL, "unknown ticket");
+        auto q = it->second;
+        if (q->done) return CONV_OK;
+        if (q->admitted) return fail(CONV_EINVAL, "the request already runs; wait for it");
+        for (auto pit = s->pending.begin(); pit != s->pending.end(); ++pit)
+            if (pit->get() == q.get()) {
+                s->pending.erase(pit);
+                break;
+            }
+        q->admitted = true;
+        q->need = 0;
+        s->inflight_reqs++;  // finish() counts it out again
+        finish(s, q, CONV_ECANCELLED, now_s());
+    }
+    s->cv_done.notify_all();
     return CONV_OK;
 }
 

@@ -124,6 +124,10 @@ struct conv_plan_s {
     struct HostMulti *hostmulti = nullptr;  // conv_apply_host_multi's slots (on its first plan)
     // Krylov workspace of ls_solve (ls.cu), created by the first solve
     wsc::LsCache *ls_cache = nullptr;
+    // device address of conv_apply_noalloc's fixed scratch array (noalloc.cu), looked up when the
+    // plan is built; NULL with the reason in noalloc_error when the lookup failed
+    void *noalloc_scratch = nullptr;
+    std::string noalloc_error;
 };
 
 namespace wsc {
@@ -145,4 +149,6 @@ conv_status conv_plan_twin(const conv_plan_s *p, conv_plan_s **twin);
 size_t spectrum_elems(const conv_plan_s *p);  // complex elements of the workspace per density
 void destroy_hostpipe(conv_plan_s *p);          // host_io.cu (both host pipelines)
 void destroy_ls_cache(conv_plan_s *p);          // ls.cu
+void noalloc_lookup(conv_plan_s *p);
+bool fault_take(int kind);                      // plan.cu: consume one armed injected fault            // noalloc.cu: address of the fixed scratch array
 }  // namespace wsc

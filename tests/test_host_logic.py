@@ -55,3 +55,16 @@ def test_plane_wave_directions():
     # the phase advances by kappa along the unit direction (cos 0.7, sin 0.7)
     h = 1.0 / n
     assert np.allclose(w[1:, :] / w[:-1, :], np.exp(1j * kappa * h * np.cos(0.7)))
+
+
+def test_fault_injection_arguments_are_checked():
+    """conv_fault_inject arms host-side faults only for the known kinds and non-negative counts
+    (the call touches no device)."""
+    from paper_2107_03958_gb300 import _native as N
+    from paper_2107_03958_gb300 import build
+    build.build()
+    lib = N.load()
+    assert lib.conv_fault_inject(99, 1) == 1
+    assert lib.conv_fault_inject(N.FAULT["alloc"], -1) == 1
+    for k in N.FAULT.values():
+        assert lib.conv_fault_inject(k, 0) == 0
