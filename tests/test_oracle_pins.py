@@ -7,6 +7,7 @@ import math
 
 import numpy as np
 import pytest
+import closed_forms
 from conftest import load_golden
 
 import oracle as O
@@ -328,16 +329,7 @@ def test_table7_poisson_ten_gaussians():
 
 
 def _rect_log_potential(X1, X2, s0, s1):
-    """-(1/2pi) int_{[s0,s1]^2} log|x-y| dy from the antiderivative
-    P(X,Y) = 1/2 [XY(log(X^2+Y^2) - 3) + X^2 atan(Y/X) + Y^2 atan(X/Y)] summed over the 4 corners."""
-    def P(X, Y):
-        r2 = X * X + Y * Y
-        L = np.log(np.where(r2 > 0, r2, 1.0))
-        A = np.where(X != 0, X * X * np.arctan(Y / np.where(X != 0, X, 1)), 0.0)
-        B = np.where(Y != 0, Y * Y * np.arctan(X / np.where(Y != 0, Y, 1)), 0.0)
-        return 0.5 * (X * Y * (L - 3) + A + B)
-    v = P(X1 - s0, X2 - s0) - P(X1 - s1, X2 - s0) - P(X1 - s0, X2 - s1) + P(X1 - s1, X2 - s1)
-    return -v / (2 * math.pi)
+    return closed_forms.rect_log_potential(X1, X2, s0, s1)
 
 
 def test_rect_potential_closed_form_brute_force():
@@ -347,6 +339,19 @@ def test_rect_potential_closed_form_brute_force():
                                0.3, 0.7, 0.3, 0.7, epsabs=1e-13)[0]
         cf = float(_rect_log_potential(np.array(x[0]), np.array(x[1]), 0.3, 0.7))
         assert abs(bf - cf) < 1e-9
+    # |x|^-1 over [0.25, 0.75]^2 (config 3's second kernel); the singular integrand is split at
+    # the target so that each piece is a smooth-edged quadrature
+    for x in [(0.41, 0.13), (0.523, 0.471), (0.95, 0.7), (0.25, 0.5)]:
+        bf = 0.0
+        for (a1, b1) in ((0.25, x[0]), (x[0], 0.75)):
+            for (a2, b2) in ((0.25, x[1]), (x[1], 0.75)):
+                lo1, hi1, lo2, hi2 = max(a1, 0.25), min(b1, 0.75), max(a2, 0.25), min(b2, 0.75)
+                if hi1 <= lo1 or hi2 <= lo2:
+                    continue
+                bf += integrate.dblquad(lambda y2, y1: 1.0 / math.hypot(x[0] - y1, x[1] - y2),
+                                        lo1, hi1, lo2, hi2, epsabs=1e-12)[0]
+        cf = float(closed_forms.rect_inv_potential(np.array(x[0]), np.array(x[1]), 0.25, 0.75))
+        assert abs(bf - cf) < 1e-8 * abs(cf), (x, bf, cf)
 
 
 def test_table8_fourier_smoothing_orders():
