@@ -4,10 +4,12 @@ eq. (An)), on one GB300 per rank.
 
 One step = the batch of 16 densities (sums of 1-8 C-infinity bumps, n x n, b = 3) convolved with
 each of log|x|, |x|^-1/2, |x|^-1, |x|^-3/2 and (i/4) H0(20 |x|): 80 convolutions.  The headline is
-the FP32 path at n = 4096; the FP64 path, n = 2048 and the Lippmann-Schwinger solver are reported
-beside it.  Inputs (16 x 4096^2 x 4 B = 1.07 GB) exceed the 129 MB L2, so no flush is needed.
+the FP64 path (the paper's arithmetic) at n = 4096; the FP32 path, n = 2048 and 8192, the
+Lippmann-Schwinger solver and the serving loop are reported beside it, and every timed sweep
+carries its error against the FP64 oracle for density 0 of each kernel (computed after the timed
+region).  Inputs (16 x 4096^2 x 8 B = 2.1 GB) exceed the 129 MB L2, so no flush is needed.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision fp32]
 """
 import argparse
 import hashlib
@@ -23,8 +25,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP32 FMA rate of the GPU from its unit counts and clock: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
-FP32_SM_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP32 and FP64 FMA rates of the GPU from its unit counts and clock (context beside the measured
+# microbenchmark peaks the rooflines divide by): 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz, and
+# GB300's nominal 1.25 TFLOP/s FP64.
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_NOMINAL_TFLOPS = 1.25
 
 METRIC = ("convolutions/s & HBM-roofline % at N=2048²/4096² (FP64 vs mixed); "
           "LS solves/s, p99 latency")
@@ -42,6 +47,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--no-extras", action="store_true", help="headline only (no FP64/n=2048/LS legs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the error of the timed outputs against the oracle")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+                    help="arithmetic of the headline sweep (the other is reported beside it)")
     ap.add_argument("--only", choices=["r2r", "r2r64", "r2c", "c2c"], default=None,
                     help="profiling case: warmup + steps applies of one plan (log kernel R2R FP32, "
                          "R2R FP64, Helmholtz R2C or C2C FP32), no other legs")
@@ -243,10 +252,12 @@ def run_reference(args, ws, rank):
 
 
 def workload_config(args):
+    other = "fp32" if args.precision == "fp64" else "fp64"
     return {"workload": "kernel sweep batched: 16 seeded bump-sum densities x {log, |x|^-0.5, "
                         "|x|^-1, |x|^-1.5, Helmholtz kappa=20}, n=%d, b=3" % args.n,
             "n": args.n, "period_b": 3, "batch": args.batch, "kernels": 5,
-            "convolutions_per_step": 5 * args.batch, "precision": "fp32 (headline), fp64 reported",
+            "convolutions_per_step": 5 * args.batch,
+            "precision": "%s (headline), %s reported beside it" % (args.precision, other),
             "embedding": "compact: weights of eq. (quad_wts) from the period-3 moments, 2n-periodic "
                          "transforms (period-3 transforms reported as fp32_period_b)",
             "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
@@ -292,7 +303,9 @@ def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, compact=
         e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    res = {"ms": ms, "plans": plans, "launches": 3 * len(plans) * steps}
+    # density 0 of the last timed step, per kernel (for the error against the oracle)
+    res = {"ms": ms, "plans": plans, "launches": 3 * len(plans) * steps,
+           "out0": [o[0].cpu().numpy() for o in outs], "u0": u[0].double().cpu().numpy()}
     if timing:
         res["passes"] = [p.timing_read() for p in plans]
         for p in plans:
@@ -300,7 +313,7 @@ def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, compact=
     return res
 
 
-def e2e_leg(n, batch, steps, warmup, compact=True):
+def e2e_leg(n, batch, steps, warmup, compact=True, precision="fp64"):
     """End to end through conv_apply_host_multi (the call that takes HOST buffers): every step
     uploads the batch of densities from pinned host memory once, runs the five plans' passes on
     each chunk and downloads every result into pinned host memory, each plan's result chunk
@@ -309,8 +322,9 @@ def e2e_leg(n, batch, steps, warmup, compact=True):
     import torch
     from paper_2107_03958_gb300 import inputs
     from paper_2107_03958_gb300.api import apply_host_multi
-    plans = make_plans(n, batch, "fp32", compact)
-    u_host = torch.from_numpy(inputs.bump_sums(n, batch)).to(torch.float32).pin_memory()
+    plans = make_plans(n, batch, precision, compact)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u_host = torch.from_numpy(inputs.bump_sums(n, batch)).to(dt).pin_memory()
     outs = [torch.empty((batch, n, n), dtype=p.out_dtype()).pin_memory() for p in plans]
     main = torch.cuda.current_stream()
 
@@ -343,6 +357,32 @@ def r2r_bytes(plan, batch):
     return batch * 2 * h * n * esz + h * h * (esz // 2)
 
 
+def oracle_reference(u0, n):
+    """The FP64 oracle's A_n u0 (eq. (An), full period-3 grid) for each kernel of the sweep."""
+    import oracle as O
+    O.set_threads(os.cpu_count() or 1)
+    M = 3 * n
+    a = O.default_trunc_radius(3.0)
+    refs = []
+    for kern, kw in SWEEP:
+        kind = "helm" if kern == "helmholtz" else kern
+        g = O.ghat_full(kind, M, 3.0, a, **kw)
+        r = O.conv(u0, M, g)
+        refs.append(r if kern == "helmholtz" else r.real)
+        del g
+    return refs
+
+
+def errors_vs_oracle(out0, refs):
+    """Relative L-infinity error (eq. (rel-err)) of density 0 of each kernel against the oracle."""
+    import numpy as np
+    errs = {}
+    for (kern, kw), o, r in zip(SWEEP, out0, refs):
+        name = kern if kern != "pow" else "pow%g" % kw["gamma"]
+        errs[name] = float(np.max(np.abs(o - r)) / np.max(np.abs(r)))
+    return errs
+
+
 def cols_roofline(run, batch, peak_tflops, hbm, peak_source):
     """Column-pass rooflines of the R2R plans of a timed sweep: the ALU view (5 L log2 L flops per
     transform, two transforms per column, h = L/2 + 1 columns per density) and the HBM view
@@ -360,7 +400,42 @@ def cols_roofline(run, batch, peak_tflops, hbm, peak_source):
             "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}}
 
 
-def n8192_leg(steps, stream, hbm):
+def sweep_roofline(run, batch, prec, alu_peak, alu_nominal, hbm, hbm_src):
+    """Roofline of a timed sweep's dominant kernel, the R2R column pass (forward column transform,
+    multiplier, inverse column transform): bound by the SMs' FFT arithmetic in both precisions (its
+    DRAM bytes equal the algorithmic bytes, at a fraction of the copy peak), so reported against
+    the measured FMA rate of the same precision, with the HBM view beside it."""
+    r2r = [(p, t) for p, t in zip(run["plans"], run["passes"]) if p.io == "r2r"]
+    tot = [0.0, 0.0, 0.0]
+    cnt = 0
+    for p, (passes, applies) in r2r:
+        for i in range(3):
+            tot[i] += passes[i]
+        cnt += applies
+    col_ms = tot[1] / cnt
+    plan = r2r[0][0]
+    col_bytes = r2r_bytes(plan, batch)
+    gbs = col_bytes / (col_ms * 1e-3) / 1e9
+    L = plan.info.transform_len
+    col_flops = (L // 2 + 1) * batch * 2 * 5.0 * L * math.log2(L)
+    tf = col_flops / (col_ms * 1e-3) / 1e12
+    tname = "double" if prec == "fp64" else "float"
+    share = [t / sum(tot) for t in tot]
+    return {"bound": "alu", "kernel": "kf_r2r_cols<%s> (column pass, compact embedding, L = 2n = %d)" % (tname, L),
+            "achieved": tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": tf / alu_peak,
+            "peak_source": "measured %s FMA microbenchmark (conv_measure_peaks, this run)" % prec.upper(),
+            "peak_nominal": alu_nominal, "frac_of_nominal": tf / alu_nominal,
+            "flops_model": "5 L log2 L per complex length-L transform, forward and inverse per column, "
+                           "L/2+1 columns per density (the conventional count; the pruned first and "
+                           "last stages do less)",
+            "flops_per_launch": col_flops, "avg_launch_ms": col_ms,
+            "traffic": recorded_traffic("kf_r2r_cols_%s_compact_n%d.txt" % (prec, plan.n)),
+            "algorithmic_bytes_per_launch": col_bytes,
+            "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_source": hbm_src},
+            "pass_share_r2r": {"rows_fwd": share[0], "cols": share[1], "rows_inv": share[2]}}
+
+
+def n8192_leg(steps, stream, hbm, fp32_peak):
     """The largest grid of the discontinuous-density sweep: n = 8192, batch 8, log kernel, FP32 R2R
     on the compact grid (L = 16384, compile-time stages, 1024 threads per line)."""
     import torch
@@ -395,8 +470,9 @@ def n8192_leg(steps, stream, hbm):
     byts = r2r_bytes(plan, B)
     return {"value": B / (ms * 1e-3), "unit": "conv/s", "batch": B, "ms_per_batch": ms, "transform_len": L,
             "plan_build_s": plan_s, "pass_ms": [x / cnt for x in t],
-            "roofline_cols": {"bound": "alu", "achieved": flops / (col_ms * 1e-3) / 1e12, "peak": FP32_SM_PEAK_TFLOPS,
-                              "unit": "TFLOP/s", "frac": flops / (col_ms * 1e-3) / 1e12 / FP32_SM_PEAK_TFLOPS,
+            "roofline_cols": {"bound": "alu", "achieved": flops / (col_ms * 1e-3) / 1e12, "peak": fp32_peak,
+                              "unit": "TFLOP/s", "frac": flops / (col_ms * 1e-3) / 1e12 / fp32_peak,
+                              "peak_source": "measured FP32 FMA microbenchmark (conv_measure_peaks)",
                               "hbm": {"achieved": byts / (col_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                                       "frac": byts / (col_ms * 1e-3) / 1e9 / hbm}}}
 
@@ -661,77 +737,64 @@ def main():
 
     peaks = measure_peaks(1 << 30)
     hbm, hbm_src = hbm_peak()
+    alu_peak = {"fp64": peaks["fp64_tflops"], "fp32": peaks["fp32_tflops"]}
+    alu_nominal = {"fp64": FP64_NOMINAL_TFLOPS, "fp32": FP32_NOMINAL_TFLOPS}
 
-    # headline: FP32 sweep at n, device-resident inputs, per-pass events
+    # headline: the sweep at args.precision, device-resident inputs, per-pass events
+    prec = args.precision
     clocks = ClockSampler(local)
     barrier(ws)
     clocks.start()
-    head = sweep_leg(args.n, args.batch, "fp32", args.steps, args.warmup, stream, timing=True)
+    head = sweep_leg(args.n, args.batch, prec, args.steps, args.warmup, stream, timing=True)
     clk = clocks.stop()
     ms = max_over_ranks(ws, head["ms"])
     convs = 5 * args.batch * args.steps
     value = job_throughput(ws, convs, ms)
+    roofline = sweep_roofline(head, args.batch, prec, alu_peak[prec], alu_nominal[prec], hbm, hbm_src)
+    roofline["live_peaks"] = peaks
+    head.pop("plans")
+    torch.cuda.empty_cache()
 
-    # dominant kernel: the R2R column pass
-    r2r = [(p, t) for p, t in zip(head["plans"], head["passes"]) if p.io == "r2r"]
-    tot = [0.0, 0.0, 0.0]
-    cnt = 0
-    for p, (passes, applies) in r2r:
-        for i in range(3):
-            tot[i] += passes[i]
-        cnt += applies
-    col_ms = tot[1] / cnt
-    col_bytes = r2r_bytes(r2r[0][0], args.batch)
-    achieved = col_bytes / (col_ms * 1e-3) / 1e9
-    share = [t / sum(tot) for t in tot]
-    # The FP32 column pass is bound by CUDA-core FFT arithmetic and shared memory, not HBM (its
-    # DRAM bytes equal the algorithmic bytes at ~20 % of the copy peak): report it against the
-    # FP32 FMA rate of the SMs, with the HBM view beside it.
-    L = r2r[0][0].info.transform_len
-    cols_per_launch = (L // 2 + 1) * args.batch
-    col_flops = cols_per_launch * 2 * 5.0 * L * math.log2(L)
-    achieved_tf = col_flops / (col_ms * 1e-3) / 1e12
-    fp32_peak = FP32_SM_PEAK_TFLOPS
-    roofline = {"bound": "alu", "kernel": "kf_r2r_cols<float> (column pass, compact embedding, L = 2n)",
-                "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved_tf / fp32_peak,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz; the live FMA "
-                               "microbenchmark is in live_peaks",
-                "flops_model": "5 L log2 L per complex length-L transform, forward and inverse per column, "
-                               "L/2+1 columns per density (the conventional count; the pruned first and "
-                               "last stages do less)",
-                "flops_per_launch": col_flops, "avg_launch_ms": col_ms,
-                "traffic": recorded_traffic("kf_r2r_cols_fp32_compact_n4096.txt"),
-                "algorithmic_bytes_per_launch": col_bytes,
-                "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                        "peak_source": hbm_src},
-                "pass_share_r2r": {"rows_fwd": share[0], "cols": share[1], "rows_inv": share[2]},
-                "live_peaks": peaks}
-
-    # end to end: pinned host inputs and results through conv_apply_host, copies timed
+    # end to end: pinned host inputs and results through conv_apply_host_multi, copies timed
     e2e_steps = max(3, args.steps // 2)
-    e2e_run = e2e_leg(args.n, args.batch, e2e_steps, max(3, args.warmup))
+    e2e_run = e2e_leg(args.n, args.batch, e2e_steps, max(3, args.warmup), precision=prec)
     e2e_ms = max_over_ranks(ws, e2e_run["ms"])
     e2e = {"value": ws * 5 * args.batch * e2e_steps / (e2e_ms * 1e-3), "unit": "conv/s",
            "h2d_bytes_per_step": e2e_run["h2d"], "d2h_bytes_per_step": e2e_run["d2h"],
            "api": "conv_apply_host_multi (pinned host buffers; one upload per chunk for the five plans)"}
 
-    extras = {}
+    # the other precision's sweep, same workload
+    other = "fp32" if prec == "fp64" else "fp64"
+    k_o = args.steps if other == "fp32" else max(2, args.steps // 4)
+    orun = sweep_leg(args.n, args.batch, other, k_o, min(args.warmup, 3), stream, timing=True)
+    o_ms = max_over_ranks(ws, orun["ms"])
+    o_roof = sweep_roofline(orun, args.batch, other, alu_peak[other], alu_nominal[other], hbm, hbm_src)
+    orun.pop("plans")
+    torch.cuda.empty_cache()
+    o_e2e = e2e_leg(args.n, args.batch, max(3, k_o // 2), 3, precision=other)
+    sibling = {"value": job_throughput(ws, 5 * args.batch * k_o, o_ms), "unit": "conv/s", "dtype": other[:1] + other[2:],
+               "steps": k_o, "ms_per_step": o_ms / k_o,
+               "tolerance_vs_oracle": 2e-6 if other == "fp32" else 1e-12,
+               "roofline": o_roof,
+               "e2e": {"value": ws * 5 * args.batch * max(3, k_o // 2) / (max_over_ranks(ws, o_e2e["ms"]) * 1e-3),
+                       "unit": "conv/s", "h2d_bytes_per_step": o_e2e["h2d"], "d2h_bytes_per_step": o_e2e["d2h"]}}
+
+    # error of density 0 of each kernel of both sweeps against the FP64 oracle (outside every
+    # timed region)
+    err = None
+    if rank == 0 and not args.no_oracle_check:
+        t0 = time.perf_counter()
+        refs = oracle_reference(head["u0"], args.n)
+        err = {"max_rel_linf": errors_vs_oracle(head["out0"], refs),
+               "tolerance": 1e-12 if prec == "fp64" else 2e-6,
+               "sample": "density 0 of the last timed step, each kernel, against the FP64 C oracle's "
+                         "full period-3 FFT convolution (%.0f s)" % (time.perf_counter() - t0)}
+        sibling["err_vs_oracle"] = {"max_rel_linf": errors_vs_oracle(orun["out0"], refs)}
+        del refs
+    del head["out0"], orun["out0"]
+
+    extras = {other: sibling}
     if not args.no_extras:
-        k64 = max(1, args.steps // 5)
-        f64 = sweep_leg(args.n, args.batch, "fp64", k64, 1, stream, timing=True)
-        f64_ms = max_over_ranks(ws, f64["ms"])
-        r64 = [(p, t) for p, t in zip(f64["plans"], f64["passes"]) if p.io == "r2r"]
-        c64 = sum(t[0][1] for _, t in r64) / sum(t[1] for _, t in r64)
-        L64 = r64[0][0].info.transform_len
-        flops = 5 * L64 * math.log2(L64) * 2 * (L64 // 2 + 1) * args.batch
-        extras["fp64"] = {"value": ws * 5 * args.batch * k64 / (f64_ms * 1e-3), "unit": "conv/s",
-                          "ms_per_step": f64_ms / k64, "steps": k64,
-                          "roofline_cols": {"bound": "alu", "achieved": flops / (c64 * 1e-3) / 1e12,
-                                            "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
-                                            "frac": flops / (c64 * 1e-3) / 1e12 / peaks["fp64_tflops"],
-                                            "flops_model": "5 M log2 M per complex length-M FFT, 2 per column",
-                                            "peak_source": "measured FP64 FMA microbenchmark"},
-                          "hbm_frac_cols": r2r_bytes(r64[0][0], args.batch) / (c64 * 1e-3) / 1e9 / hbm}
         kb = max(3, args.steps // 2)
         pb = sweep_leg(args.n, args.batch, "fp32", kb, args.warmup, stream, timing=True, compact=False)
         pb_ms = max_over_ranks(ws, pb["ms"])
@@ -750,8 +813,8 @@ def main():
         l2t = sweep_leg(n2, args.batch, "fp32", 3, 1, stream, timing=True)
         extras["fp32_n%d" % n2] = {"value": ws * 5 * args.batch * args.steps / (l2_ms * 1e-3),
                                    "unit": "conv/s", "ms_per_step": l2_ms / args.steps,
-                                   "roofline_cols": cols_roofline(l2t, args.batch, FP32_SM_PEAK_TFLOPS, hbm,
-                                                                  "FP32 FMA unit count x 2070 MHz")}
+                                   "roofline_cols": cols_roofline(l2t, args.batch, alu_peak["fp32"], hbm,
+                                                                  "measured FP32 FMA microbenchmark")}
         k64b = max(2, args.steps // 3)
         f64b = sweep_leg(n2, args.batch, "fp64", k64b, 1, stream, timing=True)
         f64b_ms = max_over_ranks(ws, f64b["ms"])
@@ -759,7 +822,7 @@ def main():
                                    "ms_per_step": f64b_ms / k64b, "steps": k64b,
                                    "roofline_cols": cols_roofline(f64b, args.batch, peaks["fp64_tflops"], hbm,
                                                                   "measured FP64 FMA microbenchmark")}
-        extras["fp32_n8192"] = n8192_leg(5, stream, hbm)
+        extras["fp32_n8192"] = n8192_leg(5, stream, hbm, alu_peak["fp32"])
         extras["ls"] = ls_leg(512, 40.0, 5, stream)
         extras["ls_larger"] = [ls_leg(1024, 40.0, 3, stream), ls_leg(2048, 40.0, 3, stream)]
         extras["ls_multi_rhs"] = ls_multi_leg(512, 40.0, 8, 3, stream)
@@ -770,9 +833,10 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "conv/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": e2e, "clocks": clk, "gpu_launches": head["launches"]}
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+                "data": "synthetic", "config": workload_config(args), "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": head["launches"],
+                "err_vs_oracle": err}
         line.update(extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
