@@ -12,6 +12,9 @@ Functions and the passage each follows:
   fs_mask                    chi^n_Omega psi, eq. (tfs) and the window psi, Sec. 2.4
   ls_apply / gmres           Nystrom system eq. (descretls), Sec. 3.3
   default_trunc_radius       the admissible truncation radius a of eq. (io), Sec. 2.1
+  bessel_k / yukawa moments  K0, K1 and the Yukawa kernel K0(kappa|x|)/(2 pi) of Sec. 3.2
+  ghat_numeric_full          moments by quadrature after rho = tau^p, eq. (cc_pts)/(cc_wts), Sec. 2.3
+  eta / ghat_localized_full  localization, eq. (io_split), Sec. 2.3
 """
 import ctypes
 import math
@@ -21,8 +24,8 @@ import numpy as np
 
 from . import build as _build
 
-LOG, POW, HELM = 0, 1, 2
-_KIND = {"log": LOG, "pow": POW, "helmholtz": HELM, "helm": HELM}
+LOG, POW, HELM, YUKAWA = 0, 1, 2, 3
+_KIND = {"log": LOG, "pow": POW, "helmholtz": HELM, "helm": HELM, "yukawa": YUKAWA}
 
 _lib = None
 
@@ -57,6 +60,18 @@ def lib():
         L.orc_gmres.argtypes = [i, i, p, d, p, p, p, i, i, d, p, p]
         L.orc_gmres.restype = i
         L.orc_max_threads.restype = i
+        L.orc_bessel_k.argtypes = [i, d]
+        L.orc_bessel_k.restype = d
+        L.orc_yukawa_moment.argtypes = [d, d, d]
+        L.orc_yukawa_moment.restype = d
+        L.orc_cc_rule.argtypes = [i, d, p, p]
+        L.orc_ghat_numeric_full.argtypes = [i, d, d, d, d, d, i, i, i, p]
+        L.orc_ghat_numeric_full.restype = i
+        L.orc_eta.argtypes = [d, d]
+        L.orc_eta.restype = d
+        L.orc_ghat_localized_full.argtypes = [i, d, d, d, d, d, i, d, i, i, p]
+        L.orc_ghat_localized_full.restype = i
+        L.orc_ghat_full_dx1log.argtypes = [d, d, d, i, p]
         L.orc_set_threads.argtypes = [i]
         _lib = L
     return _lib
@@ -126,10 +141,58 @@ def pow_moment(gamma, z):
 
 
 def ghat_full(kind, M, b, a, gamma=0.0, kappa=0.0, scale=1.0):
-    """M x M table of ghat(k), k in F_n, at FFT index q (k = q for q < M/2 else q - M)."""
+    """M x M table of ghat(k), k in F_n, at FFT index q (k = q for q < M/2 else q - M).
+    kind 'dx1log': the non-radial kernel -x1/(2 pi |x|^2) of Sec. 3.1 (odd in k1)."""
     out = np.zeros((M, M), dtype=np.complex128)
+    if kind == "dx1log":
+        lib().orc_ghat_full_dx1log(float(scale), float(b), float(a), int(M), _ptr(out))
+        return out
     lib().orc_ghat_full(_KIND[kind], float(gamma), float(kappa), float(scale), float(b),
                         float(a), int(M), _ptr(out))
+    return out
+
+
+# ---------------------------------------------------------------- moments without a closed form (Sec. 2.3)
+def bessel_k(nu, x):
+    """K_nu(x), nu in {0, 1}, by its integral representation."""
+    return lib().orc_bessel_k(int(nu), float(x))
+
+
+def yukawa_moment(kappa, s, a):
+    """2 pi int_0^a K0(kappa rho)/(2 pi) J0(s rho) rho d rho (closed form), unscaled."""
+    return lib().orc_yukawa_moment(float(kappa), float(s), float(a))
+
+
+def cc_rule(npc, alpha):
+    """Points and weights of eq. (cc_pts), (cc_wts) on [0, alpha]."""
+    x, w = np.zeros(npc), np.zeros(npc)
+    lib().orc_cc_rule(int(npc), float(alpha), _ptr(x), _ptr(w))
+    return x, w
+
+
+def ghat_numeric_full(kind, M, b, a, gamma=0.0, kappa=0.0, scale=1.0, p=4, npc=512):
+    """M x M table of ghat(k) by the quadrature of Sec. 2.3 (rho = tau^p, npc-point rule)."""
+    out = np.zeros((M, M), dtype=np.complex128)
+    rc = lib().orc_ghat_numeric_full(_KIND[kind], float(gamma), float(kappa), float(scale), float(b),
+                                     float(a), int(p), int(npc), int(M), _ptr(out))
+    if rc:
+        raise RuntimeError("orc_ghat_numeric_full failed (%d)" % rc)
+    return out
+
+
+def eta(rho, beta):
+    return lib().orc_eta(float(rho), float(beta))
+
+
+def ghat_localized_full(kind, n, b, a, beta, gamma=0.0, kappa=0.0, scale=1.0, p=4, npc=2048):
+    """M x M multiplier of the localized scheme, eq. (io_split): moments of g eta_beta plus the
+    DFT of the trapezoidal weights of g (1 - eta_beta)."""
+    M = int(round(n * b))
+    out = np.zeros((M, M), dtype=np.complex128)
+    rc = lib().orc_ghat_localized_full(_KIND[kind], float(gamma), float(kappa), float(scale), float(b),
+                                       float(a), int(n), float(beta), int(p), int(npc), _ptr(out))
+    if rc:
+        raise RuntimeError("orc_ghat_localized_full failed (%d)" % rc)
     return out
 
 

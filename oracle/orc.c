@@ -36,7 +36,9 @@ typedef double _Complex cplx;
 #define PI_L 3.141592653589793238462643383279502884L
 static const double PI = 3.14159265358979323846;
 
-enum { ORC_LOG = 0, ORC_POW = 1, ORC_HELM = 2 };
+enum { ORC_LOG = 0, ORC_POW = 1, ORC_HELM = 2, ORC_YUKAWA = 3 };
+
+double orc_yukawa_moment(double kappa, double s, double a); /* orc_moments.c */
 
 /* ------------------------------------------------------------------------------------------
  * Discrete Fourier transform.
@@ -205,6 +207,7 @@ static void gl_init(void)
  *   ORC_POW : g(x) = scale * |x|^gamma.  The closed form printed for (1/2pi)|x|^gamma is scaled
  *             by 2 pi scale.  It equals s^{-2-gamma} I(z) with I(z) = int_0^z t^{1+gamma} J0(t) dt.
  *   ORC_HELM: g(x) = scale * (i/4) H0^(1)(kappa |x|).
+ *   ORC_YUKAWA: g(x) = scale * K0(kappa |x|) / (2 pi) (Sec. 3.2), closed form in orc_moments.c.
  * ------------------------------------------------------------------------------------------ */
 
 /* I(z) = int_0^z t^{1+gamma} J0(t) dt by the power series of J0, term by term (z <= 8). */
@@ -315,6 +318,7 @@ cplx orc_ghat_radial_c(int family, double gamma, double kappa, double scale, dou
         if (kmag == 0.0) return 2.0 * PI * scale * pow(a, 2.0 + gamma) / (2.0 + gamma);
         return 2.0 * PI * scale * pow(s, -2.0 - gamma) * orc_pow_moment(gamma, z);
     }
+    if (family == ORC_YUKAWA) return scale * orc_yukawa_moment(kappa, s, a);
     /* ORC_HELM */
     double ka = kappa * a;
     cplx H0 = j0(ka) + I * y0(ka), H1 = j1(ka) + I * y1(ka);

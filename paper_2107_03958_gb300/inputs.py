@@ -87,6 +87,16 @@ def polynomial_density(n, m):
     return (X1 * (1 - X1) * X2 * (1 - X2)) ** m
 
 
+def polynomial_laplacian(n, m):
+    """Laplacian of (x1(1-x1) x2(1-x2))^m."""
+    X1, X2 = grid(n)
+    P1, P2 = X1 * (1 - X1), X2 * (1 - X2)
+
+    def d2(P, t):
+        return m * (m - 1) * P ** (m - 2) * (1 - 2 * t) ** 2 - 2 * m * P ** (m - 1)
+    return d2(P1, X1) * P2 ** m + P1 ** m * d2(P2, X2)
+
+
 def gaussian_sum(n, alpha, centres):
     X1, X2 = grid(n)
     return sum(np.exp(-alpha * ((X1 - c1) ** 2 + (X2 - c2) ** 2)) for c1, c2 in centres)
@@ -100,6 +110,20 @@ def gaussian_sum_laplacian(n, alpha, centres):
         r2 = (X1 - c1) ** 2 + (X2 - c2) ** 2
         out += (4 * alpha * alpha * r2 - 4 * alpha) * np.exp(-alpha * r2)
     return out
+
+
+def yukawa_source(n, kappa, delta=0.08, centre=(0.5, 0.5)):
+    """f = ((-4 r^2 + 4 delta^2)/delta^4 + kappa^2) exp(-r^2/delta^2), r = |x - centre|: the right-hand
+    side whose solution of -Delta u + kappa^2 u = f is yukawa_solution."""
+    X1, X2 = grid(n)
+    r2 = (X1 - centre[0]) ** 2 + (X2 - centre[1]) ** 2
+    return ((-4.0 * r2 + 4.0 * delta * delta) / delta ** 4 + kappa * kappa) * np.exp(-r2 / (delta * delta))
+
+
+def yukawa_solution(n, delta=0.08, centre=(0.5, 0.5)):
+    """exp(-|x - centre|^2 / delta^2)."""
+    X1, X2 = grid(n)
+    return np.exp(-((X1 - centre[0]) ** 2 + (X2 - centre[1]) ** 2) / (delta * delta))
 
 
 def indicator_rect(n, x0, x1, y0, y1):
@@ -138,6 +162,43 @@ def lippmann_contrast(n, kind="bump"):
     if kind == "disk":
         return 0.5 * indicator_disk(n, (0.5, 0.5), 0.3)
     raise ValueError(kind)
+
+
+def _radius(n, centre=(0.5, 0.5)):
+    X1, X2 = grid(n)
+    return np.hypot(X1 - centre[0], X2 - centre[1])
+
+
+def _half_window(t):
+    """exp(2 e^{-1/t} / (t - 1)) on (0, 1), 1 at t <= 0, 0 at t >= 1 (the half-window that the
+    smooth disc's refractive index is built with)."""
+    t = np.asarray(t, dtype=np.float64)
+    out = np.where(t <= 0.0, 1.0, 0.0)
+    mid = (t > 0.0) & (t < 1.0)
+    tm = t[mid]
+    out[mid] = np.exp(2.0 * np.exp(-1.0 / tm) / (tm - 1.0))
+    return out
+
+
+def smooth_disc_contrast(n, t1=0.45, centre=(0.5, 0.5)):
+    """m = 1 - mu for the disc with smooth refractive index: mu = 2 for r <= t0 = 0.9 t1,
+    1 + varkappa((r - t0)/(t1 - t0)) for t0 < r < t1, 1 beyond (its diameter 2 t1 = 0.9)."""
+    r = _radius(n, centre)
+    t0 = 0.9 * t1
+    mu = np.where(r <= t0, 2.0, np.where(r < t1, 1.0 + _half_window((r - t0) / (t1 - t0)), 1.0))
+    return 1.0 - mu
+
+
+def filter_disc_contrast(n, a=0.5, centre=(0.5, 0.5)):
+    """m = -exp(-(1/2) (2 r / a)^8): the smooth filter disc of diameter a."""
+    r = _radius(n, centre)
+    return -np.exp(-0.5 * (2.0 * r / a) ** 8)
+
+
+def luneburg_contrast(n, a=0.9, centre=(0.5, 0.5)):
+    """m = (2 r / a)^2 - 1 inside the Luneburg lens of diameter a, 0 outside."""
+    r = _radius(n, centre)
+    return np.where(r < 0.5 * a, (2.0 * r / a) ** 2 - 1.0, 0.0)
 
 
 def plane_wave(n, kappa, angle=0.0):
