@@ -7,17 +7,22 @@
 //
 //   log      g = scale log|x|: the closed form printed for -(1/2pi) log|x|, times -2 pi scale.
 //   |x|^gam  g = scale |x|^gamma: 2 pi scale s^{-2-gamma} I(z), I(z) = int_0^z t^{1+gamma} J0(t) dt.
-//            z > 45: I(z) = 2^{1+gamma} Gamma(1+gamma/2)/Gamma(-gamma/2)
-//                           + z (gamma J0(z) S_{gamma,-1}(z) + J1(z) S_{1+gamma,0}(z))
-//            with Lommel's S by its large-z expansion (closed form of Sec. 2.2);
-//            z <= 45: the moment integral directly, rho = a t^2 (the p = 2 substitution of Sec. 2.2,
-//            which makes t^{3 + 2 gamma} a polynomial for 2 gamma integer), composite Gauss-Legendre.
+//            z > 60: I(z) = C - T(z) with C = 2^{1+gamma} Gamma(1+gamma/2)/Gamma(-gamma/2) (the
+//            constant of Sec. 2.2's closed form) and the tail T(z) = int_z^inf t^{1+gamma} J0 dt
+//            expanded by repeated integration by parts (pow_tail below; the same function as the
+//            Lommel-function form printed in Sec. 2.2, derived and summed independently);
+//            z <= 60: the moment integral directly, rho = a t^2 (the p = 2 substitution of Sec. 2.2,
+//            which makes t^{3 + 2 gamma} a polynomial for 2 gamma integer), panel Clenshaw-Curtis.
 //   Helmholtz g = scale (i/4) H0^(1)(kappa |x|): the closed forms of Sec. 2.2, with the k = 0 value
 //            taken with -2/(kappa pi) (the s -> 0 limit of the k != 0 line; the printed sign is
-//            wrong), and direct quadrature when |s - kappa| < 0.05 kappa, where the k != 0 line is a
-//            near 0/0 quotient (its numerator vanishes at s = kappa) and loses digits.  H0 and H1
-//            at the single argument kappa a, and H0 at the quadrature nodes, are tabulated once on
-//            the host (the C library's j0/y0/j1/y1); the device evaluates J0, J1 at z = s a per k.
+//            wrong), and direct quadrature when |s - kappa| < 0.08 kappa, where the k != 0 line is a
+//            near 0/0 quotient (its numerator vanishes at s = kappa) and loses digits.  The band
+//            quadrature uses rho = a u^4 (p = 4: the integrand u^7 H0 J0 is smooth at 0 despite H0's
+//            logarithm) and panel Clenshaw-Curtis; H0 and H1 at the single argument kappa a, and H0
+//            at the quadrature nodes, are tabulated once on the host (the C library's
+//            j0/y0/j1/y1); the device evaluates J0, J1 at z = s a per k.
+// The switch points (z = 60, 8% band) sit beyond where the closed forms lose digits; between
+// them and the oracle's own switch points the two sides evaluate the moments by different methods.
 #include <cmath>
 #include <vector>
 
@@ -25,58 +30,69 @@
 
 namespace wsc {
 
-#define GL_NODES 16
-__constant__ double c_glx[GL_NODES];
-__constant__ double c_glw[GL_NODES];
+// Clenshaw-Curtis rule of CC_N + 1 points on [-1, 1] (cc_rule_host below), for the panel quadratures
+__constant__ double c_ccx[CC_N + 1];
+__constant__ double c_ccw[CC_N + 1];
 
-#define POW_ZQUAD 45.0
-#define HELM_RES_REL 5e-2  // quadrature band |s - kappa| < 5% kappa (the closed form cancels there)
+#define POW_ZTAIL 60.0
+#define HELM_BAND 8e-2  // quadrature band |s - kappa| < 8% kappa (the closed form cancels there)
 
-__device__ double lommel_S_large(double mu, double nu, double z)
+// Tail of the |x|^gamma moment integral, nu = 1 + gamma:
+//   T(z) = int_z^inf t^nu J0(t) dt   (Abel-summed where it does not converge absolutely).
+// With t J0 = (t J1)' and J1 = -J0', two integrations by parts give
+//   A_mu = int_z^inf t^mu J0 = -z^mu J1(z) - (mu - 1) z^{mu-1} J0(z) - (mu - 1)^2 A_{mu-2},
+// so that T(z) = -J1(z) z^nu sum_k c_k - J0(z) z^{nu-1} sum_k c_k (nu - 1 - 2k), with
+// c_0 = 1, c_{k+1} = -c_k (nu - 1 - 2k)^2 / z^2: an asymptotic series, summed up to its smallest
+// term.  Returns I(z) = C - T(z).
+__device__ double pow_tail(double gamma, double z, double C)
 {
-    double sum = 1.0, term = 1.0, prev = 1e300;
-    for (int m = 1; m < 200; ++m) {
-        double f = ((mu - 2.0 * m + 1.0) * (mu - 2.0 * m + 1.0) - nu * nu) / (z * z);
-        term *= -f;
-        if (term == 0.0) break;
-        if (fabs(term) >= prev) break;
-        sum += term;
-        prev = fabs(term);
-        if (fabs(term) < 1e-18 * fabs(sum)) break;
+    const double nu = 1.0 + gamma, iz2 = 1.0 / (z * z);
+    double P = 0.0, Q = 0.0, c = 1.0, last = 1e300;
+    for (int k = 0; k < 200; ++k) {
+        const double qk = c * (nu - 1.0 - 2.0 * k);
+        const double mag = fabs(c) + fabs(qk);
+        if (mag >= last) break;  // the series has started to diverge
+        P += c;
+        Q += qk;
+        last = mag;
+        if (mag < 1e-18 * (fabs(P) + fabs(Q))) break;
+        const double f = nu - 1.0 - 2.0 * k;
+        c *= -f * f * iz2;
     }
-    return pow(z, mu - 1.0) * sum;
+    return C + j1(z) * pow(z, nu) * P + j0(z) * pow(z, nu - 1.0) * Q;
 }
 
-// int_0^a rho^{1+gamma} J0(s rho) d rho = 2 a^{2+gamma} int_0^1 t^{3+2 gamma} J0(z t^2) dt
-__device__ double pow_moment_quad(double gamma, double s, double a)
+// int_0^a rho^{1+gamma} J0(s rho) d rho = 2 a^{2+gamma} int_0^1 t^{3+2 gamma} J0(z t^2) dt, on
+// 4 + ceil(z/2) panels of the Clenshaw-Curtis rule (z <= 60: at most 34 panels).
+__device__ double pow_moment_cc(double gamma, double s, double a)
 {
     const double z = s * a;
-    const int P = 16;
+    const int P = 4 + (int)ceil(0.5 * z);
     const double hw = 0.5 / P;
     double sum = 0.0;
     for (int p = 0; p < P; ++p) {
-        double mid = (p + 0.5) / P;
-        for (int i = 0; i < GL_NODES; ++i) {
-            double t = mid + hw * c_glx[i];
-            sum += c_glw[i] * pow(t, 3.0 + 2.0 * gamma) * j0(z * t * t);
+        const double mid = (p + 0.5) / P;
+        for (int i = 0; i <= CC_N; ++i) {
+            const double t = mid + hw * c_ccx[i];
+            sum += c_ccw[i] * pow(t, 3.0 + 2.0 * gamma) * j0(z * t * t);
         }
     }
     return 2.0 * pow(a, 2.0 + gamma) * hw * sum;
 }
 
-// 2 pi (i/4) int_0^a H0(kappa rho) J0(s rho) rho d rho = i pi a^2 int_0^1 H0(kappa a t^2) J0(s a t^2) t^3 dt
-// by composite Gauss-Legendre.  The nodes' H0(kappa a t^2) do not depend on s; the host tabulates
-// them once per plan (tab: per node t, weight, Re H0, Im H0), so only J0 is evaluated here.
-__device__ double2 helm_moment_quad(const double *__restrict__ tab, int nodes, double s, double a)
+// 2 pi (i/4) int_0^a H0(kappa rho) J0(s rho) rho d rho = i 2 pi a^2 int_0^1 H0(kappa a u^4) J0(s a u^4) u^7 du
+// by panel Clenshaw-Curtis.  The nodes' H0(kappa a u^4) do not depend on s; the host tabulates
+// them once per plan (tab: per node u, weight, Re H0, Im H0), so only J0 is evaluated here.
+__device__ double2 helm_moment_cc(const double *__restrict__ tab, int nodes, double s, double a)
 {
     double sr = 0.0, si = 0.0;
     for (int i = 0; i < nodes; ++i) {
-        const double t = tab[4 * i], t2 = t * t;
-        const double w = tab[4 * i + 1] * j0(s * a * t2) * t2 * t;
+        const double u = tab[4 * i], u4 = u * u * u * u;
+        const double w = tab[4 * i + 1] * j0(s * a * u4) * u4 * u * u * u;
         sr += w * tab[4 * i + 2];
         si += w * tab[4 * i + 3];
     }
-    const double c = M_PI * a * a;
+    const double c = 2.0 * M_PI * a * a;
     return make_double2(-c * si, c * sr);
 }
 
@@ -88,11 +104,17 @@ __global__ void k_ghat(int family, double gamma, double kappa, double scale, dou
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
          idx += (long long)gridDim.x * blockDim.x) {
         const int k2 = (int)(idx / h), k1 = (int)(idx - (long long)k2 * h);
+        const double km = hypot((double)k1, (double)k2);
+        const double s = 2.0 * M_PI * km / b, z = s * a;
+        if (family == CONV_K_DX1LOG) {
+            // the non-radial kernel: T(|k1|, |k2|) = scale (2 pi |k1| / b)(1 - J0(s a)) / s^2, the
+            // passes multiply by i sgn(k1) T; not symmetric in k1 <-> k2, so no mirror
+            out[idx] = km == 0.0 ? 0.0 : scale * (2.0 * M_PI * k1 / b) * (1.0 - j0(z)) / (s * s);
+            continue;
+        }
         // ghat depends on |k| only: each entry with k1 >= k2 also fills its mirror [k1][k2]
         if (k1 < k2) continue;
         const long long mirror = (long long)k1 * h + k2;
-        const double km = hypot((double)k1, (double)k2);
-        const double s = 2.0 * M_PI * km / b, z = s * a;
         if (family == CONV_K_LOG) {
             double G;
             if (km == 0.0) G = 0.25 * a * a * (1.0 - 2.0 * log(a));
@@ -101,14 +123,17 @@ __global__ void k_ghat(int family, double gamma, double kappa, double scale, dou
         } else if (family == CONV_K_POW) {
             double v;
             if (km == 0.0) v = pow(a, 2.0 + gamma) / (2.0 + gamma);
-            else if (z <= POW_ZQUAD) v = pow_moment_quad(gamma, s, a);
+            else if (z <= POW_ZTAIL) v = pow_moment_cc(gamma, s, a);
             else {
-                double c = pow(2.0, 1.0 + gamma) * tgamma(1.0 + 0.5 * gamma) / tgamma(-0.5 * gamma);
-                double I = c + z * (gamma * j0(z) * lommel_S_large(gamma, -1.0, z) +
-                                    j1(z) * lommel_S_large(1.0 + gamma, 0.0, z));
-                v = pow(s, -2.0 - gamma) * I;
+                const double C = pow(2.0, 1.0 + gamma) * tgamma(1.0 + 0.5 * gamma) / tgamma(-0.5 * gamma);
+                v = pow(s, -2.0 - gamma) * pow_tail(gamma, z, C);
             }
             out[idx] = out[mirror] = 2.0 * M_PI * scale * v;
+        } else if (family == CONV_K_YUKAWA) {
+            // closed form (Sec. 3.2 kernel K0(kappa|x|)/(2 pi)); hka.x, hka.y = K0, K1 at kappa a
+            const double ka = kappa * a;
+            const double v = (1.0 + z * j1(z) * hka.x - ka * j0(z) * hka.y) / (s * s + kappa * kappa);
+            out[idx] = out[mirror] = scale * v;
         } else {
             const double ka = kappa * a;
             double2 r;
@@ -116,8 +141,8 @@ __global__ void k_ghat(int family, double gamma, double kappa, double scale, dou
                 // (pi/(2 kappa)) (i a J1(ka) - a Y1(ka) - 2/(kappa pi))
                 double c = M_PI / (2.0 * kappa);
                 r = make_double2(c * (-a * hka.w - 2.0 / (kappa * M_PI)), c * a * hka.z);
-            } else if (fabs(s - kappa) < HELM_RES_REL * kappa) {
-                r = helm_moment_quad(htab, hnodes, s, a);
+            } else if (fabs(s - kappa) < HELM_BAND * kappa) {
+                r = helm_moment_cc(htab, hnodes, s, a);
             } else {
                 // (i pi/2) (z J1(z) H0(ka) - ka J0(z) H1(ka) - 2i/pi) / (s^2 - kappa^2)
                 double J0z = j0(z), J1z = j1(z);
@@ -140,26 +165,18 @@ __global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out,
         out[i] = (float)in[i];
 }
 
-// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n.
-static void gauss_legendre(int n, double *x, double *w)
+// Clenshaw-Curtis rule on [-1, 1]: nodes x_j = cos(j pi / N), j = 0..N (N even), and the weights
+// that integrate the interpolating Chebyshev polynomial exactly: with int_{-1}^1 T_{2k} = -2/(4k^2-1),
+//   w_j = (c_j / N) (1 - sum_{k=1}^{N/2} beta_k cos(2 k j pi / N) / (4k^2 - 1)),
+// c_j = 1 at the two ends and 2 inside, beta_k = 1 for k = N/2 and 2 below.
+void cc_rule_host(int N, double *x, double *w)
 {
-    for (int i = 0; i < (n + 1) / 2; ++i) {
-        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = 0.0;
-            for (int j = 1; j <= n; ++j) {
-                double p2 = p1;
-                p1 = p0;
-                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
-            }
-            pp = n * (z * p0 - p1) / (z * z - 1.0);
-            double dz = p0 / pp;
-            z -= dz;
-            if (std::fabs(dz) < 1e-16) break;
-        }
-        x[i] = -z;
-        x[n - 1 - i] = z;
-        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    for (int j = 0; j <= N; ++j) {
+        x[j] = std::cos(j * M_PI / N);
+        double acc = 0.0;
+        for (int k = 1; k <= N / 2; ++k)
+            acc += (k == N / 2 ? 1.0 : 2.0) * std::cos(2.0 * k * j * M_PI / N) / (4.0 * k * k - 1.0);
+        w[j] = ((j == 0 || j == N) ? 1.0 : 2.0) / N * (1.0 - acc);
     }
 }
 
@@ -203,11 +220,11 @@ conv_status copy_ghat(conv_plan_s *p, const conv_plan_s *src)
 
 conv_status build_ghat(conv_plan_s *p)
 {
-    double gx[GL_NODES], gw[GL_NODES];
-    gauss_legendre(GL_NODES, gx, gw);
+    double cx[CC_N + 1], cw[CC_N + 1];
+    cc_rule_host(CC_N, cx, cw);
     cudaStream_t st = p->setup_stream;
-    WSC_CUDA(cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, st));
-    WSC_CUDA(cudaMemcpyToSymbolAsync(c_glw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, st));
+    WSC_CUDA(cudaMemcpyToSymbolAsync(c_ccx, cx, sizeof(cx), 0, cudaMemcpyHostToDevice, st));
+    WSC_CUDA(cudaMemcpyToSymbolAsync(c_ccw, cw, sizeof(cw), 0, cudaMemcpyHostToDevice, st));
     const int hb = p->Mb / 2 + 1;
     const long long N = (long long)hb * hb;
     const int comps = p->complex_ghat ? 2 : 1;
@@ -221,34 +238,47 @@ conv_status build_ghat(conv_plan_s *p)
     double4 hka = make_double4(0, 0, 0, 0);
     double *htab = nullptr;
     int hnodes = 0;
-    if (p->kern.family == CONV_K_HELMHOLTZ) {
+    const bool closed = p->moments.method == CONV_MOMENTS_CLOSED;
+    if (closed && p->kern.family == CONV_K_YUKAWA) {
+        double k0 = 0.0, k1 = 0.0;
+        bessel_k01_host(p->kern.kappa * p->a, &k0, &k1);
+        hka = make_double4(k0, k1, 0.0, 0.0);
+    }
+    if (closed && p->kern.family == CONV_K_HELMHOLTZ) {
         const double kappa = p->kern.kappa, a = p->a, ka = kappa * a;
         hka = make_double4(::j0(ka), ::y0(ka), ::j1(ka), ::y1(ka));
-        // panels of t-width 1/P with (kappa + s) a / P <= 3 for s up to the band's top
-        const int P = std::max(32, (int)std::ceil((2.0 + HELM_RES_REL) * kappa * a / 3.0));
-        std::vector<double> tab(4 * (size_t)P * GL_NODES);
+        // panels in u = (rho/a)^{1/4}: 8 + ceil(1.5 (kappa + s) a) for s up to the band's top, each
+        // holding about two thirds of an oscillation of H0(kappa a u^4) J0(s a u^4) at u = 1
+        const int P = 8 + (int)std::ceil(1.5 * (2.0 + HELM_BAND) * kappa * a);
+        std::vector<double> tab(4 * (size_t)P * (CC_N + 1));
         const double hw = 0.5 / P;
         for (int q = 0; q < P; ++q)
-            for (int i = 0; i < GL_NODES; ++i) {
-                const double t = (q + 0.5) / P + hw * gx[i], arg = ka * t * t;
-                double *e = &tab[4 * ((size_t)q * GL_NODES + i)];
-                e[0] = t;
-                e[1] = hw * gw[i];
-                e[2] = ::j0(arg);
-                e[3] = ::y0(arg);
+            for (int i = 0; i <= CC_N; ++i) {
+                const double u = (q + 0.5) / P + hw * cx[i], arg = ka * u * u * u * u;
+                double *e = &tab[4 * ((size_t)q * (CC_N + 1) + i)];
+                e[0] = u;
+                e[1] = hw * cw[i];
+                // the integrand's limit at u = 0 is 0 (u^7 log u); H0 itself is infinite there
+                e[2] = arg > 0.0 ? ::j0(arg) : 0.0;
+                e[3] = arg > 0.0 ? ::y0(arg) : 0.0;
             }
-        hnodes = P * GL_NODES;
+        hnodes = P * (CC_N + 1);
         if (cudaMallocAsync(&htab, tab.size() * sizeof(double), st) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the Helmholtz quadrature table failed");
         }
         WSC_CUDA(cudaMemcpyAsync(htab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     }
-    int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
-    k_ghat<<<blocks, 256, 0, st>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, hb,
-                                   p->ghat_paper, hka, htab, hnodes);
-    if (htab) cudaFreeAsync(htab, st);  // in stream order, after the kernel that reads it
-    WSC_CUDA(cudaGetLastError());
+    if (closed) {
+        int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
+        k_ghat<<<blocks, 256, 0, st>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, hb,
+                                       p->ghat_paper, hka, htab, hnodes);
+        if (htab) cudaFreeAsync(htab, st);  // in stream order, after the kernel that reads it
+        WSC_CUDA(cudaGetLastError());
+    } else {
+        conv_status rc = build_moments_numeric(p, scale, p->ghat_paper, st);
+        if (rc != CONV_OK) return rc;
+    }
     // the passes' multiplier: the moments themselves, or the compact-embedding table built from them
     if (p->compact) {
         const size_t nq = (size_t)(p->n + 1) * (p->n + 1) * comps;
