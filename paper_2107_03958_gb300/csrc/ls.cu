@@ -21,6 +21,7 @@ namespace wsc {
 
 #define LS_RED_BLOCKS 296  // 2 x 148..152 SMs: fixed partition for deterministic reductions
 #define LS_RED_THREADS 256
+#define LS_MAX_RESTART 1000  // Krylov basis (restart + 1) n^2 complex values; Hessenberg (restart + 1) restart
 
 // Dot products of NV basis vectors V_i0 ... V_i0+NV-1 with w over this block's slice [lo, hi):
 // one sweep that reads w once for the NV of them.  Each thread issues the loads of four elements
@@ -122,7 +123,7 @@ __global__ void k_finalize_dots(const double2 *__restrict__ partial, int nb, int
 __global__ void k_sub_combination(const double2 *__restrict__ V, size_t ldv, int cnt,
                                   const double2 *__restrict__ h, double2 *__restrict__ w, long long N)
 {
-    __shared__ double2 hs[64];
+    extern __shared__ double2 hs[];  // cnt coefficients
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = h[i];
     __syncthreads();
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
@@ -153,7 +154,7 @@ __global__ void k_sub_combination(const double2 *__restrict__ V, size_t ldv, int
 __global__ void k_add_combination(const double2 *__restrict__ V, size_t ldv, int cnt,
                                   const double2 *__restrict__ y, double2 *__restrict__ x, long long N)
 {
-    __shared__ double2 ys[64];
+    extern __shared__ double2 ys[];  // cnt coefficients
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) ys[i] = y[i];
     __syncthreads();
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
@@ -229,73 +230,93 @@ __global__ void k_f2d(const float *__restrict__ in, double *__restrict__ out, lo
         out[t] = (double)in[t];
 }
 
-// Small dense state of one GMRES cycle, device resident.
+// Small dense state of one GMRES cycle with restart R, device resident in one allocation of
+// gmres_state_elems(R) complex values; the struct itself (its pointers into that allocation) is
+// passed to the kernels by value.
 struct GmresState {
-    double2 H[51 * 50];  // H[i * 50 + j], i <= j + 1 (rotated in place)
-    double2 cs[50], sn[50];
-    double2 e[51];
-    double2 y[50];
-    double2 hcol[51];    // h of the current column (CGS accumulations)
-    double2 nrm2;        // squared norm scratch
-    double res;          // |e[j+1]|
+    double2 *H;     // (R+1) x R, H[i * R + j], i <= j + 1 (rotated in place)
+    double2 *cs, *sn;  // R rotations
+    double2 *e;     // R + 1
+    double2 *y;     // R
+    double2 *hcol;  // R + 1: h of the current column (CGS accumulations)
+    double2 *nrm2;  // squared norm scratch (x component)
+    double *res;    // |e[j+1]|
+    int R;
 };
 
+static size_t gmres_state_elems(int R) { return (size_t)(R + 1) * R + 2 * (size_t)R + (R + 1) + R + (R + 1) + 2; }
+
+static GmresState gmres_state_view(double2 *base, int R)
+{
+    GmresState g;
+    g.R = R;
+    g.H = base;
+    g.cs = g.H + (size_t)(R + 1) * R;
+    g.sn = g.cs + R;
+    g.e = g.sn + R;
+    g.y = g.e + (R + 1);
+    g.hcol = g.y + R;
+    g.nrm2 = g.hcol + (R + 1);
+    g.res = reinterpret_cast<double *>(g.nrm2 + 1);
+    return g;
+}
+
 // e = [beta, 0, ...]; beta from the squared norm in st->nrm2
-__global__ void k_gmres_init(GmresState *st)
+__global__ void k_gmres_init(GmresState st)
 {
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 51; ++i) st->e[i] = make_double2(0, 0);
-        st->e[0] = make_double2(sqrt(st->nrm2.x), 0);
-        st->res = sqrt(st->nrm2.x);
+        for (int i = 0; i <= st.R; ++i) st.e[i] = make_double2(0, 0);
+        st.e[0] = make_double2(sqrt(st.nrm2->x), 0);
+        *st.res = sqrt(st.nrm2->x);
     }
 }
 
 // Column j of H from hcol (j+1 entries) and the new norm; apply the previous rotations, form
 // rotation j, update e and the residual estimate.
-__global__ void k_gmres_givens(GmresState *st, int j, int ldh)
+__global__ void k_gmres_givens(GmresState st, int j, int ldh)
 {
     if (threadIdx.x != 0) return;
-    for (int i = 0; i <= j; ++i) st->H[i * ldh + j] = st->hcol[i];
-    double hn = sqrt(st->nrm2.x);
-    st->H[(j + 1) * ldh + j] = make_double2(hn, 0);
+    for (int i = 0; i <= j; ++i) st.H[i * ldh + j] = st.hcol[i];
+    double hn = sqrt(st.nrm2->x);
+    st.H[(j + 1) * ldh + j] = make_double2(hn, 0);
     for (int i = 0; i < j; ++i) {
-        double2 h0 = st->H[i * ldh + j], h1 = st->H[(i + 1) * ldh + j], c = st->cs[i], s = st->sn[i];
+        double2 h0 = st.H[i * ldh + j], h1 = st.H[(i + 1) * ldh + j], c = st.cs[i], s = st.sn[i];
         // [h0; h1] <- [conj(c) h0 + conj(s) h1; -s h0 + c h1]
         double2 a = make_double2(c.x * h0.x + c.y * h0.y + s.x * h1.x + s.y * h1.y,
                                  c.x * h0.y - c.y * h0.x + s.x * h1.y - s.y * h1.x);
         double2 b = make_double2(-(s.x * h0.x - s.y * h0.y) + (c.x * h1.x - c.y * h1.y),
                                  -(s.x * h0.y + s.y * h0.x) + (c.x * h1.y + c.y * h1.x));
-        st->H[i * ldh + j] = a;
-        st->H[(i + 1) * ldh + j] = b;
+        st.H[i * ldh + j] = a;
+        st.H[(i + 1) * ldh + j] = b;
     }
-    double2 h0 = st->H[j * ldh + j], h1 = st->H[(j + 1) * ldh + j];
+    double2 h0 = st.H[j * ldh + j], h1 = st.H[(j + 1) * ldh + j];
     double r = sqrt(h0.x * h0.x + h0.y * h0.y + h1.x * h1.x + h1.y * h1.y);
     double2 c = r > 0 ? make_double2(h0.x / r, h0.y / r) : make_double2(1, 0);
     double2 s = r > 0 ? make_double2(h1.x / r, h1.y / r) : make_double2(0, 0);
-    st->cs[j] = c;
-    st->sn[j] = s;
-    st->H[j * ldh + j] = make_double2(r, 0);
-    st->H[(j + 1) * ldh + j] = make_double2(0, 0);
-    double2 ej = st->e[j];
-    st->e[j + 1] = make_double2(-(s.x * ej.x - s.y * ej.y), -(s.x * ej.y + s.y * ej.x));
-    st->e[j] = make_double2(c.x * ej.x + c.y * ej.y, c.x * ej.y - c.y * ej.x);
-    st->res = sqrt(st->e[j + 1].x * st->e[j + 1].x + st->e[j + 1].y * st->e[j + 1].y);
+    st.cs[j] = c;
+    st.sn[j] = s;
+    st.H[j * ldh + j] = make_double2(r, 0);
+    st.H[(j + 1) * ldh + j] = make_double2(0, 0);
+    double2 ej = st.e[j];
+    st.e[j + 1] = make_double2(-(s.x * ej.x - s.y * ej.y), -(s.x * ej.y + s.y * ej.x));
+    st.e[j] = make_double2(c.x * ej.x + c.y * ej.y, c.x * ej.y - c.y * ej.x);
+    *st.res = sqrt(st.e[j + 1].x * st.e[j + 1].x + st.e[j + 1].y * st.e[j + 1].y);
 }
 
 // back substitution H(0:k, 0:k) y = e(0:k)
-__global__ void k_gmres_solve(GmresState *st, int k, int ldh)
+__global__ void k_gmres_solve(GmresState st, int k, int ldh)
 {
     if (threadIdx.x != 0) return;
     for (int i = k - 1; i >= 0; --i) {
-        double2 acc = st->e[i];
+        double2 acc = st.e[i];
         for (int t = i + 1; t < k; ++t) {
-            double2 h = st->H[i * ldh + t], yt = st->y[t];
+            double2 h = st.H[i * ldh + t], yt = st.y[t];
             acc.x -= h.x * yt.x - h.y * yt.y;
             acc.y -= h.x * yt.y + h.y * yt.x;
         }
-        double2 d = st->H[i * ldh + i];
+        double2 d = st.H[i * ldh + i];
         double dd = d.x * d.x + d.y * d.y;
-        st->y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+        st.y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
     }
 }
 
@@ -305,7 +326,8 @@ struct LsWork {
     float2 *v32 = nullptr, *w32 = nullptr;
     float *m32 = nullptr;
     double2 *partial = nullptr;
-    GmresState *st = nullptr;
+    double2 *gsbuf = nullptr;  // the GMRES state's allocation
+    GmresState gs{};
     double *host_res = nullptr;  // pinned
     // several right-hand sides: their normalised copies, and the matvecs' spectrum workspaces
     // when the batch exceeds the plans' own
@@ -322,8 +344,8 @@ static bool alloc_work(LsWork &W, long long N, long long NN, int batch, size_t c
               cudaMalloc(&W.w, N * sizeof(double2)) == cudaSuccess &&
               cudaMalloc(&W.r, N * sizeof(double2)) == cudaSuccess &&
               cudaMalloc(&W.d, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&W.partial, (size_t)51 * LS_RED_BLOCKS * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&W.st, sizeof(GmresState)) == cudaSuccess &&
+              cudaMalloc(&W.partial, (size_t)(restart + 1) * LS_RED_BLOCKS * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&W.gsbuf, gmres_state_elems(restart) * sizeof(double2)) == cudaSuccess &&
               cudaMallocHost(&W.host_res, sizeof(double)) == cudaSuccess;
     if (ok && mixed)
         ok = cudaMalloc(&W.x64, N * sizeof(double2)) == cudaSuccess &&
@@ -334,6 +356,7 @@ static bool alloc_work(LsWork &W, long long N, long long NN, int batch, size_t c
     if (ok && cws) ok = cudaMalloc(&W.cws, cws) == cudaSuccess;
     if (ok && cws64) ok = cudaMalloc(&W.cws64, cws64) == cudaSuccess;
     if (!ok) cudaGetLastError();
+    if (ok) W.gs = gmres_state_view(W.gsbuf, restart);
     return ok;
 }
 
@@ -351,7 +374,7 @@ static void free_work(LsWork &W)
     cudaFree(W.cws);
     cudaFree(W.cws64);
     cudaFree(W.partial);
-    cudaFree(W.st);
+    cudaFree(W.gsbuf);
     if (W.host_res) cudaFreeHost(W.host_res);
     W = LsWork();
 }
@@ -429,15 +452,15 @@ struct Solver {
     void norm2(const double2 *v, long long len = -1)
     {
         k_multidot<<<LS_RED_BLOCKS, LS_RED_THREADS, 0, st>>>(v, 0, 1, v, len < 0 ? N : len, W.partial);
-        k_finalize_dots<<<1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, 1, &W.st->nrm2, 0);
+        k_finalize_dots<<<1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, 1, W.gs.nrm2, 0);
     }
 
     // ||v|| of len elements, waited for
     double norm_of(const double2 *v, long long len)
     {
         norm2(v, len);
-        k_gmres_init<<<1, 32, 0, st>>>(W.st);
-        return read_scalar(&W.st->res);
+        k_gmres_init<<<1, 32, 0, st>>>(W.gs);
+        return read_scalar(W.gs.res);
     }
 
     double read_scalar(const double *dptr)
@@ -457,15 +480,15 @@ struct Solver {
         // CGS with one re-orthogonalisation: h = V^H w; w -= V h; h2 = V^H w; w -= V h2
         for (int pass = 0; pass < 2; ++pass) {
             k_multidot<<<LS_RED_BLOCKS, LS_RED_THREADS, 0, st>>>(W.V, N, j + 1, W.w, N, W.partial);
-            k_finalize_dots<<<j + 1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, j + 1, W.st->hcol + 0, pass);
+            k_finalize_dots<<<j + 1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, j + 1, W.gs.hcol, pass);
             // subtract with this pass's coefficients only: recompute them into y scratch
-            k_finalize_dots<<<j + 1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, j + 1, W.st->y, 0);
-            k_sub_combination<<<grid_elem, 256, 0, st>>>(W.V, N, j + 1, W.st->y, W.w, N);
+            k_finalize_dots<<<j + 1, 32, 0, st>>>(W.partial, LS_RED_BLOCKS, j + 1, W.gs.y, 0);
+            k_sub_combination<<<grid_elem, 256, (j + 1) * sizeof(double2), st>>>(W.V, N, j + 1, W.gs.y, W.w, N);
         }
         norm2(W.w);
-        k_scale_by_invnorm<<<grid_elem, 256, 0, st>>>(W.w, vn, &W.st->nrm2, N);
-        k_gmres_givens<<<1, 32, 0, st>>>(W.st, j, ldh);
-        WSC_CUDA(cudaMemcpyAsync(W.host_res, &W.st->res, sizeof(double), cudaMemcpyDeviceToHost, st));
+        k_scale_by_invnorm<<<grid_elem, 256, 0, st>>>(W.w, vn, W.gs.nrm2, N);
+        k_gmres_givens<<<1, 32, 0, st>>>(W.gs, j, ldh);
+        WSC_CUDA(cudaMemcpyAsync(W.host_res, W.gs.res, sizeof(double), cudaMemcpyDeviceToHost, st));
         return CONV_OK;
     }
 
@@ -509,7 +532,7 @@ struct Solver {
     conv_status gmres(const double2 *b, double2 *z, double tol_abs, int maxit, bool z_is_zero,
                       int &iters, int &cycles, double &res_out, bool trust_estimate = false)
     {
-        const int ldh = 50;
+        const int ldh = W.gs.R;  // the state's allocation, which the cached step graphs were captured with
         while (true) {
             // r = b - L z
             if (z_is_zero) {
@@ -521,13 +544,13 @@ struct Solver {
             }
             z_is_zero = false;
             norm2(W.r);
-            k_gmres_init<<<1, 32, 0, st>>>(W.st);
-            double beta = read_scalar(&W.st->res);
+            k_gmres_init<<<1, 32, 0, st>>>(W.gs);
+            double beta = read_scalar(W.gs.res);
             res_out = beta;
             if (!(beta == beta)) return fail(CONV_ENONFINITE, "GMRES residual is not finite");
             if (beta <= tol_abs) return CONV_OK;
             if (iters >= maxit) return fail(CONV_ENOTCONVERGED, "GMRES reached its iteration limit");
-            k_scale_by_invnorm<<<grid_elem, 256, 0, st>>>(W.r, W.V, &W.st->nrm2, N);
+            k_scale_by_invnorm<<<grid_elem, 256, 0, st>>>(W.r, W.V, W.gs.nrm2, N);
             ++cycles;
             int j = 0;
             bool reached = false;
@@ -545,8 +568,8 @@ struct Solver {
                     break;
                 }
             }
-            k_gmres_solve<<<1, 32, 0, st>>>(W.st, j, ldh);
-            k_add_combination<<<grid_elem, 256, 0, st>>>(W.V, N, j, W.st->y, z, N);
+            k_gmres_solve<<<1, 32, 0, st>>>(W.gs, j, ldh);
+            k_add_combination<<<grid_elem, 256, std::max(j, 1) * sizeof(double2), st>>>(W.V, N, j, W.gs.y, z, N);
             WSC_CUDA(cudaGetLastError());
             if (reached && trust_estimate) return CONV_OK;
         }
@@ -571,7 +594,8 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
         return fail(CONV_EINVAL, "ls_solve needs a C2C Helmholtz plan");
     ls_opts o = {50, 2000, 1e-10, 0, 1e-5, 1};
     if (opts_in) o = *opts_in;
-    if (o.restart < 1 || o.restart > 50) return fail(CONV_EINVAL, "restart must be in [1, 50]");
+    if (o.restart < 1 || o.restart > LS_MAX_RESTART)
+        return fail(CONV_EINVAL, "restart must be in [1, " + std::to_string(LS_MAX_RESTART) + "]");
     if (o.max_iters < 1) return fail(CONV_EINVAL, "max_iters must be >= 1");
     if (!(o.tol > 0)) return fail(CONV_EINVAL, "tol must be > 0");
     if (o.refine && !(o.inner_tol > 0 && o.inner_tol < 1)) return fail(CONV_EINVAL, "inner_tol must be in (0, 1)");
@@ -677,8 +701,8 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
         tol = o.tol / std::sqrt((double)K);
     }
     S.norm2(fb);
-    k_gmres_init<<<1, 32, 0, st>>>(S.W.st);
-    double fn = S.read_scalar(&S.W.st->res);
+    k_gmres_init<<<1, 32, 0, st>>>(S.W.gs);
+    double fn = S.read_scalar(S.W.gs.res);
     if (!(fn > 0)) fn = 1.0;
 
     int iters = 0, cycles = 0, refinements = 0;
@@ -704,8 +728,8 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
             first = false;
             last_r = S.W.d;
             S.norm2(S.W.d);
-            k_gmres_init<<<1, 32, 0, st>>>(S.W.st);
-            double rn = S.read_scalar(&S.W.st->res);
+            k_gmres_init<<<1, 32, 0, st>>>(S.W.gs);
+            double rn = S.read_scalar(S.W.gs.res);
             res = rn;
             if (!(rn == rn)) {
                 rc = fail(CONV_ENONFINITE, "residual is not finite");
@@ -750,8 +774,8 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
         if (r2 == CONV_OK) {
             if (K == 1) {
                 S.norm2(r);
-                k_gmres_init<<<1, 32, 0, st>>>(S.W.st);
-                rel[0] = S.read_scalar(&S.W.st->res) / fn;
+                k_gmres_init<<<1, 32, 0, st>>>(S.W.gs);
+                rel[0] = S.read_scalar(S.W.gs.res) / fn;
             } else {
                 for (int k = 0; k < K; ++k) rel[k] = S.norm_of(r + (size_t)k * NN, NN);  // ||f_s|| = 1
             }
