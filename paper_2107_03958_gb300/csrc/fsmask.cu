@@ -43,6 +43,10 @@ struct LineGen {
     const double2 *src;   // modes 4, 5
     int n;                // mode 4: table side
     long long sl, se;     // modes 5, 6: src[line * sl + e * se] (6: e folded to L - e above L/2)
+    int nvalid;           // mode 5: elements e >= nvalid read as zero (0: all valid)
+    const void *dens;     // mode 7: density rows (line j1, element e < n), zero beyond n
+    int dens_kind;        // mode 7: 0 FP32 real, 1 FP64 real, 2 FP32 complex, 3 FP64 complex
+    const void *dmask;    // mode 7: optional n x n multiplier (FP32 for kinds 0, 2; FP64 otherwise)
 };
 
 __device__ double2 chihat(int shape, const double *g, double b, int M, int q1, int q2)
@@ -96,7 +100,28 @@ __device__ __forceinline__ double2 line_value(const LineGen &G, int line, int e)
         const int f = e <= G.L / 2 ? e : G.L - e;
         return G.src[line * G.sl + f * G.se];
     }
-    default: return G.src[line * G.sl + e * G.se];
+    case 7: {
+        if (e >= G.n) return make_double2(0.0, 0.0);
+        const size_t i = (size_t)line * G.n + e;
+        const bool f32 = (G.dens_kind & 1) == 0;
+        double m = 1.0;
+        if (G.dmask) m = f32 ? (double)reinterpret_cast<const float *>(G.dmask)[i] : reinterpret_cast<const double *>(G.dmask)[i];
+        switch (G.dens_kind) {
+        case 0: return make_double2(m * reinterpret_cast<const float *>(G.dens)[i], 0.0);
+        case 1: return make_double2(m * reinterpret_cast<const double *>(G.dens)[i], 0.0);
+        case 2: {
+            const float2 v = reinterpret_cast<const float2 *>(G.dens)[i];
+            return make_double2(m * v.x, m * v.y);
+        }
+        default: {
+            const double2 v = reinterpret_cast<const double2 *>(G.dens)[i];
+            return make_double2(m * v.x, m * v.y);
+        }
+        }
+    }
+    default:
+        if (G.nvalid > 0 && e >= G.nvalid) return make_double2(0.0, 0.0);
+        return G.src[line * G.sl + e * G.se];
     }
 }
 
@@ -306,16 +331,18 @@ struct LineFFT {
         WSC_CUDA(cudaFuncSetAttribute(k_lines_split2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         return CONV_OK;
     }
+    // T: NULL (the four-step buffer of nlines x L values is allocated in stream order) or a buffer
+    // of that size the caller owns
     template <bool INV>
     conv_status run(const LineGen &G, double2 *out, int nlines, int keep, long long ol, long long oe, double scale,
-                    int sms, cudaStream_t st) const
+                    int sms, cudaStream_t st, double2 *Tbuf = nullptr) const
     {
         if (!L1) {
             k_lines<INV><<<std::min(nlines, sms * 2), tpt, smem, st>>>(G, out, nlines, keep, ol, oe, scale, dd, tw, tpt);
             return CONV_OK;
         }
-        double2 *T = nullptr;
-        if (cudaMallocAsync(&T, (size_t)nlines * L * sizeof(double2), st) != cudaSuccess) {
+        double2 *T = Tbuf;
+        if (!T && cudaMallocAsync(&T, (size_t)nlines * L * sizeof(double2), st) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "four-step line buffer");
         }
@@ -324,7 +351,7 @@ struct LineFFT {
                                                                                              f1->dd, f1->tw, f1->tpt);
         k_lines_split2<INV><<<(int)std::min<long long>(s2, sms * 2LL), f2->tpt, f2->smem, st>>>(
             T, out, nlines, L1, L2, keep, ol, oe, scale, f2->dd, f2->tw, f2->tpt);
-        WSC_CUDA(cudaFreeAsync(T, st));
+        if (!Tbuf) WSC_CUDA(cudaFreeAsync(T, st));
         return CONV_OK;
     }
 };
@@ -401,6 +428,222 @@ conv_status build_compact_table(const double *ghat, bool cplx, int n, int M, dou
     if (rc != CONV_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "compact-embedding table");
     return CONV_OK;
+}
+
+__global__ void k_add_quadrant(const double2 *__restrict__ t, double *__restrict__ acc, long long N, int cplx,
+                               double scale)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (cplx) {
+            acc[2 * i] += scale * t[i].x;
+            acc[2 * i + 1] += scale * t[i].y;
+        } else {
+            acc[i] += scale * t[i].x;
+        }
+    }
+}
+
+// acc += scale * DFT_{M x M}(table) for a table even in both indices (the localized scheme's
+// smooth-part weights), given by its quadrant [k2][k1], k < h = M/2 + 1, real or complex; the
+// result is even too and is added to the quadrant acc (same layout).  Lines k2 <= M/2 along k1
+// first (the rest are their mirrors), then lines q1 along k2 read folded back.
+conv_status add_even_dft2(const double *quad, bool cplx, int M, double scale, double *acc, cudaStream_t st)
+{
+    const int h = M / 2 + 1, sms = sm_count();
+    LineFFT f;
+    conv_status rc = f.init(M, st);
+    if (rc != CONV_OK) return rc;
+    double2 *t1 = nullptr, *t2 = nullptr;
+    if (cudaMallocAsync(&t1, (size_t)h * h * sizeof(double2), st) != cudaSuccess ||
+        cudaMallocAsync(&t2, (size_t)h * h * sizeof(double2), st) != cudaSuccess) {
+        cudaGetLastError();
+        if (t1) cudaFreeAsync(t1, st);
+        return fail(CONV_ENOMEM, "even 2-D DFT buffers");
+    }
+    LineGen G{};
+    G.mode = cplx ? 3 : 2;
+    G.L = M;
+    G.quad = quad;
+    G.h = h;
+    rc = f.run<false>(G, t1, h, h, h, 1, 1.0, sms, st);  // t1[k2][q1]
+    G.mode = 6;
+    G.src = t1;
+    G.sl = 1;
+    G.se = h;
+    if (rc == CONV_OK) rc = f.run<false>(G, t2, h, h, 1, h, 1.0, sms, st);  // t2[q2][q1]
+    const long long N = (long long)h * h;
+    if (rc == CONV_OK)
+        k_add_quadrant<<<(int)std::min<long long>((N + 255) / 256, sms * 8LL), 256, 0, st>>>(t2, acc, N, cplx ? 1 : 0,
+                                                                                              scale);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(t1, st);
+    cudaFreeAsync(t2, st);
+    if (rc != CONV_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "even 2-D DFT");
+    return CONV_OK;
+}
+
+// ---------------------------------------------------------------- lines beyond one CTA
+// When one line of the transform (length L) does not fit one CTA's shared memory -- FP64 at
+// n = 8192 (L = 16384 compact, 24576 on the period-3 grid), FP32 at L = 24576 -- the three passes
+// run as FP64 line transforms of the full complex spectrum, each line that one CTA cannot hold
+// split four-step (L = L1 L2, a global-memory buffer between the two halves):
+//   pass 1: rows j1 < n of u (times the mask), zero-extended to L: X[k2][j1];
+//   pass 2: per chunk of columns k2, the length-L transform of X[k2][j1 < n] (zero beyond n),
+//           times the multiplier ghat(|k1|, |k2|), the inverse transform, the first n outputs back
+//           into X[k2][j1];
+//   pass 3: rows j1 of X along k2, inverse, the first n outputs: Y[j1][j2];
+//   out = beta u + alpha Y / L^2 (real part for R2R), in the plan's type.
+// Densities run one after another, so the workspace does not grow with the batch.  The arithmetic
+// is FP64 in every plan precision.
+#define LONG_CHUNK 2048
+struct LongLines {
+    LineFFT f;
+    int chunk = 0;
+};
+
+static size_t long_ws_elems(const conv_plan_s *p)
+{
+    const size_t n = p->n, L = p->M, ch = std::min<size_t>(L, LONG_CHUNK);
+    return n * L + ch * L + std::max(n, ch) * L + n * n;  // X, F, T, Y (complex FP64)
+}
+
+size_t long_lines_ws_bytes(const conv_plan_s *p) { return long_ws_elems(p) * sizeof(double2); }
+
+conv_status long_lines_init(conv_plan_s *p)
+{
+    LongLines *ll = new LongLines();
+    conv_status rc = ll->f.init(p->M, p->setup_stream);
+    if (rc != CONV_OK) {
+        delete ll;
+        return rc;
+    }
+    ll->chunk = std::min(p->M, LONG_CHUNK);
+    p->longl = ll;
+    WSC_CUDA(cudaStreamSynchronize(p->setup_stream));
+    return CONV_OK;
+}
+
+void long_lines_destroy(conv_plan_s *p)
+{
+    delete p->longl;
+    p->longl = nullptr;
+}
+
+// F[c][k1] *= ghat(|k1|, |k2|), k2 = c0 + c: the multiplier quadrant [k2][k1], h = L/2 + 1
+__global__ void k_long_multiply(double2 *__restrict__ F, int cols, int c0, int L, const double *__restrict__ g, int cplx,
+                                int odd)
+{
+    const int h = L / 2 + 1;
+    const long long N = (long long)cols * L;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i / L), k1 = (int)(i - (long long)c * L), k2 = c0 + c;
+        const int a1 = k1 <= L / 2 ? k1 : L - k1, a2 = k2 <= L / 2 ? k2 : L - k2;
+        const size_t q = (size_t)a2 * h + a1;
+        const double2 v = F[i];
+        if (odd) {  // i sgn(k1) g, 0 at the unpaired Nyquist index
+            const double t = 2 * k1 == L ? 0.0 : (2 * k1 < L ? g[q] : -g[q]);
+            F[i] = make_double2(-t * v.y, t * v.x);
+        } else if (cplx) {
+            const double gr = g[2 * q], gi = g[2 * q + 1];
+            F[i] = make_double2(v.x * gr - v.y * gi, v.x * gi + v.y * gr);
+        } else {
+            F[i] = make_double2(v.x * g[q], v.y * g[q]);
+        }
+    }
+}
+
+// out = beta u + alpha Y (alpha complex; real part for R2R), in the plan's types
+template <typename T>
+__global__ void k_long_finish(const double2 *__restrict__ Y, const void *__restrict__ u, void *__restrict__ out,
+                              long long N, int io, double are, double aim, double beta)
+{
+    typedef typename cvec<T>::t V;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double2 y = Y[i];
+        double zr = are * y.x - aim * y.y, zi = are * y.y + aim * y.x;
+        if (beta != 0.0) {
+            if (io == CONV_IO_C2C) {
+                const V uv = reinterpret_cast<const V *>(u)[i];
+                zr += beta * (double)uv.x;
+                zi += beta * (double)uv.y;
+            } else {
+                zr += beta * (double)reinterpret_cast<const T *>(u)[i];
+            }
+        }
+        if (io == CONV_IO_R2R) reinterpret_cast<T *>(out)[i] = (T)zr;
+        else reinterpret_cast<V *>(out)[i] = cmk<V>((T)zr, (T)zi);
+    }
+}
+
+conv_status long_lines_apply(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
+                             double aim, double beta, void *ws, cudaStream_t st)
+{
+    const LongLines *ll = p->longl;
+    if (!ll) return fail(CONV_EUNSUPPORTED, "long-line transforms not set up");
+    const int n = p->n, L = p->M, CH = ll->chunk, sms = sm_count();
+    const bool f32 = p->prec == CONV_P_FP32;
+    const size_t nL = (size_t)n * L;
+    double2 *X = reinterpret_cast<double2 *>(ws), *F = X + nL, *Tb = F + (size_t)CH * L,
+            *Y = Tb + std::max<size_t>(n, CH) * L;
+    const double sc = 1.0 / ((double)L * (double)L);
+    const size_t rsz = f32 ? 4 : 8;
+    const size_t in_elem = (p->io == CONV_IO_C2C ? 2 : 1) * rsz, out_elem = (p->io == CONV_IO_R2R ? 1 : 2) * rsz;
+    cudaEvent_t *ev = timing_slot(p);
+    if (ev) cudaEventRecord(ev[0], st);
+    conv_status rc = CONV_OK;
+    for (int b = 0; b < batch && rc == CONV_OK; ++b) {
+        const char *ub = reinterpret_cast<const char *>(u) + (size_t)b * n * n * in_elem;
+        char *ob = reinterpret_cast<char *>(out) + (size_t)b * n * n * out_elem;
+        LineGen G{};
+        G.L = L;
+        G.mode = 7;
+        G.n = n;
+        G.dens = ub;
+        G.dens_kind = (f32 ? 0 : 1) + (p->io == CONV_IO_C2C ? 2 : 0);
+        G.dmask = mask;
+        rc = ll->f.run<false>(G, X, n, L, 1, n, 1.0, sms, st, Tb);  // X[k2][j1]
+        if (ev && b == 0) cudaEventRecord(ev[1], st);
+        for (int c0 = 0; c0 < L && rc == CONV_OK; c0 += CH) {
+            const int cols = std::min(CH, L - c0);
+            LineGen C{};
+            C.L = L;
+            C.mode = 5;
+            C.src = X + (size_t)c0 * n;
+            C.sl = n;
+            C.se = 1;
+            C.nvalid = n;
+            rc = ll->f.run<false>(C, F, cols, L, L, 1, 1.0, sms, st, Tb);  // F[c][k1]
+            if (rc != CONV_OK) break;
+            const long long NF = (long long)cols * L;
+            k_long_multiply<<<(int)std::min<long long>((NF + 255) / 256, sms * 8LL), 256, 0, st>>>(
+                F, cols, c0, L, p->ghat64, p->complex_ghat ? 1 : 0, p->kern.family == CONV_K_DX1LOG ? 1 : 0);
+            LineGen I{};
+            I.L = L;
+            I.mode = 5;
+            I.src = F;
+            I.sl = L;
+            I.se = 1;
+            rc = ll->f.run<true>(I, X + (size_t)c0 * n, cols, n, n, 1, 1.0, sms, st, Tb);  // X[k2][j1 < n]
+        }
+        if (ev && b == 0) cudaEventRecord(ev[2], st);
+        if (rc != CONV_OK) break;
+        LineGen R{};
+        R.L = L;
+        R.mode = 5;
+        R.src = X;
+        R.sl = 1;
+        R.se = n;
+        rc = ll->f.run<true>(R, Y, n, n, n, 1, sc, sms, st, Tb);  // Y[j1][j2]
+        if (rc != CONV_OK) break;
+        const long long NN = (long long)n * n;
+        const int g2 = (int)std::min<long long>((NN + 255) / 256, sms * 8LL);
+        if (f32) k_long_finish<float><<<g2, 256, 0, st>>>(Y, ub, ob, NN, p->io, are, aim, beta);
+        else k_long_finish<double><<<g2, 256, 0, st>>>(Y, ub, ob, NN, p->io, are, aim, beta);
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    WSC_CUDA(cudaGetLastError());
+    return rc;
 }
 
 }  // namespace wsc

@@ -552,10 +552,25 @@ static conv_status device_limits(conv_plan_s *p, int &smem_optin, int &sms)
 // of each pass.  Environment overrides for experiments: WSCONV_ELEMS, WSCONV_FUSED (0/1),
 // WSCONV_TWS (0: no pass keeps its table in shared memory), WSCONV_PF (0/1: prefetch in no / every
 // pass), WSCONV_GROUPS (1: one transform per CTA), WSCONV_CFG ("r,c,i": the CFG_* bits per pass).
+// Lines that one CTA cannot hold (or, with WSCONV_LONG_LINES=1, any line: tests) take the
+// four-step FP64 line pipeline of fsmask.cu (p->long_lines).
+static bool factor_235(int L)
+{
+    for (int f : {2, 3, 5})
+        while (L % f == 0) L /= f;
+    return L == 1;
+}
+
 conv_status select_transform(conv_plan_s *p)
 {
     int smem_optin = 0, sms = 0;
     conv_status rc = device_limits(p, smem_optin, sms);
+    const char *force_long = getenv("WSCONV_LONG_LINES");
+    if ((rc == CONV_EUNSUPPORTED || (force_long && atoi(force_long) == 1)) && factor_235(p->M)) {
+        p->long_lines = true;
+        p->fused = false;
+        return CONV_OK;
+    }
     if (rc != CONV_OK) return rc;
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
     const int ncand = p->prec == CONV_P_FP64 ? (int)(sizeof kElems64 / sizeof(int)) : (int)(sizeof kElems32 / sizeof(int));
@@ -580,8 +595,12 @@ conv_status select_transform(conv_plan_s *p)
         }
         if (configure(p, c, smem_optin, sms)) return CONV_OK;
     }
-    return fail(CONV_EUNSUPPORTED, "transform length " + std::to_string(p->M) +
-                                       " is not 2^a 3^b 5^c or needs more threads than one CTA has");
+    if (factor_235(p->M)) {  // fits shared memory but needs more threads than one CTA has
+        p->long_lines = true;
+        p->fused = false;
+        return CONV_OK;
+    }
+    return fail(CONV_EUNSUPPORTED, "transform length " + std::to_string(p->M) + " is not 2^a 3^b 5^c");
 }
 
 // The autotuner's search space, as families that share E and fused: within a family the options
@@ -590,6 +609,7 @@ conv_status select_transform(conv_plan_s *p)
 std::vector<std::vector<Candidate>> transform_families(conv_plan_s *p)
 {
     std::vector<std::vector<Candidate>> out;
+    if (p->long_lines) return out;
     int smem_optin = 0, sms = 0;
     if (device_limits(p, smem_optin, sms) != CONV_OK) return out;
     const int *cand = p->prec == CONV_P_FP64 ? kElems64 : kElems32;
@@ -634,6 +654,7 @@ conv_status apply_candidate(conv_plan_s *p, const Candidate &c)
 conv_status launch_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
                             double alpha_re, double alpha_im, double beta, void *ws, cudaStream_t st)
 {
+    if (p->long_lines) return long_lines_apply(p, u, mask, out, batch, alpha_re, alpha_im, beta, ws, st);
     conv_status rc = CONV_OK;
     if (p->fused)
         WSC_DISPATCH_FUSED(p->prec, p->elems, p->ed, false,

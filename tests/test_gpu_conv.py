@@ -437,14 +437,15 @@ def test_fourier_smoothed_convolution(prec):
     assert _relerr(ref, out) <= TOL[prec]
 
 
-def test_lines_beyond_one_cta_are_reported_unsupported():
-    """A pass holds a whole line of the transform in one CTA's shared memory: FP64 passes at
-    L = 16384 (n = 8192 compact) and the FP32 period-3 lines of 24576 at n = 8192 are refused with
-    CONV_EUNSUPPORTED, as is FP64 on the period-3 grid there."""
-    from paper_2107_03958_gb300._native import ConvError
+def test_lines_beyond_one_cta_take_the_long_line_pipeline():
+    """A pass holds a whole line of the transform in one CTA's shared memory; FP64 lines of 16384
+    (n = 8192 compact) and 24576 (period 3), and FP32 lines of 24576, run as four-step FP64 line
+    transforms instead (tests/test_gpu_long_lines.py checks their results)."""
     for prec, compact in (("fp64", True), ("fp32", False), ("fp64", False)):
-        with pytest.raises(ConvError, match="CONV_EUNSUPPORTED"):
-            ConvPlan("log", n=8192, period=3, precision=prec, io="r2r", compact=compact)
+        plan = ConvPlan("log", n=8192, period=3, precision=prec, io="r2r", compact=compact)
+        assert plan.info.long_lines == 1, (prec, compact)
+        del plan
+    assert ConvPlan("log", n=4096, period=3, precision="fp64", io="r2r", compact=True).info.long_lines == 0
 
 
 @pytest.mark.parametrize("io", ["r2r", "c2c"])
