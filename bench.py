@@ -666,7 +666,9 @@ def serving_leg(count, seed=5):
     lat = sorted(r["latency_s"] for r in ok)
     lat_ls = sorted(r["latency_s"] for r, q in zip(res, reqs) if q["kind"] == "ls" and r["status"] == "CONV_OK")
     pct = lambda a, p: 1e3 * a[min(len(a) - 1, max(0, int(math.ceil(p * len(a))) - 1))] if a else None
+    conv_res = [r for r, q in zip(res, reqs) if q["kind"] == "conv" and r["status"] == "CONV_OK"]
     return {"requests": count, "completed_ok": len(ok), "wall_s": wall,
+            "conv_mean_batch": sum(r["batched_with"] for r in conv_res) / max(1, len(conv_res)),
             "requests_per_s": len(ok) / wall,
             "ls_solves_per_s": len(lat_ls) / wall, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
             "ls_p50_ms": pct(lat_ls, 0.5), "ls_p99_ms": pct(lat_ls, 0.99),
@@ -827,7 +829,14 @@ def main():
         extras["ls_larger"] = [ls_leg(1024, 40.0, 3, stream), ls_leg(2048, 40.0, 3, stream)]
         extras["ls_multi_rhs"] = ls_multi_leg(512, 40.0, 8, 3, stream)
         extras["mixed_group"] = group_leg(50, stream)
-        extras["serving"] = serving_leg(80)
+        from paper_2107_03958_gb300.api import measure_tc_stage
+        tcs = measure_tc_stage(4000)
+        tcs["what"] = ("one radix-16 stage (Ns = 16) of an FP32 length-8192 column, one column per SM in shared "
+                       "memory: CUDA-core butterflies vs a tcgen05 DFT-matrix product (BF16 hi+lo, 3 products, "
+                       "FP32 accumulation); microseconds per stage per column")
+        tcs["tensor_over_cuda_core"] = tcs["us_tensor"] / tcs["us_cuda_core"]
+        extras["tc_stage"] = tcs
+        extras["serving"] = serving_leg(2000)
         extras["served_ls_burst"] = served_ls_burst(80)
 
     if rank == 0:

@@ -41,15 +41,26 @@ typedef enum {
     CONV_ECANCELLED = 8       /* a serving request was cancelled before it ran (srv_cancel) */
 } conv_status;
 
-/* Kernel families (Sec. 2.2).  g(x) = scale * log|x|, scale * |x|^gamma (gamma > -2, 2 gamma an
- * integer), or scale * (i/4) H0^(1)(kappa |x|).  The paper's Laplace kernel is LOG with
- * scale = -1/(2 pi). */
-typedef enum { CONV_K_LOG = 0, CONV_K_POW = 1, CONV_K_HELMHOLTZ = 2 } conv_kernel_family;
+/* Kernel families (Sec. 2.2, Sec. 3.2).  g(x) = scale * log|x|, scale * |x|^gamma (gamma > -2; the
+ * closed-form moments need 2 gamma an integer, the quadrature moments of conv_plan_moments do not),
+ * scale * (i/4) H0^(1)(kappa |x|), or scale * K0(kappa |x|) / (2 pi) (the Yukawa kernel of
+ * -Delta + kappa^2, Sec. 3.2).  The paper's Laplace kernel is LOG with scale = -1/(2 pi). */
+typedef enum {
+    CONV_K_LOG = 0,
+    CONV_K_POW = 1,
+    CONV_K_HELMHOLTZ = 2,
+    CONV_K_YUKAWA = 3,
+    /* the non-radial kernel of Sec. 3.1: g(x) = scale * (-x1 / (2 pi |x|^2)) = scale * d/dx1 of
+     * -(1/2pi) log|x|; ghat(k) = i scale xi1 (1 - J0(|xi| a)) / |xi|^2, xi = 2 pi k / b, odd in k1
+     * (the unpaired Nyquist mode k1 = -M/2 is given multiplier 0, so real u gives real A_n u).
+     * R2R plans on the period-b grid with closed-form moments only (CONV_EUNSUPPORTED otherwise). */
+    CONV_K_DX1LOG = 4
+} conv_kernel_family;
 
 typedef struct {
     int family;      /* conv_kernel_family */
     double gamma;    /* CONV_K_POW exponent */
-    double kappa;    /* CONV_K_HELMHOLTZ wavenumber (> 0) */
+    double kappa;    /* CONV_K_HELMHOLTZ wavenumber, CONV_K_YUKAWA decay rate (> 0) */
     double scale;    /* multiplies g; 0 is read as 1 */
 } conv_kernel;
 
@@ -98,6 +109,32 @@ enum {
 conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_den, int n,
                          double trunc_a, conv_precision precision, conv_io io, int batch_max,
                          int flags, conv_plan_t *plan);
+
+/* How the moment table ghat is computed (Sec. 2.2, 2.3).
+ *   CONV_MOMENTS_CLOSED:     the closed forms of Sec. 2.2 (and of the Yukawa kernel, Sec. 3.2), with
+ *                            quadrature where they lose digits (conv_plan's default).
+ *   CONV_MOMENTS_QUADRATURE: Sec. 2.3: ghat(k) = 2 pi p int_0^{a^{1/p}} g(tau^p) J0(2 pi |k| tau^p/b)
+ *                            tau^{2p-1} d tau by a high-order rule, for any family (a kernel without
+ *                            closed-form moments; |x|^gamma with any gamma > -2).
+ *   CONV_MOMENTS_LOCALIZED:  Sec. 2.3, eq. (io_split): the moments of g eta_beta by the trapezoidal
+ *                            rule in tau, plus the classical trapezoidal rule for g (1 - eta_beta),
+ *                            whose weights h^2 g(|d|h)(1 - eta_beta(|d|h)) enter as their DFT.
+ *                            eta_beta = 1 on [0, beta/2], 0 beyond beta, the half-window varkappa of
+ *                            eq. (halfwindow1) in between.
+ * The quadrature rules cost O((M/2)^2 z) Bessel evaluations at plan time, z = pi sqrt2 M R / b
+ * (R = a, or beta when localized): seconds at n = 1024, minutes at n = 4096. */
+typedef enum { CONV_MOMENTS_CLOSED = 0, CONV_MOMENTS_QUADRATURE = 1, CONV_MOMENTS_LOCALIZED = 2 } conv_moment_method;
+typedef struct {
+    int method;      /* conv_moment_method */
+    int p;           /* substitution rho = tau^p, 1..16 (<= 0: 4) */
+    int nodes;       /* quadrature nodes (<= 0: chosen from the table's largest phase 2 pi |k| R / b) */
+    double beta;     /* LOCALIZED: localization radius, 0 < beta <= a (<= 0: 1) */
+} conv_moments;
+
+/* conv_plan_ex with the moment table computed as `moments` says (NULL: closed forms). */
+conv_status conv_plan_moments(const conv_kernel *kernel, int period_num, int period_den, int n,
+                              double trunc_a, conv_precision precision, conv_io io, int batch_max,
+                              int flags, const conv_moments *moments, conv_plan_t *plan);
 
 /* Bytes of workspace conv_apply needs for `batch` densities (the n x (L/2+1) or n x L spectra,
  * L the transform length). */
@@ -149,6 +186,20 @@ conv_status conv_apply_host(conv_plan_t plan, const void *u_host, const void *ma
  * allocated. */
 conv_status conv_apply_host_multi(int count, const conv_plan_t *plans, const void *u_host, const void *mask,
                                   void *const *out_host, int batch, void *stream);
+
+/* Densities of one batch convolved with DIFFERENT kernels that share one transform shape (no
+ * counterpart in the paper; a serving aid for Sec. 2.1, eq. (An)):
+ *     out[b] = A_n(u[b] . mask) with the moment table of plans[b],  b < batch,
+ * in one launch of each pass on `shape` (its workspace and launch configuration).  Every
+ * plans[b] must share the shape plan's n, period, precision, io, embedding and multiplier type
+ * (real or complex); their kernels, kappa and truncation radius may differ.  Each result is
+ * bitwise the one conv_apply gives on plans[b] alone.
+ *   batch <= 32; workspace as for conv_apply on `shape` (NULL: the shape plan's, batch <= its
+ *   batch_max).  Asynchronous on `stream`; the plans must outlive the launch.
+ * Returns CONV_EINVAL for what conv_apply rejects and for plans of another shape,
+ * CONV_EUNSUPPORTED for lines beyond one CTA (plans whose info.long_lines is set). */
+conv_status conv_apply_kernels(conv_plan_t shape, const conv_plan_t *plans, const void *u, const void *mask,
+                               void *out, int batch, void *workspace, void *stream);
 
 /* conv_apply without any allocation (the paper has no counterpart; this is a deployment aid).
  * For callers that cannot call cudaMalloc when they run the convolution: code under a device
@@ -229,6 +280,8 @@ typedef struct {
     int r2c_split;       /* R2C with complex ghat on the split pipeline (Re/Im ghat columns) */
     int static_len;      /* the transform length when its stage structure is fixed at compile
                           * time (2^l with n = L/2, or 3 2^l with n = L/3), else 0 */
+    int long_lines;      /* 1: transform lines exceed one CTA (n = 8192 in FP64, or on the
+                            period-3 grid): the passes run as four-step FP64 line transforms */
 } conv_plan_info;
 
 conv_status conv_get_info(conv_plan_t plan, conv_plan_info *info);
@@ -261,7 +314,7 @@ const char *conv_last_error(void);
  * that starts while another uses it (another thread) allocates and frees its own.
  * Returns CONV_ENOTCONVERGED (with info filled) when max_iters is reached. */
 typedef struct {
-    int restart;       /* Krylov dimension per cycle (default 50) */
+    int restart;       /* Krylov dimension per cycle, 1..1000 (default 50) */
     int max_iters;     /* total matvec limit (default 2000) */
     double tol;        /* relative residual target ||f - L x||_2 / ||f||_2 (default 1e-10) */
     int refine;        /* mixed precision: 1 = FP64 iterative refinement around an FP32 inner solve */
@@ -414,6 +467,17 @@ conv_status conv_fault_inject(int kind, int count);
  * Synchronous; allocates and frees its own buffers. */
 conv_status conv_measure_peaks(size_t bytes, double *copy_gbs, double *fp64_tflops,
                                double *fp32_tflops);
+
+/* The tensor-core alternative for the passes' butterflies, measured (no counterpart in the paper;
+ * the FFTs of Sec. 2.1): one radix-16 Stockham stage (Ns = 16) of an FP32 length-8192 column, one
+ * column per SM held in shared memory, computed (a) on the CUDA cores and (b) as a DFT-matrix
+ * product on the tensor cores (tcgen05.mma, M = 128 butterflies x N = 32 x K = 32, BF16 operands
+ * split hi + lo, three products, FP32 accumulation in tensor memory).
+ *   us_cuda_core, us_tensor: microseconds per stage per column (each SM one column), over reps
+ *   stages; max_rel_err: max |(b) - (a)| / max |(a)| over one stage.
+ * Synchronous; allocates and frees its own buffers.  CONV_ETIMEOUT if the bounded wait for the
+ * products gave up. */
+conv_status conv_measure_tc_stage(int reps, double *us_cuda_core, double *us_tensor, double *max_rel_err);
 
 #ifdef __cplusplus
 }

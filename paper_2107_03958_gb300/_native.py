@@ -16,6 +16,10 @@ class ConvKernel(ctypes.Structure):
                 ("scale", ctypes.c_double)]
 
 
+class ConvMoments(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("p", ctypes.c_int), ("nodes", ctypes.c_int), ("beta", ctypes.c_double)]
+
+
 class ConvPlanInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("M", ctypes.c_int), ("period_num", ctypes.c_int),
                 ("period_den", ctypes.c_int), ("b", ctypes.c_double), ("a", ctypes.c_double),
@@ -27,7 +31,7 @@ class ConvPlanInfo(ctypes.Structure):
                 ("groups_cols", ctypes.c_int), ("transform_len", ctypes.c_int),
                 ("compact", ctypes.c_int), ("elems", ctypes.c_int), ("smem_twiddles", ctypes.c_int),
                 ("fused", ctypes.c_int), ("static_log2", ctypes.c_int), ("r2c_split", ctypes.c_int),
-                ("static_len", ctypes.c_int)]
+                ("static_len", ctypes.c_int), ("long_lines", ctypes.c_int)]
 
 
 class LsOpts(ctypes.Structure):
@@ -71,9 +75,15 @@ PROTOTYPES = {
     "conv_plan_ex": (ctypes.c_int, [ctypes.POINTER(ConvKernel), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "conv_plan_moments": (ctypes.c_int, [ctypes.POINTER(ConvKernel), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.POINTER(ConvMoments), ctypes.POINTER(ctypes.c_void_p)]),
     "conv_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "conv_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "conv_apply_kernels": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "conv_apply_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "conv_apply_axpby": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -116,6 +126,8 @@ PROTOTYPES = {
                                          ctypes.POINTER(ctypes.c_void_p)]),
     "conv_group_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "conv_group_destroy": (None, [ctypes.c_void_p]),
+    "conv_measure_tc_stage": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "conv_measure_peaks": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]),

@@ -16,7 +16,8 @@ import torch
 
 from . import _native as N
 
-FAMILY = {"log": 0, "pow": 1, "helmholtz": 2, "helm": 2}
+FAMILY = {"log": 0, "pow": 1, "helmholtz": 2, "helm": 2, "yukawa": 3, "dx1log": 4}
+MOMENTS = {"closed": 0, "quadrature": 1, "localized": 2}
 PRECISION = {"fp64": 0, "fp32": 1}
 IO = {"r2r": 0, "r2c": 1, "c2c": 2}
 
@@ -32,7 +33,9 @@ class ConvPlan:
 
     def __init__(self, kernel="log", n=64, period=3, trunc_a=0.0, precision="fp64", io="r2r",
                  batch_max=1, gamma=0.0, kappa=0.0, scale=1.0, device=None, compact=False,
-                 autotune=False):
+                 autotune=False, moments="closed", moment_p=0, moment_nodes=0, beta=0.0):
+        """moments: 'closed' (Sec. 2.2 closed forms), 'quadrature' (Sec. 2.3, rho = tau^p) or
+        'localized' (Sec. 2.3, eq. (io_split), radius beta)."""
         self._lib = N.load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -42,9 +45,11 @@ class ConvPlan:
         self.period = (frac.numerator, frac.denominator)
         k = N.ConvKernel(FAMILY[kernel], float(gamma), float(kappa), float(scale))
         h = ctypes.c_void_p()
-        N.check(self._lib.conv_plan_ex(ctypes.byref(k), frac.numerator, frac.denominator, int(n),
-                                       float(trunc_a), PRECISION[precision], IO[io], int(batch_max),
-                                       (1 if compact else 0) | (2 if autotune else 0), ctypes.byref(h)))
+        mo = N.ConvMoments(MOMENTS[moments], int(moment_p), int(moment_nodes), float(beta))
+        N.check(self._lib.conv_plan_moments(ctypes.byref(k), frac.numerator, frac.denominator, int(n),
+                                            float(trunc_a), PRECISION[precision], IO[io], int(batch_max),
+                                            (1 if compact else 0) | (2 if autotune else 0), ctypes.byref(mo),
+                                            ctypes.byref(h)))
         self._h = h
         self.info = self._info()
         self.M, self.a = self.info.M, self.info.a
@@ -174,6 +179,24 @@ class ConvPlan:
         buf = np.zeros((h, h), dtype=np.complex128 if cplx else np.float64)
         N.check(self._lib.conv_ghat_to_host(self._h, buf.ctypes.data_as(ctypes.c_void_p)))
         return buf
+
+
+def apply_kernels(shape, plans, u, out=None, mask=None, workspace=None, stream=None):
+    """out[b] = A_n(u[b] * mask) with plans[b]'s kernel, every plan of shape's n, period, precision,
+    io and embedding, in one launch of each pass on `shape` (see conv_apply_kernels)."""
+    shape._check_grid(u, shape.in_dtype(), "u")
+    batch = 1 if u.dim() == 2 else int(np.prod(u.shape[:-2]))
+    if len(plans) != batch:
+        raise ValueError("one plan per density")
+    if out is None:
+        out = torch.empty(u.shape, dtype=shape.out_dtype(), device=u.device)
+    shape._check_grid(out, shape.out_dtype(), "out")
+    arr = (ctypes.c_void_p * batch)(*[p.handle.value for p in plans])
+    N.check(shape._lib.conv_apply_kernels(
+        shape.handle, arr, ctypes.c_void_p(u.data_ptr()),
+        ctypes.c_void_p(mask.data_ptr()) if mask is not None else None, ctypes.c_void_p(out.data_ptr()),
+        batch, ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else None, _stream_ptr(stream)))
+    return out
 
 
 def apply_host_multi(plans, u, outs=None, mask=None, stream=None):
@@ -392,6 +415,16 @@ def fault_inject(kind, count=1):
     """Arm `count` host-side injected faults of one kind ('alloc', 'wait' or 'drop'; see
     conv_fault_inject in wsconv.h); count 0 disarms it."""
     N.check(N.load().conv_fault_inject(N.FAULT[kind], int(count)))
+
+
+def measure_tc_stage(reps=2000):
+    """One radix-16 stage of a length-8192 FP32 column on the CUDA cores and as a tensor-core
+    DFT-matrix product (see conv_measure_tc_stage): microseconds per stage per column and the
+    tensor-core result's max relative difference."""
+    lib = N.load()
+    a, b, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    N.check(lib.conv_measure_tc_stage(int(reps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(e)))
+    return {"us_cuda_core": a.value, "us_tensor": b.value, "max_rel_err": e.value}
 
 
 def default_scale(kernel):

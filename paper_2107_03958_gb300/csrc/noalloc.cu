@@ -49,7 +49,7 @@ extern "C" conv_status conv_apply_noalloc(conv_plan_t p, const void *u, const vo
     void *ws = nullptr;
     conv_status rc = check_apply(p, u, mask, out, batch, 0.0, p->noalloc_scratch, &ws);
     if (rc != CONV_OK || batch == 0) return rc;
-    const size_t need = spectrum_elems(p) * (p->prec == CONV_P_FP64 ? 16 : 8) * (size_t)batch;
+    const size_t need = workspace_bytes(p, batch);
     if (need > WSCONV_NOALLOC_SCRATCH_BYTES)
         return fail(CONV_EINVAL, "conv_apply_noalloc: this plan and batch need " + std::to_string(need) +
                                      " bytes of workspace, above the fixed " +

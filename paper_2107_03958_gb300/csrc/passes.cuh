@@ -34,7 +34,27 @@ template <typename T> struct PassArgs {
     int vec;               // R2C pass 2: the output pairs may be stored as 16-byte vectors
     int tma;               // pass 1: spectra leave by TMA stores; pass 3: spectra arrive by TMA loads
     CUtensorMap tmap;      // the spectrum array's map for those copies (kernel parameter space)
+    int odd;               // pass 2: the multiplier is i sgn(k1) T(|k1|, |k2|) (the non-radial kernel)
+    int nsel;              // pass 2: 0, or the batch's own multiplier per density (conv_apply_kernels)
+    const void *gsel[WSC_MAX_SEL];
 };
+
+// x times the odd multiplier i sgn(k1) t at transform index o of a length-L column (k1 = o below
+// L/2, o - L above it; the unpaired Nyquist index L/2 gets 0).
+template <typename V, typename T>
+__device__ __forceinline__ V odd_mul(V x, T t, int o, int L)
+{
+    if (2 * o == L) return cmk<V>((T)0, (T)0);
+    const T st = 2 * o < L ? t : -t;
+    return cmk<V>(-st * x.y, st * x.x);
+}
+
+// The multiplier table of density b in pass 2: the plan's, or the batch's own per density.
+template <typename T>
+__device__ __forceinline__ const void *mult_of(const PassArgs<T> &a, int b)
+{
+    return a.nsel ? a.gsel[b] : a.ghat;
+}
 
 // Staging of a fused pass 1 with TMA stores: [input rows (prefetch), rounded to 128 bytes]
 // [output pairs: nbox x TMA_ROWS x 2 elements]; pass 3 with TMA loads: [nbox x TMA_ROWS x 2].
@@ -139,11 +159,11 @@ __global__ void WSC_LB(T, E) k_r2r_cols(const PassArgs<T> a)
     const V *twp;
     V *buf = setup_smem<T, TWS>(a, twp, g);
     const int n = a.n, M = a.M, h = a.h;
-    const T *ghat = reinterpret_cast<const T *>(a.ghat);
     for (int base = blockIdx.x * G; base < a.units; base += gridDim.x * G) {
         const int unit = base + g;
         const bool valid = unit < a.units;
         const int k2 = valid ? unit / a.batch : 0, b = valid ? unit - k2 * a.batch : 0;
+        const T *ghat = reinterpret_cast<const T *>(mult_of(a, b));
         V *col = reinterpret_cast<V *>(a.out) + (size_t)b * h * n + (size_t)k2 * n;
         for (int e = lt; e < M; e += a.tpt) buf[pidx<T>(e)] = (valid && e < n) ? col[e] : cmk<V>(0, 0);
         __syncthreads();
@@ -151,7 +171,8 @@ __global__ void WSC_LB(T, E) k_r2r_cols(const PassArgs<T> a)
         const T *gc = ghat + (size_t)k2 * h;
         for (int e = lt; e < M; e += a.tpt) {
             const int k1 = e <= M / 2 ? e : M - e;
-            buf[pidx<T>(e)] = cscale(buf[pidx<T>(e)], __ldg(&gc[k1]));
+            buf[pidx<T>(e)] = a.odd ? odd_mul(buf[pidx<T>(e)], __ldg(&gc[k1]), e, M)
+                                    : cscale(buf[pidx<T>(e)], __ldg(&gc[k1]));
         }
         __syncthreads();
         fft_smem<T, E, true, TWS>(buf, a.P, twp, lt, a.tpt);
@@ -263,8 +284,8 @@ __global__ void WSC_LB(T, E) k_c2c_cols(const PassArgs<T> a)
         for (int e = lt; e < M; e += a.tpt) {
             const int k1 = e <= M / 2 ? e : M - e;
             V z = buf[pidx<T>(e)];
-            if (CG) z = cmul(z, __ldg(reinterpret_cast<const V *>(a.ghat) + (size_t)k2q * h + k1));
-            else z = cscale(z, __ldg(reinterpret_cast<const T *>(a.ghat) + (size_t)k2q * h + k1));
+            if (CG) z = cmul(z, __ldg(reinterpret_cast<const V *>(mult_of(a, b)) + (size_t)k2q * h + k1));
+            else z = cscale(z, __ldg(reinterpret_cast<const T *>(mult_of(a, b)) + (size_t)k2q * h + k1));
             buf[pidx<T>(e)] = z;
         }
         __syncthreads();
@@ -349,6 +370,9 @@ conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *
     PassArgs<T> a{};
     a.mask = reinterpret_cast<const T *>(mask);
     a.ghat = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
+    a.nsel = p->nsel;
+    for (int i = 0; i < p->nsel; ++i) a.gsel[i] = p->sel[i];
+    a.odd = p->kern.family == CONV_K_DX1LOG ? 1 : 0;
     a.u = u;
     a.tw = reinterpret_cast<const V *>(p->tw);
     a.tw_len = p->fft.tw_len;

@@ -219,16 +219,16 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const __grid_constant__ PassArgs<T
         const int unit = base + g;
         const bool valid = unit < a.units;
         if (a.pf && !await_bulk(a, bar, par, valid)) return;
-        const int k2 = valid ? unit / a.batch : 0;
+        const int k2 = valid ? unit / a.batch : 0, bq = valid ? unit - k2 * a.batch : 0;
         V *col = col_at(valid ? unit : 0);
-        const T *gc = ghat + (size_t)k2 * h;
+        const T *gc = (a.nsel ? reinterpret_cast<const T *>(a.gsel[bq]) : ghat) + (size_t)k2 * h;
         auto src = [&](int i) -> V {
             if (!valid || i >= n) return cmk<V>(0, 0);
             return a.pf ? stg[i] : col[i];
         };
         auto mul = smem_hook([&](int o, V &x) {
             const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
-            x = cscale(x, __ldg(&gc[k1]));
+            x = a.odd ? odd_mul(x, __ldg(&gc[k1]), o, Lm) : cscale(x, __ldg(&gc[k1]));
         });
         fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
@@ -376,14 +376,14 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T
         const int unit = base + g;
         const bool valid = unit < a.units;
         if (a.pf && !await_bulk(a, bar, par, valid)) return;
-        const int k2 = valid ? unit / a.batch : 0;
+        const int k2 = valid ? unit / a.batch : 0, bq = valid ? unit - k2 * a.batch : 0;
         const size_t co = col_off(valid ? unit : 0);
         const V *cin = reinterpret_cast<const V *>(a.in) + co;
         auto src = [&](int i) -> V {
             if (!valid || i >= n) return cmk<V>(0, 0);
             return a.pf ? stg[i] : cin[i];
         };
-        const V *gc = cg + (size_t)k2 * h;
+        const V *gc = (a.nsel ? reinterpret_cast<const V *>(a.gsel[bq]) : cg) + (size_t)k2 * h;
         auto mul = smem_hook([&](int o, V &x) {
             const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             const V gk = __ldg(&gc[k1]);
@@ -570,17 +570,18 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_cols(const __grid_constant__ PassArgs<T
         const int unit = base + g;
         const bool valid = unit < a.units;
         if (a.pf && !await_bulk(a, bar, par, valid)) return;
-        const int k2 = valid ? unit / a.batch : 0;
+        const int k2 = valid ? unit / a.batch : 0, bq = valid ? unit - k2 * a.batch : 0;
         V *col = col_at(valid ? unit : 0);
         const int k2q = k2 <= M / 2 ? k2 : M - k2;
+        const void *gq = mult_of(a, bq);
         auto src = [&](int i) -> V {
             if (!valid || i >= n) return cmk<V>(0, 0);
             return a.pf ? stg[i] : col[i];
         };
         auto mul = smem_hook([&](int o, V &x) {
             const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
-            if (CG) x = cmul(x, __ldg(reinterpret_cast<const V *>(a.ghat) + (size_t)k2q * h + k1));
-            else x = cscale(x, __ldg(reinterpret_cast<const T *>(a.ghat) + (size_t)k2q * h + k1));
+            if (CG) x = cmul(x, __ldg(reinterpret_cast<const V *>(gq) + (size_t)k2q * h + k1));
+            else x = cscale(x, __ldg(reinterpret_cast<const T *>(gq) + (size_t)k2q * h + k1));
         });
         fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
@@ -684,6 +685,9 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
     PassArgs<T> a{};
     a.err = p->dev_err;
     a.give_up = fault_take(CONV_FAULT_WAIT) ? 1 : 0;
+    a.nsel = p->nsel;
+    for (int i = 0; i < p->nsel; ++i) a.gsel[i] = p->sel[i];
+    a.odd = p->kern.family == CONV_K_DX1LOG ? 1 : 0;
     a.mask = reinterpret_cast<const T *>(mask);
     a.ghat = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
     a.u = u;

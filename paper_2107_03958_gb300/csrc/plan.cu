@@ -68,11 +68,18 @@ size_t spectrum_elems(const conv_plan_s *p)
     return (size_t)(p->io == CONV_IO_R2R ? p->h : p->M) * p->n;
 }
 
+size_t workspace_bytes(const conv_plan_s *p, int batch)
+{
+    if (p->long_lines) return batch > 0 ? long_lines_ws_bytes(p) : 0;  // densities run one at a time
+    return spectrum_elems(p) * (p->prec == CONV_P_FP64 ? 16 : 8) * (size_t)batch;
+}
+
 void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im);
 
 // Per-stage twiddle blocks of the plan's radix sequence, in the plan precision.
 static conv_status upload_twiddles(conv_plan_s *p)
 {
+    if (p->long_lines) return CONV_OK;  // the long-line pipeline keeps its own tables
     std::vector<double> h;
     stage_twiddles(p->fft, h);
     const bool f64 = p->prec == CONV_P_FP64;
@@ -253,6 +260,7 @@ void conv_destroy(conv_plan_t p)
     if (!p) return;
     destroy_hostpipe(p);
     destroy_ls_cache(p);
+    long_lines_destroy(p);
     if (p->ghat64 && p->ghat64 != p->ghat_paper) cudaFree(p->ghat64);
     if (p->ghat_paper) cudaFree(p->ghat_paper);
     if (p->ghat32) cudaFree(p->ghat32);
@@ -278,8 +286,8 @@ conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den,
 // n, truncation radius and embedding whose FP64 tables (moments, compact multiplier) are copied
 // instead of computed again (the FP64 twin of an FP32 plan).
 static conv_status plan_create(const conv_kernel *kernel, int period_num, int period_den, int n, double trunc_a,
-                               conv_precision precision, conv_io io, int batch_max, int flags, const conv_plan_s *share,
-                               conv_plan_t *plan)
+                               conv_precision precision, conv_io io, int batch_max, int flags,
+                               const conv_moments *moments, const conv_plan_s *share, conv_plan_t *plan)
 {
     g_last_error.clear();
     if (!plan) return fail(CONV_EINVAL, "plan output pointer is NULL");
@@ -298,17 +306,26 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
         return fail(CONV_EINVAL, "unknown io mode");
     if (batch_max < 1) return fail(CONV_EINVAL, "batch_max must be >= 1");
     const int fam = kernel->family;
-    if (fam != CONV_K_LOG && fam != CONV_K_POW && fam != CONV_K_HELMHOLTZ)
+    if (fam != CONV_K_LOG && fam != CONV_K_POW && fam != CONV_K_HELMHOLTZ && fam != CONV_K_YUKAWA &&
+        fam != CONV_K_DX1LOG)
         return fail(CONV_EINVAL, "unknown kernel family");
-    if (fam == CONV_K_HELMHOLTZ && !(kernel->kappa > 0.0))
-        return fail(CONV_EINVAL, "Helmholtz kernel needs kappa > 0");
+    if (fam == CONV_K_DX1LOG &&
+        (io != CONV_IO_R2R || (flags & CONV_PLAN_COMPACT) || (moments && moments->method != CONV_MOMENTS_CLOSED)))
+        return fail(CONV_EUNSUPPORTED, "the non-radial kernel runs R2R on the period-b grid with closed-form moments");
+    if ((fam == CONV_K_HELMHOLTZ || fam == CONV_K_YUKAWA) && !(kernel->kappa > 0.0))
+        return fail(CONV_EINVAL, "Helmholtz and Yukawa kernels need kappa > 0");
     if (fam == CONV_K_HELMHOLTZ && io == CONV_IO_R2R)
         return fail(CONV_EINVAL, "Helmholtz kernel has a complex ghat: use R2C or C2C");
+    conv_moments mo{};
+    if (moments) mo = *moments;
+    if (mo.method != CONV_MOMENTS_CLOSED && mo.method != CONV_MOMENTS_QUADRATURE && mo.method != CONV_MOMENTS_LOCALIZED)
+        return fail(CONV_EINVAL, "unknown moment method");
+    if (mo.p > 16 || mo.nodes < 0) return fail(CONV_EINVAL, "moment substitution power must be <= 16, nodes >= 0");
     if (fam == CONV_K_POW) {
         if (!(kernel->gamma > -2.0)) return fail(CONV_EINVAL, "|x|^gamma needs gamma > -2");
         double tg = 2.0 * kernel->gamma;
-        if (std::fabs(tg - std::round(tg)) > 1e-12)
-            return fail(CONV_EUNSUPPORTED, "|x|^gamma moments need 2*gamma integer");
+        if (mo.method == CONV_MOMENTS_CLOSED && std::fabs(tg - std::round(tg)) > 1e-12)
+            return fail(CONV_EUNSUPPORTED, "closed-form |x|^gamma moments need 2*gamma integer (use quadrature moments)");
     }
     const int M = (int)Mll;
     if (M % 2) return fail(CONV_EUNSUPPORTED, "M = n b must be even");
@@ -320,7 +337,10 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
         a = 0.5 * (std::sqrt(2.0) + b - 1.0);
     }
     if (flags & ~(CONV_PLAN_COMPACT | CONV_PLAN_AUTOTUNE)) return fail(CONV_EINVAL, "unknown plan flags");
+    if (mo.method == CONV_MOMENTS_LOCALIZED && mo.beta > a)
+        return fail(CONV_EINVAL, "localization radius beta must not exceed the truncation radius a");
     conv_plan_s *p = new conv_plan_s();
+    p->moments = mo;
     p->kern = *kernel;
     p->pnum = period_num;
     p->pden = period_den;
@@ -367,9 +387,10 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
         }
     }
     if (rc == CONV_OK) rc = upload_twiddles(p);
+    if (rc == CONV_OK && p->long_lines) rc = long_lines_init(p);
     if (rc == CONV_OK) rc = share ? copy_ghat(p, share) : build_ghat(p);
     if (rc == CONV_OK) {
-        p->ws_bytes = spectrum_elems(p) * elem_bytes(p) * (size_t)batch_max;
+        p->ws_bytes = workspace_bytes(p, batch_max);
         if (fault_take(CONV_FAULT_ALLOC)) {
             rc = fail(CONV_ENOMEM, "cudaMalloc of the workspace failed (injected fault)");
         } else if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) {
@@ -381,7 +402,7 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
         cudaError_t e = cudaStreamSynchronize(p->setup_stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "plan setup");
     }
-    if (rc == CONV_OK && (flags & CONV_PLAN_AUTOTUNE)) rc = autotune(p);
+    if (rc == CONV_OK && (flags & CONV_PLAN_AUTOTUNE) && !p->long_lines) rc = autotune(p);
     if (rc == CONV_OK) noalloc_lookup(p);
     if (rc != CONV_OK) {
         conv_destroy(p);
@@ -395,7 +416,16 @@ conv_status conv_plan_ex(const conv_kernel *kernel, int period_num, int period_d
                          double trunc_a, conv_precision precision, conv_io io, int batch_max, int flags,
                          conv_plan_t *plan)
 {
-    return plan_create(kernel, period_num, period_den, n, trunc_a, precision, io, batch_max, flags, nullptr, plan);
+    return plan_create(kernel, period_num, period_den, n, trunc_a, precision, io, batch_max, flags, nullptr, nullptr,
+                       plan);
+}
+
+conv_status conv_plan_moments(const conv_kernel *kernel, int period_num, int period_den, int n, double trunc_a,
+                              conv_precision precision, conv_io io, int batch_max, int flags,
+                              const conv_moments *moments, conv_plan_t *plan)
+{
+    return plan_create(kernel, period_num, period_den, n, trunc_a, precision, io, batch_max, flags, moments, nullptr,
+                       plan);
 }
 
 conv_status conv_device_status(conv_plan_t p, void *stream)
@@ -427,7 +457,7 @@ conv_status conv_fault_inject(int kind, int count)
 conv_status conv_workspace_size(conv_plan_t p, int batch, size_t *bytes)
 {
     if (!p || !bytes || batch < 0) return fail(CONV_EINVAL, "bad argument");
-    *bytes = spectrum_elems(p) * elem_bytes(p) * (size_t)batch;
+    *bytes = workspace_bytes(p, batch);
     return CONV_OK;
 }
 
@@ -448,6 +478,35 @@ conv_status conv_apply(conv_plan_t p, const void *u, const void *mask, void *out
     return conv_apply_axpby(p, u, mask, out, batch, 1.0, 0.0, 0.0, workspace, stream);
 }
 
+conv_status conv_apply_kernels(conv_plan_t shape, const conv_plan_t *plans, const void *u, const void *mask,
+                               void *out, int batch, void *workspace, void *stream)
+{
+    void *ws = nullptr;
+    conv_status rc = check_apply(shape, u, mask, out, batch, 0.0, workspace, &ws);
+    if (rc != CONV_OK || batch == 0) return rc;
+    if (!plans) return fail(CONV_EINVAL, "plans is NULL");
+    if (batch > WSC_MAX_SEL)
+        return fail(CONV_EINVAL, "conv_apply_kernels takes at most " + std::to_string(WSC_MAX_SEL) + " densities");
+    if (shape->long_lines) return fail(CONV_EUNSUPPORTED, "conv_apply_kernels: lines beyond one CTA");
+    const void *sel[WSC_MAX_SEL];
+    for (int b = 0; b < batch; ++b) {
+        const conv_plan_s *q = plans[b];
+        if (!q) return fail(CONV_EINVAL, "a plan in the list is NULL");
+        if (q->n != shape->n || q->Mb != shape->Mb || q->M != shape->M || q->prec != shape->prec ||
+            q->io != shape->io || q->compact != shape->compact || q->complex_ghat != shape->complex_ghat ||
+            q->device != shape->device || q->long_lines)
+            return fail(CONV_EINVAL, "conv_apply_kernels: every plan must share n, period, precision, io, "
+                                     "embedding and multiplier type with the shape plan");
+        sel[b] = shape->prec == CONV_P_FP64 ? (const void *)q->ghat64 : q->ghat32;
+    }
+    // the kernel parameters of this launch carry the tables; the plan field lasts only the launch
+    shape->nsel = batch;
+    for (int b = 0; b < batch; ++b) shape->sel[b] = sel[b];
+    rc = launch_pipeline(shape, u, mask, out, batch, 1.0, 0.0, 0.0, ws, reinterpret_cast<cudaStream_t>(stream));
+    shape->nsel = 0;
+    return rc;
+}
+
 conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
 {
     if (!p || !info) return fail(CONV_EINVAL, "bad argument");
@@ -462,6 +521,7 @@ conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
     info->static_log2 = p->fused && p->ed >= 1000 && p->ed < 2000 ? p->ed - 1000 : 0;
     info->static_len = !p->fused ? 0 : (p->ed >= 2000 ? 3 << (p->ed - 2000) : (p->ed >= 1000 ? 1 << (p->ed - 1000) : 0));
     info->r2c_split = p->r2c_split ? 1 : 0;
+    info->long_lines = p->long_lines ? 1 : 0;
     info->period_num = p->pnum;
     info->period_den = p->pden;
     info->b = p->b;
@@ -521,6 +581,6 @@ namespace wsc {
 conv_status conv_plan_twin(const conv_plan_s *p, conv_plan_s **twin)
 {
     return plan_create(&p->kern, p->pnum, p->pden, p->n, p->a, CONV_P_FP64, CONV_IO_C2C, 1,
-                       p->compact ? CONV_PLAN_COMPACT : 0, p, twin);
+                       p->compact ? CONV_PLAN_COMPACT : 0, &p->moments, p, twin);
 }
 }  // namespace wsc

@@ -2,12 +2,18 @@
 // paper; this is the serving layer around the Sec. 2.1 convolution and the Sec. 3.3 solver).
 //
 // Requests arrive at any time (srv_submit).  A dispatcher thread admits them first-fit against a
-// device-memory budget (plan tables, workspaces, Krylov bases), keeps plans resident in a cache, and
-//   - convolution requests with the same plan key that are waiting together are gathered into one
-//     batched launch (their inputs copied into the plan's staging buffer, results scattered back),
-//     on that plan's own stream, so different plans' batches overlap on the GPU;
-//   - Lippmann-Schwinger requests run on worker threads, each solve on its own stream, overlapping
-//     with everything else.
+// device-memory budget (plan tables, workspaces, Krylov bases) and keeps plans resident in a cache.
+//   - Plans are built on builder threads, off the dispatcher: a request whose plan is missing waits
+//     for its build while every other request keeps flowing.
+//   - Convolution requests wait in one ready queue per transform shape (n, period, precision, io):
+//     requests on different kernels (log, |x|^gamma, Helmholtz with any kappa) share a shape.  A
+//     shape's queue is launched as one batch when nothing of that shape is on the GPU, or when it
+//     holds a full batch; requests that arrive while a batch runs gather into the next one.  A
+//     batch of several plans is one conv_apply_kernels launch per pass (each density with its own
+//     plan's multiplier) on the leading request's plan, its inputs gathered into that plan's
+//     staging buffer and its results scattered back.
+//   - Lippmann-Schwinger requests run on worker threads, each solve on its own stream,
+//     overlapping with everything else.
 // A completion thread polls the batches' events; srv_wait blocks on a request's completion.
 // Results do not depend on what else is in flight: each density of a batch is transformed by the
 // same kernels with the same arithmetic as alone, and GMRES uses fixed-order reductions.
@@ -43,6 +49,14 @@ struct PlanKey {
     }
 };
 
+struct ShapeKey {
+    int n, pnum, pden, prec, io;
+    bool operator<(const ShapeKey &o) const
+    {
+        return std::tie(n, pnum, pden, prec, io) < std::tie(o.n, o.pnum, o.pden, o.prec, o.io);
+    }
+};
+
 struct CachedPlan {
     conv_plan_t plan = nullptr;
     cudaStream_t stream = nullptr;
@@ -65,9 +79,17 @@ struct Req {
 
 struct Batch {
     std::vector<std::shared_ptr<Req>> reqs;
-    std::shared_ptr<CachedPlan> cp;
+    std::shared_ptr<CachedPlan> cp;  // the leading request's plan: stream, staging, workspace
+    ShapeKey shape{};
     cudaEvent_t ev = nullptr;
     int pin = -1;  // pinned slot receiving the plan's device status word after the apply
+};
+
+// A plan being built: the bytes reserved for it at admission and the requests waiting for it.
+struct BuildJob {
+    srv_request r;  // the request that asked first (its kernel and shape)
+    size_t reserved = 0;
+    std::vector<std::shared_ptr<Req>> waiters;
 };
 
 }  // namespace wsc
@@ -82,14 +104,19 @@ struct srv_s {
     std::deque<std::shared_ptr<wsc::Req>> pending;
     std::map<long long, std::shared_ptr<wsc::Req>> all;
     std::map<wsc::PlanKey, std::shared_ptr<wsc::CachedPlan>> plans;
+    std::map<wsc::PlanKey, wsc::BuildJob> building;          // plans being built
+    std::deque<wsc::PlanKey> build_queue;                     // ... not yet taken by a builder
+    std::map<wsc::ShapeKey, std::deque<std::shared_ptr<wsc::Req>>> ready;  // conv requests by shape
+    std::map<wsc::ShapeKey, int> shape_inflight;              // batches of a shape on the GPU
     std::deque<wsc::Batch> inflight;
     std::deque<std::shared_ptr<wsc::Req>> ls_queue;
     int inflight_reqs = 0;
     long long next_ticket = 1;
     bool stop = false;
     int device = 0;
+    std::condition_variable cv_build;
     std::thread dispatcher, completer;
-    std::vector<std::thread> workers;
+    std::vector<std::thread> workers, builders;
     srv_stats stats{};
 };
 
@@ -110,6 +137,11 @@ static PlanKey key_of(const srv_request &r)
     k.prec = r.kind == SRV_LS ? r.precision : r.precision;
     k.io = r.kind == SRV_LS ? CONV_IO_C2C + 100 : r.io;  // LS plans are cached apart from conv plans
     return k;
+}
+
+static ShapeKey shape_of(const srv_request &r)
+{
+    return ShapeKey{r.n, r.period_num, r.period_den, r.precision, r.io};
 }
 
 // Bytes of one LS solve's Krylov basis and vectors.
@@ -197,11 +229,10 @@ static bool make_room(srv_t s, size_t need)
     return true;
 }
 
-static std::shared_ptr<CachedPlan> get_plan(srv_t s, const srv_request &r, int &status)
+// Builds the plan of request r (no lock held); nullptr with the status on failure.
+static std::shared_ptr<CachedPlan> build_plan(srv_t s, const srv_request &r, int &status)
 {
-    PlanKey k = key_of(r);
-    auto it = s->plans.find(k);
-    if (it != s->plans.end()) return it->second;
+    cudaSetDevice(s->device);
     auto cp = std::make_shared<CachedPlan>();
     const conv_io io = r.kind == SRV_LS ? CONV_IO_C2C : (conv_io)r.io;
     status = conv_plan_ex(&r.kernel, r.period_num, r.period_den, r.n, 0.0, (conv_precision)r.precision, io,
@@ -219,15 +250,14 @@ static std::shared_ptr<CachedPlan> get_plan(srv_t s, const srv_request &r, int &
         if (cudaMalloc(&cp->stage_in, in_b * s->batch_max) != cudaSuccess ||
             cudaMalloc(&cp->stage_out, out_b * s->batch_max) != cudaSuccess) {
             cudaGetLastError();
+            cudaFree(cp->stage_in);
+            cudaStreamDestroy(cp->stream);
             conv_destroy(cp->plan);
             status = fail(CONV_ENOMEM, "serving staging buffers");
             return nullptr;
         }
         cp->bytes += (in_b + out_b) * s->batch_max;
     }
-    s->in_use += cp->bytes;
-    s->plans[k] = cp;
-    s->stats.plans_built++;
     return cp;
 }
 
@@ -242,7 +272,8 @@ static size_t out_bytes(const srv_request &r)
     return (size_t)r.n * r.n * (r.io == CONV_IO_R2R ? e : 2 * e);
 }
 
-// Launch one batch of same-plan convolution requests on the plan's stream.  Caller holds s->mu.
+// Launch one batch of same-shape convolution requests on the leading plan's stream.  Caller holds
+// s->mu.
 static void launch_batch(srv_t s, Batch &bt)
 {
     auto &cp = bt.cp;
@@ -254,9 +285,12 @@ static void launch_batch(srv_t s, Batch &bt)
         st = conv_apply(cp->plan, r0.in, r0.mask, r0.out, 1, nullptr, cp->stream);
     } else {
         const size_t ib = in_bytes(r0), ob = out_bytes(r0);
-        for (int i = 0; i < B; ++i)
+        conv_plan_t plans[WSC_MAX_SEL];
+        for (int i = 0; i < B; ++i) {
+            plans[i] = bt.reqs[i]->cp->plan;
             cudaMemcpyAsync((char *)cp->stage_in + i * ib, bt.reqs[i]->r.in, ib, cudaMemcpyDeviceToDevice, cp->stream);
-        st = conv_apply(cp->plan, cp->stage_in, r0.mask, cp->stage_out, B, nullptr, cp->stream);
+        }
+        st = conv_apply_kernels(cp->plan, plans, cp->stage_in, r0.mask, cp->stage_out, B, nullptr, cp->stream);
         for (int i = 0; i < B; ++i)
             cudaMemcpyAsync(bt.reqs[i]->r.out, (char *)cp->stage_out + i * ob, ob, cudaMemcpyDeviceToDevice, cp->stream);
     }
@@ -273,8 +307,23 @@ static void launch_batch(srv_t s, Batch &bt)
         q->res.batched_with = B;
         q->res.status = st;
     }
+    s->shape_inflight[bt.shape]++;
     s->stats.batches++;
     s->stats.batched_requests += B;
+}
+
+// An admitted request whose plan is resident: conv requests join their shape's ready queue, LS
+// solves the workers' queue.  Caller holds s->mu.
+static void route(srv_t s, const std::shared_ptr<Req> &q, const std::shared_ptr<CachedPlan> &cp)
+{
+    q->cp = cp;
+    cp->users++;
+    if (q->r.kind == SRV_LS) {
+        s->ls_queue.push_back(q);
+        s->cv_ls.notify_one();
+    } else {
+        s->ready[shape_of(q->r)].push_back(q);
+    }
 }
 
 static void dispatcher_loop(srv_t s)
@@ -283,17 +332,19 @@ static void dispatcher_loop(srv_t s)
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
         // admission: first fit in arrival order
-        std::vector<std::shared_ptr<Req>> admitted;
         for (auto it = s->pending.begin(); it != s->pending.end();) {
             auto q = *it;
             if (s->inflight_reqs >= s->max_inflight) break;
-            PlanKey k = key_of(q->r);
+            const PlanKey k = key_of(q->r);
             const auto pit = s->plans.find(k);
-            const bool have = pit != s->plans.end();
+            const auto bit = s->building.find(k);
+            const bool have = pit != s->plans.end(), queued = bit != s->building.end();
             // an LS solve on an idle plan uses the Krylov workspace the plan keeps (counted in its
             // bytes); one beside another solve on the same plan allocates its own
-            const size_t extra = (have && pit->second->users > 0) ? request_bytes(q->r) : 0;
-            const size_t need = extra + (have ? 0 : plan_bytes_estimate(q->r, s->batch_max, s->plan_flags));
+            const bool shares = (have && pit->second->users > 0) || (queued && !bit->second.waiters.empty());
+            const size_t extra = shares ? request_bytes(q->r) : 0;
+            const size_t plan_need = (have || queued) ? 0 : plan_bytes_estimate(q->r, s->batch_max, s->plan_flags);
+            const size_t need = extra + plan_need;
             if (need > s->budget) {  // can never fit
                 it = s->pending.erase(it);
                 q->admitted = true;
@@ -307,48 +358,80 @@ static void dispatcher_loop(srv_t s)
                 ++it;
                 continue;
             }
-            int status = CONV_OK;
-            auto cp = get_plan(s, q->r, status);
             it = s->pending.erase(it);
             q->admitted = true;
             s->inflight_reqs++;
-            if (!cp) {
-                q->need = 0;
-                finish(s, q, status, now_s());
-                s->cv_done.notify_all();
-                continue;
+            q->need = extra;
+            s->in_use += need;
+            if (have) {
+                route(s, q, pit->second);
+            } else if (queued) {
+                bit->second.waiters.push_back(q);
+            } else {
+                BuildJob &job = s->building[k];
+                job.r = q->r;
+                job.reserved = plan_need;
+                job.waiters.push_back(q);
+                s->build_queue.push_back(k);
+                s->cv_build.notify_one();
             }
-            q->cp = cp;
-            q->need = cp->users > 0 ? request_bytes(q->r) : 0;
-            cp->users++;
-            s->in_use += q->need;
-            admitted.push_back(q);
         }
-        // group admitted convolutions by plan; hand LS solves to the workers
-        std::map<CachedPlan *, Batch> groups;
-        for (auto &q : admitted) {
-            if (q->r.kind == SRV_LS) {
-                s->ls_queue.push_back(q);
-                s->cv_ls.notify_one();
-                continue;
-            }
-            Batch &bt = groups[q->cp.get()];
-            bt.cp = q->cp;
-            // masks are per batch: start a new batch when the mask differs or the batch is full
-            if (!bt.reqs.empty() && (bt.reqs[0]->r.mask != q->r.mask || (int)bt.reqs.size() >= s->batch_max)) {
+        // launch: a shape's ready requests go as one batch when nothing of that shape is on the GPU
+        // or a full batch is waiting; a batch shares one mask
+        for (auto &kv : s->ready) {
+            auto &dq = kv.second;
+            while (!dq.empty() && (s->shape_inflight[kv.first] == 0 || (int)dq.size() >= s->batch_max)) {
+                Batch bt;
+                bt.shape = kv.first;
+                bt.cp = dq.front()->cp;
+                const void *mask = dq.front()->r.mask;
+                for (auto qi = dq.begin(); qi != dq.end() && (int)bt.reqs.size() < s->batch_max;) {
+                    if ((*qi)->r.mask == mask) {
+                        bt.reqs.push_back(*qi);
+                        qi = dq.erase(qi);
+                    } else {
+                        ++qi;
+                    }
+                }
                 launch_batch(s, bt);
                 s->inflight.push_back(bt);
-                bt = Batch();
-                bt.cp = q->cp;
             }
-            bt.reqs.push_back(q);
         }
-        for (auto &g : groups)
-            if (!g.second.reqs.empty()) {
-                launch_batch(s, g.second);
-                s->inflight.push_back(g.second);
-            }
         s->cv_dispatch.wait_for(lk, std::chrono::microseconds(200));
+    }
+}
+
+// Builder: takes a plan key from the queue, builds the plan without the lock, then makes it
+// resident and routes the requests that waited for it (or fails them with the build's status).
+static void builder_loop(srv_t s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        s->cv_build.wait(lk, [&] { return s->stop || !s->build_queue.empty(); });
+        if (s->build_queue.empty()) break;
+        const PlanKey k = s->build_queue.front();
+        s->build_queue.pop_front();
+        const srv_request r = s->building[k].r;
+        lk.unlock();
+        int status = CONV_OK;
+        auto cp = build_plan(s, r, status);
+        lk.lock();
+        BuildJob job = std::move(s->building[k]);
+        s->building.erase(k);
+        if (cp) {
+            s->in_use += cp->bytes;
+            s->in_use -= job.reserved;
+            s->plans[k] = cp;
+            s->stats.plans_built++;
+            for (auto &q : job.waiters) route(s, q, cp);
+        } else {
+            s->in_use -= job.reserved;
+            const double t = now_s();
+            for (auto &q : job.waiters) finish(s, q, status, t);
+            s->cv_done.notify_all();
+        }
+        s->cv_dispatch.notify_one();
     }
 }
 
@@ -380,6 +463,7 @@ static void completer_loop(srv_t s)
                     s->free_pins.push_back(bt.pin);
                 }
                 for (auto &q : bt.reqs) finish(s, q, q->res.status, t);
+                s->shape_inflight[bt.shape]--;
             }
             if (!done.empty()) {
                 s->cv_done.notify_all();
@@ -452,6 +536,7 @@ conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch
     s->dispatcher = std::thread(dispatcher_loop, s);
     s->completer = std::thread(completer_loop, s);
     for (int i = 0; i < ls_workers; ++i) s->workers.emplace_back(ls_worker, s);
+    for (int i = 0; i < 2; ++i) s->builders.emplace_back(builder_loop, s);
     *out = s;
     return CONV_OK;
 }
@@ -543,6 +628,8 @@ void srv_destroy(srv_t s)
     }
     s->cv_dispatch.notify_all();
     s->cv_ls.notify_all();
+    s->cv_build.notify_all();
+    for (auto &b : s->builders) b.join();
     s->dispatcher.join();
     for (auto &w : s->workers) w.join();
     s->completer.join();

@@ -13,6 +13,7 @@
 struct conv_plan_s;
 namespace wsc {
 struct LsCache;
+struct LongLines;
 }
 
 namespace wsc {
@@ -57,6 +58,12 @@ template <typename T, int E, int ED, bool TWS> int blocks_per_sm_fused(int threa
 // row passes' strided spectrum accesses (R2R and split R2C: pass 1 stores, pass 3 loads).
 enum { CFG_TWS = 1, CFG_PF = 2, CFG_ONE = 4, CFG_TMA = 8, CFG_DEFAULT = -1 };
 
+// panel quadratures of the moment tables (ghat.cu, moments.cu): Clenshaw-Curtis rules of CC_N + 1 points
+#define CC_N 16
+
+// densities of a conv_apply_kernels batch (each its own multiplier, passed in the kernel parameters)
+#define WSC_MAX_SEL 32
+
 // rows (k2 values) per TMA box
 #define TMA_ROWS 256
 // tma.cu
@@ -90,12 +97,18 @@ struct conv_plan_s {
     conv_io io;
     int batch_max;
     bool complex_ghat;
+    conv_moments moments{};  // how ghat is computed (closed forms by default)
     bool r2c_split = false;  // R2C with complex ghat on the split pipeline (fused passes)
     int device;
     cudaStream_t setup_stream = nullptr;  // private stream for plan-time device work
     int elems;  // complex elements per thread in the transform kernels
     bool tws;   // twiddle table staged in shared memory
     bool fused; // passes on the fused transform (global-memory first/last stages)
+    bool long_lines = false;                 // lines beyond one CTA: four-step FP64 pipeline (fsmask.cu)
+    wsc::LongLines *longl = nullptr;
+    // conv_apply_kernels: for the duration of one launch, each density's multiplier table
+    int nsel = 0;
+    const void *sel[WSC_MAX_SEL] = {};
     int ed = 0; // fused: 16 * first radix + last radix
     wsc::FFTDesc fft;
     wsc::FFTDesc *fft_dev = nullptr;  // device copy read by the pass kernels
@@ -144,11 +157,21 @@ conv_status select_transform(conv_plan_s *p);
 // ghat.cu
 conv_status build_ghat(conv_plan_s *p);
 conv_status copy_ghat(conv_plan_s *p, const conv_plan_s *src);  // src's FP64 tables, no recomputation
+// moments.cu: the Sec. 2.3 quadrature or localized moments into the plan's moment quadrant
+conv_status build_moments_numeric(conv_plan_s *p, double scale, double *table, cudaStream_t st);
+void bessel_k01_host(double x, double *k0, double *k1);
 // plan.cu: the FP64 C2C twin of an FP32 plan (refinement residuals), tables copied from it
 conv_status conv_plan_twin(const conv_plan_s *p, conv_plan_s **twin);
 size_t spectrum_elems(const conv_plan_s *p);  // complex elements of the workspace per density
 void destroy_hostpipe(conv_plan_s *p);          // host_io.cu (both host pipelines)
 void destroy_ls_cache(conv_plan_s *p);          // ls.cu
 void noalloc_lookup(conv_plan_s *p);
+// fsmask.cu: the pipeline for transform lines beyond one CTA
+conv_status long_lines_init(conv_plan_s *p);
+void long_lines_destroy(conv_plan_s *p);
+size_t long_lines_ws_bytes(const conv_plan_s *p);
+conv_status long_lines_apply(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
+                             double aim, double beta, void *ws, cudaStream_t st);
+size_t workspace_bytes(const conv_plan_s *p, int batch);  // plan.cu: conv_workspace_size
 bool fault_take(int kind);                      // plan.cu: consume one armed injected fault            // noalloc.cu: address of the fixed scratch array
 }  // namespace wsc

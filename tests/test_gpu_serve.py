@@ -109,3 +109,31 @@ def test_cached_ls_plans_count_their_krylov_workspace():
         assert basis <= st["bytes_in_use"] <= budget, st
         assert st["plans_evicted"] == i, st
     srv.close()
+
+
+def test_same_shape_requests_on_different_kernels_share_a_batch():
+    """Convolutions of one transform shape (n, period, precision, io) on different kernels queue
+    together while a batch of their shape runs, and go as one launch per pass with each density's
+    own multiplier: fewer batches than requests, each result bitwise its own apply alone."""
+    n = 256
+    srv = Server(mem_budget_bytes=8 << 30, max_inflight=64, conv_batch_max=16, ls_workers=1, compact=True)
+    kinds = [("log", {"scale": -1.0}), ("pow", {"gamma": -0.5}), ("pow", {"gamma": -1.0}), ("pow", {"gamma": -1.5})]
+    reqs = []
+    for i in range(24):
+        kernel, kw = kinds[i % 4]
+        u = torch.tensor(inputs.bump_sums(n, 1, seed=500 + i)[0], dtype=torch.float32, device="cuda")
+        reqs.append((kernel, kw, u, torch.empty_like(u)))
+    # warm the four plans so that every request below finds its plan resident
+    for kernel, kw, u, out in reqs[:4]:
+        srv.wait(srv.submit_conv(u, out, kernel=kernel, precision="fp32", **kw), timeout_s=120)
+    before = srv.stats()
+    tickets = [srv.submit_conv(u, out, kernel=kernel, precision="fp32", **kw) for kernel, kw, u, out in reqs]
+    res = [srv.wait(t, timeout_s=120) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == "CONV_OK" for r in res)
+    batches = st["batches"] - before["batches"]
+    assert batches < len(reqs), (batches, st)
+    assert max(r["batched_with"] for r in res) > 1
+    for kernel, kw, u, out in reqs:
+        assert torch.equal(_conv_alone(n, kernel, kw, "fp32", "r2r", u, True), out), kernel
