@@ -282,6 +282,8 @@ typedef struct {
                           * time (2^l with n = L/2, or 3 2^l with n = L/3), else 0 */
     int long_lines;      /* 1: transform lines exceed one CTA (n = 8192 in FP64, or on the
                             period-3 grid): the passes run as four-step FP64 line transforms */
+    int cols_pingpong;   /* 1: the R2R column pass holds two buffers per line and alternates
+                            between them stage by stage (one barrier per stage) */
 } conv_plan_info;
 
 conv_status conv_get_info(conv_plan_t plan, conv_plan_info *info);

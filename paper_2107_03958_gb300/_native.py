@@ -31,7 +31,8 @@ class ConvPlanInfo(ctypes.Structure):
                 ("groups_cols", ctypes.c_int), ("transform_len", ctypes.c_int),
                 ("compact", ctypes.c_int), ("elems", ctypes.c_int), ("smem_twiddles", ctypes.c_int),
                 ("fused", ctypes.c_int), ("static_log2", ctypes.c_int), ("r2c_split", ctypes.c_int),
-                ("static_len", ctypes.c_int), ("long_lines", ctypes.c_int)]
+                ("static_len", ctypes.c_int), ("long_lines", ctypes.c_int),
+                ("cols_pingpong", ctypes.c_int)]
 
 
 class LsOpts(ctypes.Structure):

@@ -50,6 +50,12 @@ struct FFTDesc {
     unsigned long long mag[WSC_MAX_STAGES];  // ceil(2^40 / Ns): j / Ns == (j * mag) >> 40 for j < 2^24, Ns < 2^16
 };
 
+// Compile-time lengths whose shared-memory twiddle table holds every stage's blocks but the last
+// stage's: FP64 L = 2^13, whose full table (131 KB) does not fit beside the 139 KB line; the last,
+// radix-2 stage (one power per butterfly) reads the global table.
+__host__ __device__ constexpr bool tw_split_ed(int ed, int elem_bytes) { return elem_bytes == 8 && ed == 1013; }
+template <typename T, int ED> __host__ __device__ constexpr bool tw_split_ok() { return tw_split_ed(ED, (int)sizeof(T)); }
+
 // ---------------------------------------------------------------- small DFTs
 template <bool INV, typename V> __device__ __forceinline__ void dft2(V *x) {
     V a = x[0], b = x[1];

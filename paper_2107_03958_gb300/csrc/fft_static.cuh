@@ -18,6 +18,12 @@
 // The runtime path recomputes these per element (shifts, magic-number divisions, stage-table
 // loads); here each stage computes a handful of per-thread bases and the rest folds into the
 // load/store immediates.
+//
+// Ping-pong (PP): with two transform buffers per line, stage s reads X_s and writes X_{s+1}
+// (X_even = b0, X_odd = b1), so no thread can overwrite an input another thread has yet to read
+// and each stage needs one barrier (after its stores) instead of two; the warps of a stage then
+// overlap one another's loads, arithmetic and stores.  Without it b0 = b1 and every stage waits
+// once after its loads and once after its stores.
 #pragma once
 #include "fft_fused.cuh"
 
@@ -55,9 +61,10 @@ template <int ED, bool FULL16 = false> struct StaticStages {
 // only the inputs below n and runs a butterfly with the others fixed at zero.
 // HOUT: only outputs o < n are used (the crop): the last stage stores only p < R/2 (n = L/2) or
 // p = 0 (n = L/3, the last radix is 3), and the arithmetic feeding the rest drops out.
-template <typename T, int E, int ED, int S, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst>
-__device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw, int lt,
-                                       const Src &src, const Dst &dst)
+template <typename T, int E, int ED, int S, bool INV, bool TWS, bool HIN, bool HOUT, bool PP, class Src, class Dst>
+__device__ __forceinline__ void sstage(const typename cvec<T>::t *bin, typename cvec<T>::t *buf,
+                                       const typename cvec<T>::t *__restrict__ tw, int lt, const Src &src,
+                                       const Dst &dst)
 {
     typedef typename cvec<T>::t V;
     typedef StaticStages<ED, sizeof(T) == 8> P;  // FP64 tables hold all fifteen radix-16 powers
@@ -105,11 +112,11 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
         for (int q = 0; q < R; ++q) {
             const int c = b * TPT + q * NBF;
             if (pin && c >= NIN) v[b][q] = cmk<V>(0, 0);
-            else if constexpr (SRC_SMEM) v[b][q] = buf[pl + c + (c >> PS)];
+            else if constexpr (SRC_SMEM) v[b][q] = bin[pl + c + (c >> PS)];
             else v[b][q] = src(lt + c);
         }
     }
-    if constexpr (SRC_SMEM && DST_SMEM) __syncthreads();
+    if constexpr (SRC_SMEM && DST_SMEM && !PP) __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int cb = b * TPT, ck = cb & (Ns - 1), cj = cb >> lNs;
@@ -139,34 +146,52 @@ __device__ __forceinline__ void sstage(typename cvec<T>::t *buf, const typename 
     if constexpr (DST_SMEM) __syncthreads();
 }
 
-template <typename T, int E, int ED, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst, class After0, int S>
-__device__ __forceinline__ void fft_static_from(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw,
-                                                int lt, const Src &src, const Dst &dst, const After0 &after0)
+template <typename T, int E, int ED, bool INV, bool TWS, bool HIN, bool HOUT, bool PP, class Src, class Dst, class After0,
+          int S>
+__device__ __forceinline__ void fft_static_from(typename cvec<T>::t *b0, typename cvec<T>::t *b1,
+                                                const typename cvec<T>::t *__restrict__ tw,
+                                                const typename cvec<T>::t *__restrict__ twg, int lt, const Src &src,
+                                                const Dst &dst, const After0 &after0)
 {
     constexpr int NST = StaticStages<ED>::NST;
     static_assert(NST >= 2, "at least two stages");
+    // stage S reads X_S and writes X_{S+1}
+    typename cvec<T>::t *bin = (S & 1) ? b1 : b0, *bout = (S & 1) ? b0 : b1;
+    // a table split between shared and global memory: the last stage reads the global one
+    constexpr bool GLOBAL_TW = TWS && S == NST - 1 && tw_split_ok<T, ED>();
+    constexpr bool TWS_S = TWS && !GLOBAL_TW;
+    const typename cvec<T>::t *tws = GLOBAL_TW ? twg : tw;
     // keep each stage's per-thread bases from being hoisted to the kernel start (register pressure)
     int lt_ = lt;
     asm volatile("" : "+r"(lt_));
     if constexpr (S == 0) {
-        sstage<T, E, ED, 0, INV, TWS, HIN, HOUT>(buf, tw, lt_, src, ToSmem{});
+        sstage<T, E, ED, 0, INV, TWS_S, HIN, HOUT, PP>(bin, bout, tws, lt_, src, ToSmem{});
         after0();
     } else if constexpr (S == NST - 1) {
-        sstage<T, E, ED, S, INV, TWS, HIN, HOUT>(buf, tw, lt_, FromSmem{}, dst);
+        sstage<T, E, ED, S, INV, TWS_S, HIN, HOUT, PP>(bin, bout, tws, lt_, FromSmem{}, dst);
     } else {
-        sstage<T, E, ED, S, INV, TWS, HIN, HOUT>(buf, tw, lt_, FromSmem{}, ToSmem{});
+        sstage<T, E, ED, S, INV, TWS_S, HIN, HOUT, PP>(bin, bout, tws, lt_, FromSmem{}, ToSmem{});
     }
     if constexpr (S + 1 < NST)
-        fft_static_from<T, E, ED, INV, TWS, HIN, HOUT, Src, Dst, After0, S + 1>(buf, tw, lt, src, dst, after0);
+        fft_static_from<T, E, ED, INV, TWS, HIN, HOUT, PP, Src, Dst, After0, S + 1>(b0, b1, tw, twg, lt, src, dst,
+                                                                                   after0);
 }
 
-// Whole transform of compile-time length ED; same contract as fft_fused.
-template <typename T, int E, int ED, bool INV, bool TWS, bool HIN, bool HOUT, class Src, class Dst, class After0>
-__device__ __forceinline__ void fft_static(typename cvec<T>::t *buf, const typename cvec<T>::t *__restrict__ tw, int lt,
-                                           const Src &src, const Dst &dst, const After0 &after0)
+// Whole transform of compile-time length ED; same contract as fft_fused.  Shared-memory inputs
+// (FromSmem) are read from b0; shared-memory outputs end in X_NST (final_buf).  b1 = b0 without PP.
+// tw: the twiddle table (shared memory with TWS); twg: the global table, which the last stage
+// reads when the shared copy holds only the earlier stages' blocks (tw_split_ok).
+template <typename T, int E, int ED, bool INV, bool TWS, bool HIN, bool HOUT, bool PP, class Src, class Dst, class After0>
+__device__ __forceinline__ void fft_static(typename cvec<T>::t *b0, typename cvec<T>::t *b1,
+                                           const typename cvec<T>::t *__restrict__ tw,
+                                           const typename cvec<T>::t *__restrict__ twg, int lt, const Src &src,
+                                           const Dst &dst, const After0 &after0)
 {
-    fft_static_from<T, E, ED, INV, TWS, HIN, HOUT, Src, Dst, After0, 0>(buf, tw, lt, src, dst, after0);
+    fft_static_from<T, E, ED, INV, TWS, HIN, HOUT, PP, Src, Dst, After0, 0>(b0, b1, tw, twg, lt, src, dst, after0);
 }
+
+// The buffer holding a compile-time transform's shared-memory outputs, X_NST, and the other one.
+template <int ED> __device__ __forceinline__ bool final_in_b1() { return ED >= 1000 && (StaticStages<ED>::NST & 1); }
 
 // The pass kernels' transform: ED >= 1000 selects the static path for length 2^(ED - 1000) or
 // 3 2^(ED - 2000) (which the host picks only for n = L/2 or n = L/3 respectively, so HIN and HOUT
@@ -175,11 +200,25 @@ __device__ __forceinline__ void fft_static(typename cvec<T>::t *buf, const typen
 template <typename T, int E, int ED, bool INV, bool TWS, bool HIN = false, bool HOUT = false, class Src, class Dst,
           class After0 = NoHook>
 __device__ __forceinline__ void fft_any(typename cvec<T>::t *buf, const FFTDesc *__restrict__ P,
-                                        const typename cvec<T>::t *__restrict__ tw, int lt, int tpt, const Src &src,
+                                        const typename cvec<T>::t *__restrict__ tw,
+                                        const typename cvec<T>::t *__restrict__ twg, int lt, int tpt, const Src &src,
                                         const Dst &dst, const After0 &after0 = After0{})
 {
-    if constexpr (ED >= 1000) fft_static<T, E, ED, INV, TWS, HIN, HOUT>(buf, tw, lt, src, dst, after0);
+    if constexpr (ED >= 1000) fft_static<T, E, ED, INV, TWS, HIN, HOUT, false>(buf, buf, tw, twg, lt, src, dst, after0);
     else fft_fused<T, E, ED, INV, TWS>(buf, P, tw, lt, tpt, src, dst, after0);
+}
+
+// fft_any with a second buffer: the compile-time lengths ping-pong between b0 and b1 when PP is
+// set (outputs in X_NST, see final_in_b1); the runtime path uses b0 alone.
+template <typename T, int E, int ED, bool INV, bool TWS, bool HIN, bool HOUT, bool PP, class Src, class Dst,
+          class After0 = NoHook>
+__device__ __forceinline__ void fft_any2(typename cvec<T>::t *b0, typename cvec<T>::t *b1, const FFTDesc *__restrict__ P,
+                                         const typename cvec<T>::t *__restrict__ tw,
+                                         const typename cvec<T>::t *__restrict__ twg, int lt, int tpt, const Src &src,
+                                         const Dst &dst, const After0 &after0 = After0{})
+{
+    if constexpr (ED >= 1000) fft_static<T, E, ED, INV, TWS, HIN, HOUT, PP>(b0, PP ? b1 : b0, tw, twg, lt, src, dst, after0);
+    else fft_fused<T, E, ED, INV, TWS>(b0, P, tw, lt, tpt, src, dst, after0);
 }
 
 // Transform length of the compile-time path (0 for the runtime path).

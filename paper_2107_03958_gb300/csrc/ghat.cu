@@ -188,14 +188,14 @@ conv_status copy_ghat(conv_plan_s *p, const conv_plan_s *src)
 {
     cudaStream_t st = p->setup_stream;
     p->ghat_bytes = src->ghat_bytes;
-    if (cudaMalloc(&p->ghat_paper, p->ghat_bytes) != cudaSuccess) {
+    if (dev_alloc(&p->ghat_paper, p->ghat_bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(CONV_ENOMEM, "cudaMalloc of the moment table failed");
     }
     WSC_CUDA(cudaMemcpyAsync(p->ghat_paper, src->ghat_paper, p->ghat_bytes, cudaMemcpyDeviceToDevice, st));
     if (p->compact) {
         p->table_bytes = src->table_bytes;
-        if (cudaMalloc(&p->ghat64, p->table_bytes) != cudaSuccess) {
+        if (dev_alloc(&p->ghat64, p->table_bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the compact multiplier failed");
         }
@@ -206,7 +206,7 @@ conv_status copy_ghat(conv_plan_s *p, const conv_plan_s *src)
     }
     if (p->prec == CONV_P_FP32) {
         const long long NT = (long long)(p->table_bytes / sizeof(double));
-        if (cudaMalloc(&p->ghat32, (size_t)NT * sizeof(float)) != cudaSuccess) {
+        if (dev_alloc(&p->ghat32, (size_t)NT * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the FP32 multiplier failed");
         }
@@ -229,7 +229,7 @@ conv_status build_ghat(conv_plan_s *p)
     const long long N = (long long)hb * hb;
     const int comps = p->complex_ghat ? 2 : 1;
     p->ghat_bytes = (size_t)N * comps * sizeof(double);
-    if (cudaMalloc(&p->ghat_paper, p->ghat_bytes) != cudaSuccess) {
+    if (dev_alloc(&p->ghat_paper, p->ghat_bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(CONV_ENOMEM, "cudaMalloc of the moment table failed");
     }
@@ -283,7 +283,7 @@ conv_status build_ghat(conv_plan_s *p)
     if (p->compact) {
         const size_t nq = (size_t)(p->n + 1) * (p->n + 1) * comps;
         p->table_bytes = nq * sizeof(double);
-        if (cudaMalloc(&p->ghat64, p->table_bytes) != cudaSuccess) {
+        if (dev_alloc(&p->ghat64, p->table_bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the compact multiplier failed");
         }
@@ -295,7 +295,7 @@ conv_status build_ghat(conv_plan_s *p)
     }
     if (p->prec == CONV_P_FP32) {
         const long long NT = (long long)(p->table_bytes / sizeof(double));
-        if (cudaMalloc(&p->ghat32, (size_t)NT * sizeof(float)) != cudaSuccess) {
+        if (dev_alloc(&p->ghat32, (size_t)NT * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the FP32 multiplier failed");
         }

@@ -340,21 +340,21 @@ struct LsWork {
 static bool alloc_work(LsWork &W, long long N, long long NN, int batch, size_t cws, size_t cws64, int restart,
                        bool mixed)
 {
-    bool ok = cudaMalloc(&W.V, (size_t)(restart + 1) * N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&W.w, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&W.r, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&W.d, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&W.partial, (size_t)(restart + 1) * LS_RED_BLOCKS * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&W.gsbuf, gmres_state_elems(restart) * sizeof(double2)) == cudaSuccess &&
-              cudaMallocHost(&W.host_res, sizeof(double)) == cudaSuccess;
+    bool ok = dev_alloc(&W.V, (size_t)(restart + 1) * N * sizeof(double2)) == cudaSuccess &&
+              dev_alloc(&W.w, N * sizeof(double2)) == cudaSuccess &&
+              dev_alloc(&W.r, N * sizeof(double2)) == cudaSuccess &&
+              dev_alloc(&W.d, N * sizeof(double2)) == cudaSuccess &&
+              dev_alloc(&W.partial, (size_t)(restart + 1) * LS_RED_BLOCKS * sizeof(double2)) == cudaSuccess &&
+              dev_alloc(&W.gsbuf, gmres_state_elems(restart) * sizeof(double2)) == cudaSuccess &&
+              (W.host_res = pinned_slot()) != nullptr;
     if (ok && mixed)
-        ok = cudaMalloc(&W.x64, N * sizeof(double2)) == cudaSuccess &&
-             cudaMalloc(&W.v32, N * sizeof(float2)) == cudaSuccess &&
-             cudaMalloc(&W.w32, N * sizeof(float2)) == cudaSuccess &&
-             cudaMalloc(&W.m32, NN * sizeof(float)) == cudaSuccess;
-    if (ok && batch > 1) ok = cudaMalloc(&W.fsc, N * sizeof(double2)) == cudaSuccess;
-    if (ok && cws) ok = cudaMalloc(&W.cws, cws) == cudaSuccess;
-    if (ok && cws64) ok = cudaMalloc(&W.cws64, cws64) == cudaSuccess;
+        ok = dev_alloc(&W.x64, N * sizeof(double2)) == cudaSuccess &&
+             dev_alloc(&W.v32, N * sizeof(float2)) == cudaSuccess &&
+             dev_alloc(&W.w32, N * sizeof(float2)) == cudaSuccess &&
+             dev_alloc(&W.m32, NN * sizeof(float)) == cudaSuccess;
+    if (ok && batch > 1) ok = dev_alloc(&W.fsc, N * sizeof(double2)) == cudaSuccess;
+    if (ok && cws) ok = dev_alloc(&W.cws, cws) == cudaSuccess;
+    if (ok && cws64) ok = dev_alloc(&W.cws64, cws64) == cudaSuccess;
     if (!ok) cudaGetLastError();
     if (ok) W.gs = gmres_state_view(W.gsbuf, restart);
     return ok;
@@ -362,20 +362,20 @@ static bool alloc_work(LsWork &W, long long N, long long NN, int batch, size_t c
 
 static void free_work(LsWork &W)
 {
-    cudaFree(W.V);
-    cudaFree(W.w);
-    cudaFree(W.r);
-    cudaFree(W.d);
-    cudaFree(W.x64);
-    cudaFree(W.v32);
-    cudaFree(W.w32);
-    cudaFree(W.m32);
-    cudaFree(W.fsc);
-    cudaFree(W.cws);
-    cudaFree(W.cws64);
-    cudaFree(W.partial);
-    cudaFree(W.gsbuf);
-    if (W.host_res) cudaFreeHost(W.host_res);
+    dev_free(W.V);
+    dev_free(W.w);
+    dev_free(W.r);
+    dev_free(W.d);
+    dev_free(W.x64);
+    dev_free(W.v32);
+    dev_free(W.w32);
+    dev_free(W.m32);
+    dev_free(W.fsc);
+    dev_free(W.cws);
+    dev_free(W.cws64);
+    dev_free(W.partial);
+    dev_free(W.gsbuf);
+    pinned_slot_release(W.host_res);
     W = LsWork();
 }
 
@@ -408,7 +408,7 @@ void destroy_ls_cache(conv_plan_s *p)
     if (!p->ls_cache) return;
     drop_graphs(p->ls_cache);
     free_work(p->ls_cache->W);
-    cudaFree(p->ls_cache->m64);
+    dev_free(p->ls_cache->m64);
     if (p->ls_cache->cap) cudaStreamDestroy(p->ls_cache->cap);
     delete p->ls_cache;
     p->ls_cache = nullptr;
@@ -647,7 +647,7 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
             cudaStreamSynchronize(st);
             drop_graphs(cache);
             free_work(cache->W);
-            cudaFree(cache->m64);
+            dev_free(cache->m64);
             cache->m64 = nullptr;
         }
         if (!cache->W.V) {
@@ -662,7 +662,7 @@ static conv_status ls_solve_impl(conv_plan_t p, const double *m, const void *f, 
         }
         S.W = cache->W;
         if (!mixed) {  // the FP64 matvec reads the contrast from the plan's copy
-            if (!cache->m64 && cudaMalloc(&cache->m64, NN * sizeof(double)) != cudaSuccess) {
+            if (!cache->m64 && dev_alloc(&cache->m64, NN * sizeof(double)) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(CONV_ENOMEM, "ls_solve contrast buffer");
             }

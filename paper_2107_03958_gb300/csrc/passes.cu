@@ -440,7 +440,8 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         maxT = std::min(maxT, static_max_threads(ed));
         if (tpt > maxT) return false;
     }
-    const size_t twb = (size_t)d.tw_len * esz;
+    // twiddle bytes in shared memory (TWS): the whole table, or all but the last stage's blocks
+    const size_t twb = (size_t)(tw_split_ed(ed, (int)(esz / 2)) ? d.toff[d.nst - 1] : d.tw_len) * esz;
     // Staging per group (fused passes), by pass:
     //   pass 1: prefetched input rows (n elements V, rounded to 128 B), then with TMA stores the
     //           row pair's spectrum pairs, nbox x TMA_ROWS x 2 elements;
@@ -481,6 +482,7 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         const size_t sb = stage_bytes(pass, pairs, pf, tma);
         S.tpt = tpt;
         S.groups = G;
+        S.pp = false;
         S.tws = tws;
         S.pf = pf;
         S.tma = tma;
@@ -503,8 +505,27 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
     if (fused) {
         split = p->io == CONV_IO_R2C && p->complex_ghat && shape(opt[1], 1, false, 2, C);
         const bool pairs = p->io == CONV_IO_R2R || split;
-        if (!shape(opt[0], 0, pairs, 1, R) || (!split && !shape(opt[1], 1, false, 1, C)) ||
-            !shape(opt[2], 2, pairs, 1, I))
+        // the lengths with ping-pong kernels (R2R passes, and the split pipeline's pass 1): two
+        // buffers per group when that costs none of the pass's options or groups.  By default
+        // passes 1 and 2 (n = 4096, batch 16: pass 1 1.633 -> 1.595 ms, pass 2 3.221 -> 3.134 ms;
+        // pass 3 1.342 -> 1.404 ms, so not pass 3).  WSCONV_PP selects the passes (bits 1, 2, 4
+        // for passes 1, 2, 3; 0 turns it off).
+        const char *pp_env = getenv("WSCONV_PP");
+        const int pp_mask = pingpong_ed(ed, (int)(esz / 2)) ? (pp_env ? atoi(pp_env) : 3) : 0;
+        auto shape_pp = [&](int cfg, int pass, bool prs, LaunchShape &S) -> bool {
+            if (!shape(cfg, pass, prs, 1, S)) return false;
+            LaunchShape two;
+            if ((pp_mask >> pass) & 1 && shape(cfg, pass, prs, 2, two) && two.tws == S.tws && two.pf == S.pf &&
+                two.tma == S.tma && two.groups == S.groups) {
+                two.pp = true;
+                S = two;
+            }
+            return true;
+        };
+        const bool r2r = p->io == CONV_IO_R2R;
+        if (!(pairs ? shape_pp(opt[0], 0, pairs, R) : shape(opt[0], 0, pairs, 1, R)) ||
+            (!split && !(r2r ? shape_pp(opt[1], 1, false, C) : shape(opt[1], 1, false, 1, C))) ||
+            !(r2r ? shape_pp(opt[2], 2, pairs, I) : shape(opt[2], 2, pairs, 1, I)))
             return false;
     } else {
         if (!shape(opt[0], 0, false, 1, R)) return false;

@@ -20,7 +20,7 @@ template <typename T> struct PassArgs {
     const void *ghat;      // pass 2: moment quadrant [k2][k1] (T or complex V)
     const void *u;         // pass 3: u for the beta term
     const V *tw;           // per-stage twiddle blocks (FFTDesc), global
-    int tw_len;            // entries of the twiddle table
+    int tw_len;            // entries of the twiddle table (TWS: of its shared-memory copy)
     const FFTDesc *P;
     int n, h, M, tpt;
     int units;             // work items over the whole batch

@@ -104,15 +104,17 @@ __device__ __forceinline__ void store_pair(typename cvec<T>::t *p, typename cvec
 
 // Pass 1.  Staging: rows j1, j1 + 1 of u (adjacent in memory), n T each; one bulk copy
 // (a.pf requires n sizeof(T) to be a multiple of 16 and u 16-byte aligned).
-template <typename T, int E, int ED, bool TWS>
+template <typename T, int E, int ED, bool TWS, bool PP = false>
 __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
-    V *buf = setup_smem<T, TWS>(a, twp, g);
+    // PP: two buffers per group, the transform ping-pongs between them (fft_static.cuh)
+    V *buf = setup_smem<T, TWS>(a, twp, PP ? 2 * g : g);
+    V *buf2 = PP ? buf + padded_len<T>(a.M) : buf;
     unsigned long long *bar;
-    T *stg = reinterpret_cast<T *>(stage_area<T, TWS>(a, g, G, bar));
+    T *stg = reinterpret_cast<T *>(stage_area<T, TWS, PP ? 2 : 1>(a, g, G, bar));
     const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2, stride = gridDim.x * G;
     const bool pair_vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0;
     // TMA stores: the spectrum pairs (A_k, B_k) of the item, k < h, side by side in shared memory
@@ -154,7 +156,9 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const __grid_constant__ PassAr
             }
             return cmk<V>(x, y);
         };
-        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, ToSmem{}, [&]() { fetch(unit + stride); });
+        fft_any2<T, E, ED, false, TWS, pruned<ED>(), false, PP>(buf, buf2, a.P, twp, a.tw, lt, a.tpt, src, ToSmem{},
+                                                                [&]() { fetch(unit + stride); });
+        const V *spec = (PP && final_in_b1<ED>()) ? buf2 : buf;  // the spectrum Z
         if (a.tma) {
             // the previous item's stores have to have read the pairs before they are rewritten
             if (lt == 0) bulk_wait_read();
@@ -163,7 +167,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const __grid_constant__ PassAr
         if (valid) {
             V *Wb = reinterpret_cast<V *>(a.out) + (size_t)b * h * n;
             for (int k = lt; k < h; k += a.tpt) {
-                V Zk = buf[pidx<T>(k)], Zm = buf[pidx<T>(k == 0 ? 0 : M - k)];
+                V Zk = spec[pidx<T>(k)], Zm = spec[pidx<T>(k == 0 ? 0 : M - k)];
                 const V A = cmk<V>((T)0.5 * (Zk.x + Zm.x), (T)0.5 * (Zk.y - Zm.y));
                 const V B = cmk<V>((T)0.5 * (Zk.y + Zm.y), (T)-0.5 * (Zk.x - Zm.x));
                 if (a.tma) {
@@ -190,15 +194,17 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_fwd(const __grid_constant__ PassAr
 
 // Pass 2.  Staging: the column's n spectrum values (contiguous in W); one bulk copy (a.pf
 // requires n sizeof(V) to be a multiple of 16 and W 16-byte aligned).
-template <typename T, int E, int ED, bool TWS>
+template <typename T, int E, int ED, bool TWS, bool PP = false>
 __global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
-    V *buf = setup_smem<T, TWS>(a, twp, g);
+    // PP: two buffers per group, the transforms ping-pong between them (fft_static.cuh)
+    V *buf = setup_smem<T, TWS>(a, twp, PP ? 2 * g : g);
+    V *buf2 = PP ? buf + padded_len<T>(a.M) : buf;
     unsigned long long *bar;
-    V *stg = stage_area<T, TWS>(a, g, G, bar);
+    V *stg = stage_area<T, TWS, PP ? 2 : 1>(a, g, G, bar);
     const int n = a.n, M = a.M, h = a.h, stride = gridDim.x * G;
     const T *ghat = reinterpret_cast<const T *>(a.ghat);
     auto col_at = [&](int unit) -> V * {
@@ -230,26 +236,32 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const __grid_constant__ PassArgs<T
             const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             x = a.odd ? odd_mul(x, __ldg(&gc[k1]), o, Lm) : cscale(x, __ldg(&gc[k1]));
         });
-        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any2<T, E, ED, false, TWS, pruned<ED>(), false, PP>(buf, buf2, a.P, twp, a.tw, lt, a.tpt, src, mul,
+                                                                [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        // the inverse starts from the buffer the forward transform ended in
+        if (final_in_b1<ED>() && PP)
+            fft_any2<T, E, ED, true, TWS, false, pruned<ED>(), PP>(buf2, buf, a.P, twp, a.tw, lt, a.tpt, FromSmem{}, dst);
+        else
+            fft_any2<T, E, ED, true, TWS, false, pruned<ED>(), PP>(buf, buf2, a.P, twp, a.tw, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
 
 // Pass 3.  Staging: the row pair's spectra W[k][j1], W[k][j1+1] for k <= M/2, side by side;
 // gathered by cp.async (a.pf requires W 16-byte aligned and, in FP32, n even).
-template <typename T, int E, int ED, bool TWS>
+template <typename T, int E, int ED, bool TWS, bool PP = false>
 __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
-    V *buf = setup_smem<T, TWS>(a, twp, g);
+    V *buf = setup_smem<T, TWS>(a, twp, PP ? 2 * g : g);
+    V *buf2 = PP ? buf + padded_len<T>(a.M) : buf;
     unsigned long long *bar;
-    V *stg = stage_area<T, TWS>(a, g, G, bar);
+    V *stg = stage_area<T, TWS, PP ? 2 : 1>(a, g, G, bar);
     const int n = a.n, M = a.M, h = a.h, pairs = (n + 1) / 2, stride = gridDim.x * G;
     const bool pair_vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
     const T alpha = a.alpha.x, beta = a.beta;
@@ -328,7 +340,8 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const __grid_constant__ PassAr
             oa[o] = ra;
             if (has2) oa[n + o] = rb;
         };
-        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any2<T, E, ED, true, TWS, false, pruned<ED>(), PP>(buf, buf2, a.P, twp, a.tw, lt, a.tpt, src, dst,
+                                                               [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -390,8 +403,8 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T
             bim[pidx<T>(o)] = cscale(x, gk.y);
             x = cscale(x, gk.x);
         });
-        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(bre, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
-        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bre, a.P, twp, lt, a.tpt, FromSmem{}, ToSmem{});
+        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(bre, a.P, twp, a.tw, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bre, a.P, twp, a.tw, lt, a.tpt, FromSmem{}, ToSmem{});
         V *cout = reinterpret_cast<V *>(a.out) + 2 * co;
         auto dst = [&](int o, V xi) {
             if (!valid || o >= n) return;
@@ -405,7 +418,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T
             cout[2 * o] = xr;
             cout[2 * o + 1] = xi;
         };
-        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bim, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bim, a.P, twp, a.tw, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -485,7 +498,7 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_rows_inv(const __grid_constant__ PassAr
             if (a.beta != (T)0) z.x += a.beta * ua[o];
             o_[o] = z;
         };
-        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, a.tw, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -536,7 +549,7 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_rows_fwd(const __grid_constant__ PassAr
         auto dst = [&](int o, V z) {
             if (valid) Wb[(size_t)o * n + j1] = z;
         };
-        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, a.tw, lt, a.tpt, src, dst, [&]() { fetch(unit + stride); });
         __syncthreads();
     }
 }
@@ -583,11 +596,11 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_cols(const __grid_constant__ PassArgs<T
             if (CG) x = cmul(x, __ldg(reinterpret_cast<const V *>(gq) + (size_t)k2q * h + k1));
             else x = cscale(x, __ldg(reinterpret_cast<const T *>(gq) + (size_t)k2q * h + k1));
         });
-        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
+        fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(buf, a.P, twp, a.tw, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
         auto dst = [&](int o, V x) {
             if (valid && o < n) col[o] = x;
         };
-        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, FromSmem{}, dst);
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, a.tw, lt, a.tpt, FromSmem{}, dst);
         __syncthreads();
     }
 }
@@ -639,7 +652,7 @@ __global__ void WSC_LBF(T, E, ED) kf_c2c_rows_inv(const __grid_constant__ PassAr
             }
             o_[o] = z;
         };
-        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(buf, a.P, twp, a.tw, lt, a.tpt, src, dst, [&]() { gather(unit + stride); });
         __syncthreads();
     }
     if (a.pf) cp_async_wait_all();
@@ -652,6 +665,11 @@ template <typename T, int E, int ED, bool TWS> conv_status set_attrs_fused(int s
     WSC_ATTR((kf_r2r_rows_fwd<T, E, ED, TWS>));
     WSC_ATTR((kf_r2r_cols<T, E, ED, TWS>));
     WSC_ATTR((kf_r2r_rows_inv<T, E, ED, TWS>));
+    if constexpr (pingpong_ok<T, ED>()) {
+        WSC_ATTR((kf_r2r_rows_fwd<T, E, ED, TWS, true>));
+        WSC_ATTR((kf_r2r_cols<T, E, ED, TWS, true>));
+        WSC_ATTR((kf_r2r_rows_inv<T, E, ED, TWS, true>));
+    }
     WSC_ATTR((kf_r2c_cols<T, E, ED, TWS>));
     WSC_ATTR((kf_r2c_rows_inv<T, E, ED, TWS>));
     WSC_ATTR((kf_c2c_rows_fwd<T, E, ED, TWS, true>));
@@ -692,7 +710,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
     a.ghat = p->prec == CONV_P_FP64 ? (const void *)p->ghat64 : p->ghat32;
     a.u = u;
     a.tw = reinterpret_cast<const V *>(p->tw);
-    a.tw_len = p->fft.tw_len;
+    a.tw_len = tw_split_ok<T, ED>() ? p->fft.toff[p->fft.nst - 1] : p->fft.tw_len;  // the shared-memory copy
     a.P = p->fft_dev;
     a.n = n;
     a.h = h;
@@ -729,6 +747,16 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         if ((S).tws) K<WSC_TARGS TA, true, X><<<grid(S, a.units), (S).tpt * (S).groups, (S).smem, st>>>(a); \
         else K<WSC_TARGS TA, false, X><<<grid(S, a.units), (S).tpt * (S).groups, (S).smem, st>>>(a);     \
     } while (0)
+    // kernels with a ping-pong variant: launched with it when the pass's shape holds two buffers
+#define WSC_LAUNCH_PP(S, K)                                      \
+    do {                                                         \
+        if constexpr (pingpong_ok<T, ED>()) {                    \
+            if ((S).pp) WSC_LAUNCH2(S, K, (T, E, ED), true);     \
+            else WSC_LAUNCH(S, K, (T, E, ED));                   \
+        } else {                                                 \
+            WSC_LAUNCH(S, K, (T, E, ED));                        \
+        }                                                        \
+    } while (0)
     cudaEvent_t *ev = timing_slot(p);
     if (ev) cudaEventRecord(ev[0], st);
     if (p->io == CONV_IO_R2R) {
@@ -739,7 +767,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.stage_len = R.stage;
         a.pf = R.pf && al(u, 16) && (n * sizeof(T)) % 16 == 0;
         tma_map(R, ws, n);
-        WSC_LAUNCH(R, kf_r2r_rows_fwd, (T, E, ED));
+        WSC_LAUNCH_PP(R, kf_r2r_rows_fwd);
         if (ev) cudaEventRecord(ev[1], st);
         a.tpt = C.tpt;
         a.in = ws;
@@ -747,7 +775,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.stage_len = C.stage;
         a.pf = pf_cols;
         a.tma = 0;
-        WSC_LAUNCH(C, kf_r2r_cols, (T, E, ED));
+        WSC_LAUNCH_PP(C, kf_r2r_cols);
         if (ev) cudaEventRecord(ev[2], st);
         a.tpt = I.tpt;
         a.out = out;
@@ -756,7 +784,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.pf = I.pf && ws16 && (sizeof(T) == 8 || n % 2 == 0);
         if (a.pf) tma_map(I, ws, n);
         else a.tma = 0;
-        WSC_LAUNCH(I, kf_r2r_rows_inv, (T, E, ED));
+        WSC_LAUNCH_PP(I, kf_r2r_rows_inv);
     } else if (p->r2c_split) {
         a.tpt = R.tpt;
         a.in = u;
@@ -765,7 +793,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.stage_len = R.stage;
         a.pf = R.pf && al(u, 16) && (n * sizeof(T)) % 16 == 0;
         tma_map(R, ws, n);
-        WSC_LAUNCH(R, kf_r2r_rows_fwd, (T, E, ED));
+        WSC_LAUNCH_PP(R, kf_r2r_rows_fwd);
         if (ev) cudaEventRecord(ev[1], st);
         // W2 follows W on the next even element (the workspace holds batch (3 h n + 1) values)
         V *W2 = reinterpret_cast<V *>(ws) + (((size_t)batch * h * n + 1) & ~(size_t)1);
@@ -824,6 +852,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
             WSC_LAUNCH2(I, kf_c2c_rows_inv, (T, E, ED), false);
     }
     if (ev) cudaEventRecord(ev[3], st);
+#undef WSC_LAUNCH_PP
 #undef WSC_LAUNCH2
 #undef WSC_LAUNCH
 #undef WSC_TARGS

@@ -84,7 +84,7 @@ static conv_status upload_twiddles(conv_plan_s *p)
     stage_twiddles(p->fft, h);
     const bool f64 = p->prec == CONV_P_FP64;
     const size_t bytes = h.size() * (f64 ? sizeof(double) : sizeof(float));
-    if (cudaMalloc(&p->tw, bytes) != cudaSuccess) {
+    if (dev_alloc(&p->tw, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(CONV_ENOMEM, "cudaMalloc of the twiddle table failed");
     }
@@ -105,7 +105,7 @@ conv_status apply_candidate(conv_plan_s *p, const Candidate &c);
 // Re-upload the stage table and twiddles after the launch configuration changed.
 static conv_status reupload(conv_plan_s *p)
 {
-    if (p->tw) cudaFree(p->tw);
+    dev_free(p->tw);
     p->tw = nullptr;
     conv_status rc = upload_twiddles(p);
     if (rc != CONV_OK) return rc;
@@ -247,6 +247,40 @@ conv_status check_apply(conv_plan_s *p, const void *u, const void *mask, const v
     return CONV_OK;
 }
 
+// The plan's tables and workspace go back to the memory pool at once (dmem.cu), so with
+// wait_device = false the caller must know that no queued or running work uses the plan: the
+// serving runtime releases only plans whose requests have completed.  conv_destroy waits for the
+// device first, as a cudaFree would, and then trims the pool.
+void plan_release(conv_plan_s *p, bool wait_device)
+{
+    if (!p) return;
+    int cur = -1;
+    if (wait_device) {
+        cudaGetDevice(&cur);
+        if (cur != p->device) cudaSetDevice(p->device);
+        if (cudaDeviceSynchronize() != cudaSuccess) cudaGetLastError();
+    }
+    destroy_hostpipe(p);
+    destroy_ls_cache(p);
+    long_lines_destroy(p);
+    if (p->ghat64 != p->ghat_paper) dev_free(p->ghat64);
+    dev_free(p->ghat_paper);
+    dev_free(p->ghat32);
+    dev_free(p->tw);
+    dev_free(p->fft_dev);
+    if (p->setup_stream) cudaStreamDestroy(p->setup_stream);
+    dev_free(p->ws);
+    if (p->fp64_twin) plan_release(p->fp64_twin, false);
+    for (auto &v : {&p->tev_used, &p->tev_free})
+        for (auto &e : *v)
+            for (auto x : e) cudaEventDestroy(x);
+    if (wait_device) {
+        dev_pool_trim(p->device);
+        if (cur != p->device) cudaSetDevice(cur);
+    }
+    delete p;
+}
+
 }  // namespace wsc
 
 using namespace wsc;
@@ -255,25 +289,7 @@ extern "C" {
 
 const char *conv_last_error(void) { return g_last_error.c_str(); }
 
-void conv_destroy(conv_plan_t p)
-{
-    if (!p) return;
-    destroy_hostpipe(p);
-    destroy_ls_cache(p);
-    long_lines_destroy(p);
-    if (p->ghat64 && p->ghat64 != p->ghat_paper) cudaFree(p->ghat64);
-    if (p->ghat_paper) cudaFree(p->ghat_paper);
-    if (p->ghat32) cudaFree(p->ghat32);
-    if (p->tw) cudaFree(p->tw);
-    if (p->fft_dev) cudaFree(p->fft_dev);
-    if (p->setup_stream) cudaStreamDestroy(p->setup_stream);
-    if (p->ws) cudaFree(p->ws);
-    if (p->fp64_twin) conv_destroy(p->fp64_twin);
-    for (auto &v : {&p->tev_used, &p->tev_free})
-        for (auto &e : *v)
-            for (auto x : e) cudaEventDestroy(x);
-    delete p;
-}
+void conv_destroy(conv_plan_t p) { plan_release(p, true); }
 
 conv_status conv_plan(const conv_kernel *kernel, int period_num, int period_den, int n,
                       double trunc_a, conv_precision precision, conv_io io, int batch_max,
@@ -365,8 +381,14 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
         return fail(CONV_EUNSUPPORTED, "transform length must be at least 4");
     }
     // plan-time device work runs on a private non-blocking stream, so building a plan never waits
-    // for (or stalls) work other threads have in flight on the device
-    if (cudaStreamCreateWithFlags(&p->setup_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    // for (or stalls) work other threads have in flight on the device; at the greatest priority,
+    // so its short kernels start ahead of long-running work queued on other streams
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+        cudaGetLastError();
+        prio_hi = 0;
+    }
+    if (cudaStreamCreateWithPriority(&p->setup_stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return fail(CONV_ECUDA, "stream creation failed");
@@ -375,7 +397,7 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
     if (rc == CONV_OK) {
         // the stage table, then the device status word on the next 16-byte boundary
         const size_t err_off = (sizeof(FFTDesc) + 15) & ~(size_t)15;
-        if (cudaMalloc(&p->fft_dev, err_off + 16) != cudaSuccess) {
+        if (dev_alloc(&p->fft_dev, err_off + 16) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(CONV_ENOMEM, "cudaMalloc of the stage table failed");
         } else {
@@ -393,7 +415,7 @@ static conv_status plan_create(const conv_kernel *kernel, int period_num, int pe
         p->ws_bytes = workspace_bytes(p, batch_max);
         if (fault_take(CONV_FAULT_ALLOC)) {
             rc = fail(CONV_ENOMEM, "cudaMalloc of the workspace failed (injected fault)");
-        } else if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) {
+        } else if (dev_alloc(&p->ws, p->ws_bytes) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(CONV_ENOMEM, "cudaMalloc of the workspace failed");
         }
@@ -522,6 +544,7 @@ conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
     info->static_len = !p->fused ? 0 : (p->ed >= 2000 ? 3 << (p->ed - 2000) : (p->ed >= 1000 ? 1 << (p->ed - 1000) : 0));
     info->r2c_split = p->r2c_split ? 1 : 0;
     info->long_lines = p->long_lines ? 1 : 0;
+    info->cols_pingpong = p->cols.pp ? 1 : 0;
     info->period_num = p->pnum;
     info->period_den = p->pden;
     info->b = p->b;

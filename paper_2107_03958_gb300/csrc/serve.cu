@@ -105,7 +105,9 @@ struct srv_s {
     std::map<long long, std::shared_ptr<wsc::Req>> all;
     std::map<wsc::PlanKey, std::shared_ptr<wsc::CachedPlan>> plans;
     std::map<wsc::PlanKey, wsc::BuildJob> building;          // plans being built
-    std::deque<wsc::PlanKey> build_queue;                     // ... not yet taken by a builder
+    std::deque<wsc::PlanKey> build_queue;                     // ... not yet taken by a builder:
+                                                              // convolution plans ahead of LS plans
+    int prio_hi = 0, prio_lo = 0;                             // stream priorities (greatest, least)
     std::map<wsc::ShapeKey, std::deque<std::shared_ptr<wsc::Req>>> ready;  // conv requests by shape
     std::map<wsc::ShapeKey, int> shape_inflight;              // batches of a shape on the GPU
     std::deque<wsc::Batch> inflight;
@@ -219,11 +221,13 @@ static bool make_room(srv_t s, size_t need)
         auto cp = victim->second;
         s->plans.erase(victim);
         s->in_use -= cp->bytes;
+        // idle: every request that held it has completed (their batches' events, their solves'
+        // stream syncs), so its memory returns to the pool without a device-wide wait
         cudaStreamSynchronize(cp->stream);
-        conv_destroy(cp->plan);
+        plan_release(cp->plan, false);
         cudaStreamDestroy(cp->stream);
-        cudaFree(cp->stage_in);
-        cudaFree(cp->stage_out);
+        dev_free(cp->stage_in);
+        dev_free(cp->stage_out);
         s->stats.plans_evicted++;
     }
     return true;
@@ -238,7 +242,9 @@ static std::shared_ptr<CachedPlan> build_plan(srv_t s, const srv_request &r, int
     status = conv_plan_ex(&r.kernel, r.period_num, r.period_den, r.n, 0.0, (conv_precision)r.precision, io,
                           r.kind == SRV_LS ? 1 : s->batch_max, s->plan_flags, &cp->plan);
     if (status != CONV_OK) return nullptr;
-    cudaStreamCreateWithFlags(&cp->stream, cudaStreamNonBlocking);
+    // convolution batches at the greatest priority: a batch is short and its requests wait on it,
+    // while LS solves (least priority) run for many milliseconds
+    cudaStreamCreateWithPriority(&cp->stream, cudaStreamNonBlocking, s->prio_hi);
     conv_plan_info inf;
     conv_get_info(cp->plan, &inf);
     cp->bytes = inf.ghat_bytes + inf.workspace_bytes + (inf.precision == CONV_P_FP32 ? inf.ghat_bytes / 2 : 0) +
@@ -247,12 +253,12 @@ static std::shared_ptr<CachedPlan> build_plan(srv_t s, const srv_request &r, int
         const size_t cz = 2 * elem_bytes_of(r.precision);
         const size_t in_b = (size_t)r.n * r.n * (io == CONV_IO_C2C ? cz : cz / 2);
         const size_t out_b = (size_t)r.n * r.n * (io == CONV_IO_R2R ? cz / 2 : cz);
-        if (cudaMalloc(&cp->stage_in, in_b * s->batch_max) != cudaSuccess ||
-            cudaMalloc(&cp->stage_out, out_b * s->batch_max) != cudaSuccess) {
+        if (dev_alloc(&cp->stage_in, in_b * s->batch_max) != cudaSuccess ||
+            dev_alloc(&cp->stage_out, out_b * s->batch_max) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(cp->stage_in);
+            dev_free(cp->stage_in);
             cudaStreamDestroy(cp->stream);
-            conv_destroy(cp->plan);
+            plan_release(cp->plan, false);
             status = fail(CONV_ENOMEM, "serving staging buffers");
             return nullptr;
         }
@@ -372,7 +378,15 @@ static void dispatcher_loop(srv_t s)
                 job.r = q->r;
                 job.reserved = plan_need;
                 job.waiters.push_back(q);
-                s->build_queue.push_back(k);
+                // a convolution waits only for its plan, a solve runs for many times longer:
+                // convolution plans are built first
+                if (q->r.kind == SRV_CONV) {
+                    auto pos = s->build_queue.begin();
+                    while (pos != s->build_queue.end() && pos->io < CONV_IO_C2C + 100) ++pos;
+                    s->build_queue.insert(pos, k);
+                } else {
+                    s->build_queue.push_back(k);
+                }
                 s->cv_build.notify_one();
             }
         }
@@ -478,7 +492,7 @@ static void ls_worker(srv_t s)
 {
     cudaSetDevice(s->device);
     cudaStream_t st;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, s->prio_lo);
     while (true) {
         std::shared_ptr<Req> q;
         {
@@ -527,6 +541,10 @@ conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch
     s->batch_max = conv_batch_max;
     s->ls_workers = ls_workers;
     cudaGetDevice(&s->device);
+    if (cudaDeviceGetStreamPriorityRange(&s->prio_lo, &s->prio_hi) != cudaSuccess) {
+        cudaGetLastError();
+        s->prio_lo = s->prio_hi = 0;
+    }
     if (cudaHostAlloc(&s->status_pin, (size_t)(max_inflight + 1) * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -536,7 +554,7 @@ conv_status srv_create(size_t mem_budget_bytes, int max_inflight, int conv_batch
     s->dispatcher = std::thread(dispatcher_loop, s);
     s->completer = std::thread(completer_loop, s);
     for (int i = 0; i < ls_workers; ++i) s->workers.emplace_back(ls_worker, s);
-    for (int i = 0; i < 2; ++i) s->builders.emplace_back(builder_loop, s);
+    for (int i = 0; i < 4; ++i) s->builders.emplace_back(builder_loop, s);
     *out = s;
     return CONV_OK;
 }
@@ -635,11 +653,12 @@ void srv_destroy(srv_t s)
     s->completer.join();
     for (auto &kv : s->plans) {
         cudaStreamSynchronize(kv.second->stream);
-        conv_destroy(kv.second->plan);
+        plan_release(kv.second->plan, false);
         cudaStreamDestroy(kv.second->stream);
-        cudaFree(kv.second->stage_in);
-        cudaFree(kv.second->stage_out);
+        dev_free(kv.second->stage_in);
+        dev_free(kv.second->stage_out);
     }
+    dev_pool_trim(s->device);
     cudaFreeHost(s->status_pin);
     delete s;
 }

@@ -40,6 +40,11 @@ __host__ __device__ constexpr int static_max_threads(int ed) { return ed == 1014
 template <typename T, int E, int ED> struct maxt_fused {
     static const int v = ED >= 1000 ? static_max_threads(ED) : maxt<T, E>::v;
 };
+// Compile-time lengths whose R2R column pass may hold two buffers per line and ping-pong between
+// them (one barrier per stage): FP32 L = 2^12, 2^13 (two 66 KB buffers at L = 2^13 beside the
+// prefetched column).
+__host__ __device__ constexpr bool pingpong_ed(int ed, int elem_bytes) { return elem_bytes == 4 && (ed == 1012 || ed == 1013); }
+template <typename T, int ED> __host__ __device__ constexpr bool pingpong_ok() { return pingpong_ed(ED, (int)sizeof(T)); }
 
 template <typename T, int E, bool TWS>
 conv_status run_pipeline(conv_plan_s *p, const void *u, const void *mask, void *out, int batch,
@@ -82,6 +87,7 @@ struct LaunchShape {
     bool tws;      // twiddle table in shared memory
     bool pf;       // fused passes: prefetch of the next work item into the staging area
     bool tma;      // pass 1: TMA stores of the spectra; pass 3: TMA loads into the staging area
+    bool pp;       // R2R column pass: two transform buffers per group (ping-pong stages)
 };
 
 }  // namespace wsc
@@ -165,7 +171,7 @@ conv_status conv_plan_twin(const conv_plan_s *p, conv_plan_s **twin);
 size_t spectrum_elems(const conv_plan_s *p);  // complex elements of the workspace per density
 void destroy_hostpipe(conv_plan_s *p);          // host_io.cu (both host pipelines)
 void destroy_ls_cache(conv_plan_s *p);          // ls.cu
-void noalloc_lookup(conv_plan_s *p);
+void noalloc_lookup(conv_plan_s *p);             // noalloc.cu: address of the fixed scratch array
 // fsmask.cu: the pipeline for transform lines beyond one CTA
 conv_status long_lines_init(conv_plan_s *p);
 void long_lines_destroy(conv_plan_s *p);
@@ -173,5 +179,15 @@ size_t long_lines_ws_bytes(const conv_plan_s *p);
 conv_status long_lines_apply(conv_plan_s *p, const void *u, const void *mask, void *out, int batch, double are,
                              double aim, double beta, void *ws, cudaStream_t st);
 size_t workspace_bytes(const conv_plan_s *p, int batch);  // plan.cu: conv_workspace_size
-bool fault_take(int kind);                      // plan.cu: consume one armed injected fault            // noalloc.cu: address of the fixed scratch array
+bool fault_take(int kind);                      // plan.cu: consume one armed injected fault
+// plan.cu: free a plan; wait_device = false only when no queued or running work uses it
+void plan_release(conv_plan_s *p, bool wait_device);
+// dmem.cu: device memory from a stream-ordered pool (no implicit synchronisation); dev_free only
+// for memory no queued or running work reads or writes
+cudaError_t dev_alloc(void **ptr, size_t bytes);
+template <class P> cudaError_t dev_alloc(P **ptr, size_t bytes) { return dev_alloc(reinterpret_cast<void **>(ptr), bytes); }
+void dev_free(void *ptr);
+void dev_pool_trim(int dev);
+double *pinned_slot();                          // one page-locked double (64-byte slot)
+void pinned_slot_release(double *slot);
 }  // namespace wsc

@@ -411,6 +411,27 @@ def test_full_size_kernel_sweep(prec, compact):
         assert _relerr(ref, out[i].cpu().numpy()) <= TOL[prec]
 
 
+@pytest.mark.parametrize("n", [2048, 4096])
+def test_pingpong_column_pass(n, monkeypatch):
+    """The FP32 compact R2R passes at L = 4096 and 8192 alternate between two buffers per line
+    (one barrier per stage): the same arithmetic as the one-buffer passes, so bitwise the same
+    results, and the oracle's to the FP32 tolerance."""
+    B = 4
+    kw = KERNELS["pow-1"]
+    u = inputs.bump_sums(n, B, seed=21)
+    outs = {}
+    for pp in ("7", "0"):  # all three passes / none
+        monkeypatch.setenv("WSCONV_PP", pp)
+        plan = ConvPlan(n=n, period=3, precision="fp32", io="r2r", batch_max=B, compact=True, **kw)
+        assert plan.info.cols_pingpong == (pp == "7")
+        outs[pp] = plan.apply(torch.tensor(u, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+        plan.device_status()
+    assert np.array_equal(outs["7"], outs["0"])
+    g = O.ghat_full("pow", plan.M, plan.b, plan.a, gamma=-1.0)
+    ref = O.conv(u[B - 1], plan.M, g).real
+    assert _relerr(ref, outs["7"][B - 1]) <= TOL["fp32"]
+
+
 # ------------------------------------------------------------------ Fourier smoothing (Sec. 2.4)
 @pytest.mark.parametrize("shape,geom", [("disk", (0.5, 0.5, 0.3)), ("rect", (0.25, 0.75, 0.25, 0.75)),
                                         ("rect", (0.3, 0.7, 0.3, 0.7)), ("disk", (0.47, 0.55, 0.21))])
