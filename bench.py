@@ -435,6 +435,24 @@ def sweep_roofline(run, batch, prec, alu_peak, alu_nominal, hbm, hbm_src):
             "pass_share_r2r": {"rows_fwd": share[0], "cols": share[1], "rows_inv": share[2]}}
 
 
+def period3_view(n, batch, prec, col_ms, step_ms, hbm):
+    """Effective bandwidth against the bytes the plain three-pass schedule on the period-3 grid
+    (M = 3n, spectra of n x (3n/2 + 1) per density, multiplier quadrant (3n/2 + 1)^2) moves: per
+    R2R convolution 65 n^2 B in FP32 (130 n^2 in FP64), per Helmholtz one 102 n^2 (204 n^2); the
+    R2R column pass 24 n^2 per density + 9 n^2 per launch in FP32 (twice that in FP64).  The compact
+    embedding moves fewer bytes than this, so these fractions credit it with the bytes it saves."""
+    f = 2 if prec == "fp64" else 1
+    nn = float(n) * n
+    col = f * (24 * nn * batch + 9 * nn)
+    step = f * batch * (4 * 65 * nn + 102 * nn)
+    return {"model": "period-3 three-pass schedule bytes (FP32 65 n^2 per R2R conv, 102 n^2 per "
+                     "Helmholtz conv; FP64 twice)",
+            "col_bytes_per_launch": col, "col_gbs": col / (col_ms * 1e-3) / 1e9,
+            "col_frac": col / (col_ms * 1e-3) / 1e9 / hbm,
+            "step_bytes": step, "step_gbs": step / (step_ms * 1e-3) / 1e9,
+            "step_frac": step / (step_ms * 1e-3) / 1e9 / hbm}
+
+
 def n8192_leg(steps, stream, hbm, fp32_peak):
     """The largest grid of the discontinuous-density sweep: n = 8192, batch 8, log kernel, FP32 R2R
     on the compact grid (L = 16384, compile-time stages, 1024 threads per line)."""
@@ -757,6 +775,8 @@ def main():
     value = job_throughput(ws, convs, ms)
     roofline = sweep_roofline(head, args.batch, prec, alu_peak[prec], alu_nominal[prec], hbm, hbm_src)
     roofline["live_peaks"] = peaks
+    roofline["hbm_period3_schedule"] = period3_view(args.n, args.batch, prec, roofline["avg_launch_ms"],
+                                                    ms / args.steps, hbm)
     head.pop("plans")
     torch.cuda.empty_cache()
 
@@ -774,6 +794,7 @@ def main():
     orun = sweep_leg(args.n, args.batch, other, k_o, min(args.warmup, 3), stream, timing=True)
     o_ms = max_over_ranks(ws, orun["ms"])
     o_roof = sweep_roofline(orun, args.batch, other, alu_peak[other], alu_nominal[other], hbm, hbm_src)
+    o_roof["hbm_period3_schedule"] = period3_view(args.n, args.batch, other, o_roof["avg_launch_ms"], o_ms / k_o, hbm)
     orun.pop("plans")
     torch.cuda.empty_cache()
     o_e2e = e2e_leg(args.n, args.batch, max(3, k_o // 2), 3, precision=other)

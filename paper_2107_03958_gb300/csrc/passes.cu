@@ -401,6 +401,14 @@ static int default_options(const conv_plan_s *p, int ed, int pass)
     // L = 2^14 at 1024 threads: 32 warps per SM hide the latency a prefetch would, and its staging
     // does not fit beside the 139 KB line (n = 8192, batch 8: 16.2 -> 15.4 ms per batch)
     if (ed == 1014) return 0;
+    // FP64 column passes: twiddles in shared memory.  Read through L1, the fifteen powers a
+    // radix-16 butterfly loads are hoisted into registers and the kernel spills (556 B a thread at
+    // L = 2^13), whose write-backs doubled its DRAM writes (9.2 GB against 4.3 GB algorithmic per
+    // launch at n = 4096, batch 16); from shared memory it does not spill, at +0.4 % time.  At
+    // L = 2^13 only the radix-16 stages' blocks fit beside the line (tw_split_ed), without room for
+    // the prefetch (which made no measurable difference there).
+    if (ed >= 1000 && ed < 2000 && p->prec == CONV_P_FP64 && pass == 1)
+        return tw_split_ed(ed, 8) ? CFG_TWS : CFG_TWS | CFG_PF;
     if (ed >= 1000) return pass == 2 ? (pairs ? CFG_PF | CFG_TMA : CFG_TWS) : CFG_PF;
     if (!pairs) return pass == 2 ? 0 : CFG_TWS;
     return pass == 1 ? CFG_TWS : CFG_TWS | CFG_PF | CFG_TMA;
