@@ -733,6 +733,47 @@ def served_ls_burst(count, seed=5):
     return out
 
 
+def served_conv_burst(count, seed=6):
+    """The convolution requests of the serving mix (n from the mix's sizes, kernels of the sweep,
+    Helmholtz kappa ~ U[5, 60]; FP32), all submitted at once to a server whose plans are already
+    resident (one untimed pass first): saturated throughput with continuous batching by transform
+    shape (batch up to 16) against the same server with batches of one."""
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import Server
+    reqs = [r for r in inputs.serving_requests(count, rate=200.0, seed=seed, ls_fraction=0.0)]
+    bufs = []
+    for r in reqs:
+        n = r["n"]
+        u = torch.tensor(inputs.bump_sums(n, 1, seed=r["seed"])[0], dtype=torch.float32, device="cuda")
+        cplx = r["kernel"] == "helmholtz"
+        bufs.append((u, torch.empty((n, n), dtype=torch.complex64 if cplx else torch.float32, device="cuda")))
+    out = {"requests": len(reqs), "sizes": sorted(set(r["n"] for r in reqs))}
+    for bmax, name in ((16, "batched"), (1, "unbatched")):
+        srv = Server(mem_budget_bytes=150 << 30, max_inflight=64, conv_batch_max=bmax, ls_workers=1, compact=True)
+        for timed in (False, True):
+            torch.cuda.synchronize()
+            st0 = srv.stats()
+            t0 = time.perf_counter()
+            tickets = []
+            for r, (u, o) in zip(reqs, bufs):
+                io = "r2c" if r["kernel"] == "helmholtz" else "r2r"
+                tickets.append(srv.submit_conv(u, o, kernel=r["kernel"], precision="fp32", io=io, **dict(r["params"])))
+            res = [srv.wait(t, timeout_s=600) for t in tickets]
+            wall = time.perf_counter() - t0
+            st1 = srv.stats()
+        srv.close()
+        lat = sorted(r["latency_s"] for r in res if r["status"] == "CONV_OK")
+        pct = lambda a, p: 1e3 * a[min(len(a) - 1, max(0, int(math.ceil(p * len(a))) - 1))] if a else None
+        out[name] = {"conv_per_s": len(lat) / wall, "wall_s": wall, "completed_ok": len(lat),
+                     "batches": st1["batches"] - st0["batches"],
+                     "batched_requests": st1["batched_requests"] - st0["batched_requests"],
+                     "mean_batch": sum(r["batched_with"] for r in res) / max(1, len(res)),
+                     "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99)}
+    out["batched_over_unbatched"] = out["batched"]["conv_per_s"] / out["unbatched"]["conv_per_s"]
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -862,6 +903,7 @@ def main():
         extras["tc_stage"] = tcs
         extras["serving"] = serving_leg(2000)
         extras["served_ls_burst"] = served_ls_burst(80)
+        extras["served_conv_burst"] = served_conv_burst(400)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "conv/s", "n_gpus": ws, "steps": args.steps,
