@@ -55,6 +55,9 @@ struct FFTDesc {
 // radix-2 stage (one power per butterfly) reads the global table.
 __host__ __device__ constexpr bool tw_split_ed(int ed, int elem_bytes) { return elem_bytes == 8 && ed == 1013; }
 template <typename T, int ED> __host__ __device__ constexpr bool tw_split_ok() { return tw_split_ed(ED, (int)sizeof(T)); }
+// Compile-time lengths whose split R2C column pass may run with one buffer per CTA: those of the
+// 512-thread kernels (at L = 2^14, 1024 threads of 64 registers, that kernel spills 600 B).
+__host__ __device__ constexpr bool split_one_ed(int ed) { return ed >= 1000 && ed != 1014; }
 
 // ---------------------------------------------------------------- small DFTs
 template <bool INV, typename V> __device__ __forceinline__ void dft2(V *x) {

@@ -491,6 +491,7 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
         S.tpt = tpt;
         S.groups = G;
         S.pp = false;
+        S.one = false;
         S.tws = tws;
         S.pf = pf;
         S.tma = tma;
@@ -507,11 +508,26 @@ static bool configure(conv_plan_s *p, const Candidate &c, int smem_optin, int sm
     int opt[3];
     for (int k = 0; k < 3; ++k) opt[k] = c[2 + k] == CFG_DEFAULT ? default_options(p, ed, k) : c[2 + k];
     LaunchShape R, C, I;
-    // R2C with complex ghat runs the split pipeline when its pass 2 fits two buffers per CTA;
-    // otherwise the C2C layout
+    // R2C with complex ghat runs the split pipeline when its pass 2 fits two buffers per CTA.
+    // Where two lines do not fit one CTA (FP64 at L = 8192), the compile-time lengths run it with
+    // one buffer and a global scratch line per CTA group (after the spectra in the workspace:
+    // workspace_bytes counts them).  Otherwise the C2C layout.
+    const bool cplx_r2c = p->io == CONV_IO_R2C && p->complex_ghat;
+    p->split_scratch_elems = 0;
     bool split = false;
     if (fused) {
-        split = p->io == CONV_IO_R2C && p->complex_ghat && shape(opt[1], 1, false, 2, C);
+        split = cplx_r2c && shape(opt[1], 1, false, 2, C);
+        const char *one_env = getenv("WSCONV_SPLIT_ONE");  // 0: never, 1: even where two buffers fit
+        const int one_mode = one_env ? atoi(one_env) : -1;
+        if (cplx_r2c && split_one_ed(ed) && one_mode != 0 && (!split || one_mode == 1)) {
+            LaunchShape C1;
+            if (shape(opt[1], 1, false, 1, C1)) {
+                C1.one = true;
+                C = C1;
+                split = true;
+                p->split_scratch_elems = (size_t)C1.max_ctas * C1.groups * M;
+            }
+        }
         const bool pairs = p->io == CONV_IO_R2R || split;
         // the lengths with ping-pong kernels (R2R passes, and the split pipeline's pass 1): two
         // buffers per group when that costs none of the pass's options or groups.  By default

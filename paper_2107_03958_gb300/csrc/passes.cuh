@@ -37,6 +37,7 @@ template <typename T> struct PassArgs {
     int odd;               // pass 2: the multiplier is i sgn(k1) T(|k1|, |k2|) (the non-radial kernel)
     int nsel;              // pass 2: 0, or the batch's own multiplier per density (conv_apply_kernels)
     const void *gsel[WSC_MAX_SEL];
+    void *scratch;         // split pass 2 with one buffer per group: one global line per group
 };
 
 // x times the odd multiplier i sgn(k1) t at transform index o of a length-L column (k1 = o below

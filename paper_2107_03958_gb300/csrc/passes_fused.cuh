@@ -359,16 +359,19 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_rows_inv(const __grid_constant__ PassAr
 
 // Pass 2.  Two transform buffers per group: Re ghat's product transforms in the first, Im ghat's
 // in the second.  Staging: the column of W (one bulk copy, as in the R2R pass 2).
-template <typename T, int E, int ED, bool TWS>
+template <typename T, int E, int ED, bool TWS, bool ONE = false>
 __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T> a)
 {
     typedef typename cvec<T>::t V;
     const int g = threadIdx.x / a.tpt, lt = threadIdx.x - g * a.tpt, G = blockDim.x / a.tpt;
     const V *twp;
-    V *bre = setup_smem<T, TWS>(a, twp, 2 * g);
-    V *bim = bre + padded_len<T>(a.M);
+    // ONE: a single buffer per group (two lines do not fit, FP64 at L = 8192); the Im-ghat
+    // spectrum waits in the group's global scratch line, in L2, while the Re part is inverted
+    V *bre = setup_smem<T, TWS>(a, twp, ONE ? g : 2 * g);
+    V *bim = ONE ? nullptr : bre + padded_len<T>(a.M);
+    V *tmp = ONE ? reinterpret_cast<V *>(a.scratch) + ((size_t)blockIdx.x * G + g) * a.M : nullptr;
     unsigned long long *bar;
-    V *stg = stage_area<T, TWS, 2>(a, g, G, bar);
+    V *stg = stage_area<T, TWS, ONE ? 1 : 2>(a, g, G, bar);
     const int n = a.n, M = a.M, h = a.h, stride = gridDim.x * G;
     const V *cg = reinterpret_cast<const V *>(a.ghat);
     auto col_off = [&](int unit) -> size_t {
@@ -400,12 +403,29 @@ __global__ void WSC_LBF(T, E, ED) kf_r2c_cols(const __grid_constant__ PassArgs<T
         auto mul = smem_hook([&](int o, V &x) {
             const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
             const V gk = __ldg(&gc[k1]);
-            bim[pidx<T>(o)] = cscale(x, gk.y);
+            if constexpr (ONE) tmp[o] = cscale(x, gk.y);
+            else bim[pidx<T>(o)] = cscale(x, gk.y);
             x = cscale(x, gk.x);
         });
         fft_any<T, E, ED, false, TWS, pruned<ED>(), false>(bre, a.P, twp, a.tw, lt, a.tpt, src, mul, [&]() { fetch(unit + stride); });
-        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bre, a.P, twp, a.tw, lt, a.tpt, FromSmem{}, ToSmem{});
         V *cout = reinterpret_cast<V *>(a.out) + 2 * co;
+        if constexpr (ONE) {
+            // Wr straight to the output pairs' first halves; then Wi from the scratch line (its
+            // stores by the whole group are visible after the barriers of the first inverse)
+            auto dst_r = [&](int o, V xr) {
+                if (valid && o < n) cout[2 * o] = xr;
+            };
+            fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bre, a.P, twp, a.tw, lt, a.tpt, FromSmem{}, dst_r);
+            __syncthreads();
+            auto src_i = [&](int i) -> V { return tmp[i]; };
+            auto dst_i = [&](int o, V xi) {
+                if (valid && o < n) cout[2 * o + 1] = xi;
+            };
+            fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bre, a.P, twp, a.tw, lt, a.tpt, src_i, dst_i);
+            __syncthreads();
+            continue;
+        }
+        fft_any<T, E, ED, true, TWS, false, pruned<ED>()>(bre, a.P, twp, a.tw, lt, a.tpt, FromSmem{}, ToSmem{});
         auto dst = [&](int o, V xi) {
             if (!valid || o >= n) return;
             const V xr = bre[pidx<T>(o)];
@@ -671,6 +691,7 @@ template <typename T, int E, int ED, bool TWS> conv_status set_attrs_fused(int s
         WSC_ATTR((kf_r2r_rows_inv<T, E, ED, TWS, true>));
     }
     WSC_ATTR((kf_r2c_cols<T, E, ED, TWS>));
+    if constexpr (split_one_ed(ED)) WSC_ATTR((kf_r2c_cols<T, E, ED, TWS, true>));
     WSC_ATTR((kf_r2c_rows_inv<T, E, ED, TWS>));
     WSC_ATTR((kf_c2c_rows_fwd<T, E, ED, TWS, true>));
     WSC_ATTR((kf_c2c_rows_fwd<T, E, ED, TWS, false>));
@@ -805,7 +826,14 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.pf = pf_cols;
         a.tma = 0;
         a.vec = al(W2, 16);
-        WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
+        if constexpr (split_one_ed(ED)) {
+            // one buffer per group: the scratch lines follow W2 (batch (3 h n + 1) values in all)
+            a.scratch = reinterpret_cast<V *>(ws) + (((size_t)batch * (3 * (size_t)h * n + 1) + 1) & ~(size_t)1);
+            if (C.one) WSC_LAUNCH2(C, kf_r2c_cols, (T, E, ED), true);
+            else WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
+        } else {
+            WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
+        }
         if (ev) cudaEventRecord(ev[2], st);
         a.tpt = I.tpt;
         a.in = W2;

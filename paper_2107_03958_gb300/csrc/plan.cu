@@ -71,7 +71,10 @@ size_t spectrum_elems(const conv_plan_s *p)
 size_t workspace_bytes(const conv_plan_s *p, int batch)
 {
     if (p->long_lines) return batch > 0 ? long_lines_ws_bytes(p) : 0;  // densities run one at a time
-    return spectrum_elems(p) * (p->prec == CONV_P_FP64 ? 16 : 8) * (size_t)batch;
+    const size_t esz = p->prec == CONV_P_FP64 ? 16 : 8;
+    // the split pass 2's scratch lines follow the spectra on an even element
+    const size_t scratch = p->split_scratch_elems ? p->split_scratch_elems + 1 : 0;
+    return batch > 0 ? (spectrum_elems(p) * (size_t)batch + scratch) * esz : 0;
 }
 
 void stage_twiddles(const FFTDesc &d, std::vector<double> &re_im);
@@ -114,6 +117,21 @@ static conv_status reupload(conv_plan_s *p)
     return CONV_OK;
 }
 
+// After a change of launch configuration: a plan workspace large enough for the new one (the
+// split pass's scratch lines depend on it).
+static conv_status fit_workspace(conv_plan_s *p)
+{
+    const size_t need = workspace_bytes(p, p->batch_max);
+    if (need <= p->ws_bytes) return CONV_OK;
+    WSC_CUDA(cudaStreamSynchronize(p->setup_stream));
+    dev_free(p->ws);
+    p->ws = nullptr;
+    p->ws_bytes = 0;
+    if (dev_alloc(&p->ws, need) != cudaSuccess) return fail(CONV_ENOMEM, "workspace allocation failed");
+    p->ws_bytes = need;
+    return CONV_OK;
+}
+
 // Autotuner: for every family of launch configurations (elements per thread, fused or not) time
 // each distinct option set on zero densities at the plan's batch size, pass by pass; keep each
 // pass's fastest option (fused passes choose independently; the plain passes share one) and the
@@ -129,7 +147,8 @@ static conv_status autotune(conv_plan_s *p)
         auto it = cache.find(key);
         if (it != cache.end()) {
             conv_status rc = apply_candidate(p, it->second);
-            return rc == CONV_OK ? reupload(p) : rc;
+            if (rc == CONV_OK) rc = reupload(p);
+            return rc == CONV_OK ? fit_workspace(p) : rc;
         }
     }
     const auto fams = transform_families(p);
@@ -157,6 +176,8 @@ static conv_status autotune(conv_plan_s *p)
         Candidate fpick = fam[0];
         for (const auto &c : fam) {
             rc = apply_candidate(p, c);
+            // a configuration whose workspace (the split pass's scratch lines) exceeds the plan's
+            if (rc == CONV_OK && workspace_bytes(p, p->batch_max) > p->ws_bytes) continue;
             if (rc == CONV_OK) rc = reupload(p);
             if (rc != CONV_OK) break;
             p->timing = false;
@@ -192,6 +213,7 @@ static conv_status autotune(conv_plan_s *p)
     if (rc != CONV_OK) return rc;
     rc = apply_candidate(p, pick);
     if (rc == CONV_OK) rc = reupload(p);
+    if (rc == CONV_OK) rc = fit_workspace(p);
     if (rc == CONV_OK) {
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = pick;

@@ -88,6 +88,7 @@ struct LaunchShape {
     bool pf;       // fused passes: prefetch of the next work item into the staging area
     bool tma;      // pass 1: TMA stores of the spectra; pass 3: TMA loads into the staging area
     bool pp;       // R2R column pass: two transform buffers per group (ping-pong stages)
+    bool one;      // split R2C column pass: one buffer per group, the Im part via a global line
 };
 
 }  // namespace wsc
@@ -105,6 +106,7 @@ struct conv_plan_s {
     bool complex_ghat;
     conv_moments moments{};  // how ghat is computed (closed forms by default)
     bool r2c_split = false;  // R2C with complex ghat on the split pipeline (fused passes)
+    size_t split_scratch_elems = 0;  // split pass 2 with one buffer per CTA: its global lines
     int device;
     cudaStream_t setup_stream = nullptr;  // private stream for plan-time device work
     int elems;  // complex elements per thread in the transform kernels

@@ -377,6 +377,35 @@ def test_compile_time_length_on_the_period_2_grid(io):
         assert _relerr(ref[i], out[i]) <= TOL["fp32"]
 
 
+@pytest.mark.parametrize("prec,n,compact", [("fp64", 128, True), ("fp32", 256, True), ("fp32", 128, False)])
+def test_split_r2c_one_buffer(prec, n, compact, monkeypatch):
+    """The split Helmholtz column pass with one buffer per CTA (the Im-ghat spectrum parked in a
+    global scratch line), forced at small n: bitwise the two-buffer pass's results, and the
+    oracle's.  FP64 at n = 4096 (L = 8192) takes it by default (test_full_size_helmholtz_r2c)."""
+    B = 3
+    kw = KERNELS["helm20"]
+    u = inputs.bump_sums(n, B, seed=31)
+    outs = {}
+    for one in ("1", "0"):
+        monkeypatch.setenv("WSCONV_SPLIT_ONE", one)
+        plan = ConvPlan(n=n, period=3, precision=prec, io="r2c", batch_max=B, compact=compact, **kw)
+        assert plan.info.r2c_split == 1
+        assert plan.workspace_bytes(B) >= plan.workspace_bytes(1)
+        outs[one] = plan.apply(torch.tensor(u, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+        plan.device_status()
+    assert np.array_equal(outs["1"], outs["0"])
+    kind, okw = _oracle_kw(kw)
+    g = O.ghat_full(kind, plan.M, plan.b, plan.a, **okw)
+    for i in range(B):
+        assert _relerr(O.conv(u[i], plan.M, g), outs["1"][i]) <= TOL[prec]
+
+
+def test_fp64_helmholtz_n4096_runs_split():
+    plan = ConvPlan("helmholtz", n=4096, period=3, precision="fp64", io="r2c", batch_max=16, compact=True,
+                    kappa=20.0)
+    assert plan.info.r2c_split == 1
+
+
 @pytest.mark.parametrize("compact", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_full_size_helmholtz_r2c(prec, compact):
