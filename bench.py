@@ -51,9 +51,9 @@ def parse():
                     help="skip the error of the timed outputs against the oracle")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="arithmetic of the headline sweep (the other is reported beside it)")
-    ap.add_argument("--only", choices=["r2r", "r2r64", "r2c", "c2c"], default=None,
+    ap.add_argument("--only", choices=["r2r", "r2r64", "r2c", "r2c64", "c2c"], default=None,
                     help="profiling case: warmup + steps applies of one plan (log kernel R2R FP32, "
-                         "R2R FP64, Helmholtz R2C or C2C FP32), no other legs")
+                         "R2R FP64, Helmholtz R2C FP32 or FP64, C2C FP32), no other legs")
     return ap.parse_args()
 
 
@@ -612,10 +612,11 @@ def profile_case(args):
     import torch
     from paper_2107_03958_gb300 import inputs
     from paper_2107_03958_gb300.api import ConvPlan
-    prec = "fp64" if args.only == "r2r64" else "fp32"
+    prec = "fp64" if args.only in ("r2r64", "r2c64") else "fp32"
     compact = os.environ.get("BENCH_PERIOD_B", "0") != "1"
-    if args.only in ("c2c", "r2c"):
-        plan = ConvPlan("helmholtz", n=args.n, period=3, precision=prec, io=args.only,
+    if args.only in ("c2c", "r2c", "r2c64"):
+        io = "r2c" if args.only == "r2c64" else args.only
+        plan = ConvPlan("helmholtz", n=args.n, period=3, precision=prec, io=io,
                         batch_max=args.batch, kappa=20.0, compact=compact)
         dt = plan.cplx_dtype if args.only == "c2c" else plan.real_dtype
         u = torch.tensor(inputs.bump_sums(args.n, args.batch), dtype=dt, device="cuda")
