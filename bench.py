@@ -313,6 +313,37 @@ def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, compact=
     return res
 
 
+def shared_rows_leg(n, batch, precision, steps, warmup, stream, compact=True):
+    """The same sweep through conv_apply_multi: the five kernels' row transforms of pass 1 run
+    once per step (they depend only on the densities), then passes 2 and 3 of each plan.  Each
+    output is bitwise the independent apply's; reported beside the headline, which runs five
+    independent applies."""
+    import torch
+    from paper_2107_03958_gb300 import inputs
+    from paper_2107_03958_gb300.api import apply_multi, multi_workspace_bytes
+    plans = make_plans(n, batch, precision, compact)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u = torch.from_numpy(inputs.bump_sums(n, batch)).to(dt).cuda()
+    outs = [torch.empty((batch, n, n), dtype=p.out_dtype(), device="cuda") for p in plans]
+    ws = torch.empty(multi_workspace_bytes(plans, batch), dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            apply_multi(plans, u, outs=outs, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            apply_multi(plans, u, outs=outs, workspace=ws, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    for p in plans:
+        p.device_status()
+    return {"value": 5 * batch / (ms * 1e-3), "unit": "conv/s", "ms_per_step": ms, "steps": steps,
+            "launches_per_step": 1 + 2 * len(plans), "api": "conv_apply_multi"}
+
+
 def e2e_leg(n, batch, steps, warmup, compact=True, precision="fp64"):
     """End to end through conv_apply_host_multi (the call that takes HOST buffers): every step
     uploads the batch of densities from pinned host memory once, runs the five plans' passes on
@@ -903,6 +934,11 @@ def main():
         tcs["tensor_over_cuda_core"] = tcs["us_tensor"] / tcs["us_cuda_core"]
         extras["tc_stage"] = tcs
         extras["serving"] = serving_leg(2000)
+        extras["shared_rows"] = {
+            "fp64": shared_rows_leg(args.n, args.batch, "fp64", max(2, args.steps // 4), 2, stream),
+            "fp32": shared_rows_leg(args.n, args.batch, "fp32", args.steps, 3, stream),
+            "note": "the same 80-convolution sweep with pass 1 computed once for the five kernels"}
+        torch.cuda.empty_cache()
         extras["served_ls_burst"] = served_ls_burst(80)
         extras["served_conv_burst"] = served_conv_burst(400)
 

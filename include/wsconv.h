@@ -201,6 +201,34 @@ conv_status conv_apply_host_multi(int count, const conv_plan_t *plans, const voi
 conv_status conv_apply_kernels(conv_plan_t shape, const conv_plan_t *plans, const void *u, const void *mask,
                                void *out, int batch, void *workspace, void *stream);
 
+/* The same densities convolved with several kernels, A_n^(k)(u . mask) for each plan k, with the
+ * row transforms of pass 1 computed once (Sec. 2.1, eq. (An): the forward row transform of the
+ * zero-extended density does not depend on the kernel; the paper's Tables 1-3 apply four
+ * kernels to one density):
+ *     outs[k][b] = A_n^(k)(u[b] . mask),   k < count, b < batch.
+ *   plans:  `count` distinct plans running the fused R2R or split R2C passes (real densities; a
+ *           plan whose info.fused is 0 or info.long_lines is 1 is refused), sharing n, period,
+ *           precision, embedding and the row pass's launch configuration; kernels may differ.
+ *   u, mask: as for conv_apply (real densities of the plans' precision).
+ *   outs:   `count` device arrays, outs[k] batch x n x n in plans[k]'s output layout, distinct
+ *           and not aliasing u.
+ *   workspace: NULL (then batch <= every plan's batch_max; a workspace comes from the library's
+ *           memory pool and returns to it in stream order) or conv_multi_workspace_size bytes,
+ *           16-byte aligned, owned by the caller.
+ * Each result is bitwise the one conv_apply gives on plans[k] alone.  Asynchronous on `stream`.
+ * The call sets per-plan launch state for its duration: calls on the same plans must not
+ * overlap (from several threads).
+ * Returns CONV_EINVAL for what conv_apply rejects and for mismatched plans, CONV_EUNSUPPORTED for
+ * plans outside the fused R2R / split R2C pipelines, CONV_ENOMEM when the pool cannot supply
+ * the workspace. */
+conv_status conv_apply_multi(const conv_plan_t *plans, int count, const void *u, const void *mask,
+                             void *const *outs, int batch, void *workspace, void *stream);
+
+/* Bytes of the caller's workspace conv_apply_multi needs for `batch` densities: the shared row
+ * spectrum (batch x n x (L/2 + 1) complex, rounded to 256 bytes) plus the largest of the plans'
+ * own conv_workspace_size.  CONV_EINVAL / CONV_EUNSUPPORTED as conv_apply_multi. */
+conv_status conv_multi_workspace_size(const conv_plan_t *plans, int count, int batch, size_t *bytes);
+
 /* conv_apply without any allocation (the paper has no counterpart; this is a deployment aid).
  * For callers that cannot call cudaMalloc when they run the convolution: code under a device
  * memory budget that forbids new allocations, real-time loops where an allocation may block, or

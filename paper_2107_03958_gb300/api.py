@@ -199,6 +199,33 @@ def apply_kernels(shape, plans, u, out=None, mask=None, workspace=None, stream=N
     return out
 
 
+def apply_multi(plans, u, outs=None, mask=None, workspace=None, stream=None):
+    """A_n(u * mask) with every plan in `plans` (R2R or split R2C plans of one grid, precision and
+    embedding) on the same device densities `u`, pass 1's row transforms computed once (see
+    conv_apply_multi).  Returns the list of outputs."""
+    p0 = plans[0]
+    p0._check_grid(u, p0.in_dtype(), "u")
+    batch = 1 if u.dim() == 2 else int(np.prod(u.shape[:-2]))
+    if outs is None:
+        outs = [torch.empty(u.shape, dtype=p.out_dtype(), device=u.device) for p in plans]
+    for p, o in zip(plans, outs):
+        p._check_grid(o, p.out_dtype(), "out")
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
+    oarr = (ctypes.c_void_p * len(plans))(*[o.data_ptr() for o in outs])
+    N.check(p0._lib.conv_apply_multi(
+        arr, len(plans), ctypes.c_void_p(u.data_ptr()),
+        ctypes.c_void_p(mask.data_ptr()) if mask is not None else None, oarr, batch,
+        ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else None, _stream_ptr(stream)))
+    return outs
+
+
+def multi_workspace_bytes(plans, batch):
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
+    b = ctypes.c_size_t()
+    N.check(plans[0]._lib.conv_multi_workspace_size(arr, len(plans), int(batch), ctypes.byref(b)))
+    return b.value
+
+
 def apply_host_multi(plans, u, outs=None, mask=None, stream=None):
     """A_n(u * mask) with every plan in `plans` for one batch of host densities `u` (a CPU tensor;
     pinned for overlap): each chunk is uploaded once and the plans run on it in turn.  The plans

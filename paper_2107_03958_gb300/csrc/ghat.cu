@@ -81,8 +81,9 @@ __device__ double pow_moment_cc(double gamma, double s, double a)
 }
 
 // 2 pi (i/4) int_0^a H0(kappa rho) J0(s rho) rho d rho = i 2 pi a^2 int_0^1 H0(kappa a u^4) J0(s a u^4) u^7 du
-// by panel Clenshaw-Curtis.  The nodes' H0(kappa a u^4) do not depend on s; the host tabulates
-// them once per plan (tab: per node u, weight, Re H0, Im H0), so only J0 is evaluated here.
+// by panel Clenshaw-Curtis.  The nodes' H0(kappa a u^4) do not depend on s; k_helm_band_table
+// tabulates them once per plan (tab: per node u, weight, Re H0, Im H0), so only J0 is evaluated
+// here.
 __device__ double2 helm_moment_cc(const double *__restrict__ tab, int nodes, double s, double a)
 {
     double sr = 0.0, si = 0.0;
@@ -94,6 +95,24 @@ __device__ double2 helm_moment_cc(const double *__restrict__ tab, int nodes, dou
     }
     const double c = 2.0 * M_PI * a * a;
     return make_double2(-c * si, c * sr);
+}
+
+// The band quadrature's node table (per node u, weight, Re H0, Im H0 of H0(kappa a u^4)): P
+// panels of CC_N + 1 Clenshaw-Curtis nodes on [q/P, (q+1)/P], one thread per node.  The integrand's
+// limit at u = 0 is 0 (u^7 log u); H0 itself is infinite there.
+__global__ void k_helm_band_table(double *__restrict__ tab, int P, double ka)
+{
+    const int nodes = P * (CC_N + 1);
+    const double hw = 0.5 / P;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nodes; t += gridDim.x * blockDim.x) {
+        const int q = t / (CC_N + 1), i = t - q * (CC_N + 1);
+        const double u = (q + 0.5) / P + hw * c_ccx[i], arg = ka * u * u * u * u;
+        double *e = tab + 4 * (size_t)t;
+        e[0] = u;
+        e[1] = hw * c_ccw[i];
+        e[2] = arg > 0.0 ? j0(arg) : 0.0;
+        e[3] = arg > 0.0 ? y0(arg) : 0.0;
+    }
 }
 
 // hka = (J0, Y0, J1, Y1)(kappa a), tabulated on the host.
@@ -248,26 +267,16 @@ conv_status build_ghat(conv_plan_s *p)
         const double kappa = p->kern.kappa, a = p->a, ka = kappa * a;
         hka = make_double4(::j0(ka), ::y0(ka), ::j1(ka), ::y1(ka));
         // panels in u = (rho/a)^{1/4}: 8 + ceil(1.5 (kappa + s) a) for s up to the band's top, each
-        // holding about two thirds of an oscillation of H0(kappa a u^4) J0(s a u^4) at u = 1
+        // holding about two thirds of an oscillation of H0(kappa a u^4) J0(s a u^4) at u = 1; the
+        // nodes' H0 values are computed on the device (thousands of nodes at large kappa a)
         const int P = 8 + (int)std::ceil(1.5 * (2.0 + HELM_BAND) * kappa * a);
-        std::vector<double> tab(4 * (size_t)P * (CC_N + 1));
-        const double hw = 0.5 / P;
-        for (int q = 0; q < P; ++q)
-            for (int i = 0; i <= CC_N; ++i) {
-                const double u = (q + 0.5) / P + hw * cx[i], arg = ka * u * u * u * u;
-                double *e = &tab[4 * ((size_t)q * (CC_N + 1) + i)];
-                e[0] = u;
-                e[1] = hw * cw[i];
-                // the integrand's limit at u = 0 is 0 (u^7 log u); H0 itself is infinite there
-                e[2] = arg > 0.0 ? ::j0(arg) : 0.0;
-                e[3] = arg > 0.0 ? ::y0(arg) : 0.0;
-            }
         hnodes = P * (CC_N + 1);
-        if (cudaMallocAsync(&htab, tab.size() * sizeof(double), st) != cudaSuccess) {
+        if (cudaMallocAsync(&htab, 4 * (size_t)hnodes * sizeof(double), st) != cudaSuccess) {
             cudaGetLastError();
             return fail(CONV_ENOMEM, "cudaMalloc of the Helmholtz quadrature table failed");
         }
-        WSC_CUDA(cudaMemcpyAsync(htab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_helm_band_table<<<(hnodes + 255) / 256, 256, 0, st>>>(htab, P, ka);
+        WSC_CUDA(cudaGetLastError());
     }
     if (closed) {
         int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);

@@ -207,13 +207,15 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const __grid_constant__ PassArgs<T
     V *stg = stage_area<T, TWS, PP ? 2 : 1>(a, g, G, bar);
     const int n = a.n, M = a.M, h = a.h, stride = gridDim.x * G;
     const T *ghat = reinterpret_cast<const T *>(a.ghat);
-    auto col_at = [&](int unit) -> V * {
+    // column k2 of density b: read from a.in, written to a.out (the same array but for
+    // conv_apply_multi, whose plans read one shared pass-1 spectrum)
+    auto col_off = [&](int unit) -> size_t {
         const int k2 = unit / a.batch, b = unit - k2 * a.batch;
-        return reinterpret_cast<V *>(a.out) + (size_t)b * h * n + (size_t)k2 * n;
+        return (size_t)b * h * n + (size_t)k2 * n;
     };
     auto fetch = [&](int unit) {
         if (!a.pf || lt != 0 || unit >= a.units) return;
-        issue_bulk(stg, col_at(unit), (unsigned)((size_t)n * sizeof(V)), bar);
+        issue_bulk(stg, reinterpret_cast<const V *>(a.in) + col_off(unit), (unsigned)((size_t)n * sizeof(V)), bar);
     };
     unsigned par = 0;
     if (a.pf) {
@@ -226,11 +228,13 @@ __global__ void WSC_LBF(T, E, ED) kf_r2r_cols(const __grid_constant__ PassArgs<T
         const bool valid = unit < a.units;
         if (a.pf && !await_bulk(a, bar, par, valid)) return;
         const int k2 = valid ? unit / a.batch : 0, bq = valid ? unit - k2 * a.batch : 0;
-        V *col = col_at(valid ? unit : 0);
+        const size_t co = col_off(valid ? unit : 0);
+        const V *cin = reinterpret_cast<const V *>(a.in) + co;
+        V *col = reinterpret_cast<V *>(a.out) + co;
         const T *gc = (a.nsel ? reinterpret_cast<const T *>(a.gsel[bq]) : ghat) + (size_t)k2 * h;
         auto src = [&](int i) -> V {
             if (!valid || i >= n) return cmk<V>(0, 0);
-            return a.pf ? stg[i] : col[i];
+            return a.pf ? stg[i] : cin[i];
         };
         auto mul = smem_hook([&](int o, V &x) {
             const int Lm = pruned<ED>() ? static_len<ED>() : M, k1 = o <= Lm / 2 ? o : Lm - o;
@@ -780,6 +784,9 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
     } while (0)
     cudaEvent_t *ev = timing_slot(p);
     if (ev) cudaEventRecord(ev[0], st);
+    // p->run_passes: the passes this launch runs (conv_apply_multi runs pass 1 once for several
+    // plans, then passes 2 and 3 of each from the shared spectrum p->w_in)
+    const int run = p->run_passes;
     if (p->io == CONV_IO_R2R) {
         a.tpt = R.tpt;
         a.in = u;
@@ -788,16 +795,19 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.stage_len = R.stage;
         a.pf = R.pf && al(u, 16) && (n * sizeof(T)) % 16 == 0;
         tma_map(R, ws, n);
-        WSC_LAUNCH_PP(R, kf_r2r_rows_fwd);
+        if (run & 1) WSC_LAUNCH_PP(R, kf_r2r_rows_fwd);
         if (ev) cudaEventRecord(ev[1], st);
         a.tpt = C.tpt;
-        a.in = ws;
+        a.in = p->w_in ? p->w_in : ws;
+        a.out = ws;
         a.units = batch * h;
         a.stage_len = C.stage;
-        a.pf = pf_cols;
+        a.pf = pf_cols && al(a.in, 16);
         a.tma = 0;
-        WSC_LAUNCH_PP(C, kf_r2r_cols);
+        if (run & 2) WSC_LAUNCH_PP(C, kf_r2r_cols);
         if (ev) cudaEventRecord(ev[2], st);
+        if (!(run & 4)) goto launched;
+        a.in = ws;
         a.tpt = I.tpt;
         a.out = out;
         a.units = batch * ((n + 1) / 2);
@@ -814,27 +824,30 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         a.stage_len = R.stage;
         a.pf = R.pf && al(u, 16) && (n * sizeof(T)) % 16 == 0;
         tma_map(R, ws, n);
-        WSC_LAUNCH_PP(R, kf_r2r_rows_fwd);
+        if (run & 1) WSC_LAUNCH_PP(R, kf_r2r_rows_fwd);
         if (ev) cudaEventRecord(ev[1], st);
         // W2 follows W on the next even element (the workspace holds batch (3 h n + 1) values)
         V *W2 = reinterpret_cast<V *>(ws) + (((size_t)batch * h * n + 1) & ~(size_t)1);
         a.tpt = C.tpt;
-        a.in = ws;
+        a.in = p->w_in ? p->w_in : ws;
         a.out = W2;
         a.units = batch * h;
         a.stage_len = C.stage;
-        a.pf = pf_cols;
+        a.pf = pf_cols && al(a.in, 16);
         a.tma = 0;
         a.vec = al(W2, 16);
         if constexpr (split_one_ed(ED)) {
             // one buffer per group: the scratch lines follow W2 (batch (3 h n + 1) values in all)
             a.scratch = reinterpret_cast<V *>(ws) + (((size_t)batch * (3 * (size_t)h * n + 1) + 1) & ~(size_t)1);
-            if (C.one) WSC_LAUNCH2(C, kf_r2c_cols, (T, E, ED), true);
-            else WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
+            if (run & 2) {
+                if (C.one) WSC_LAUNCH2(C, kf_r2c_cols, (T, E, ED), true);
+                else WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
+            }
         } else {
-            WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
+            if (run & 2) WSC_LAUNCH(C, kf_r2c_cols, (T, E, ED));
         }
         if (ev) cudaEventRecord(ev[2], st);
+        if (!(run & 4)) goto launched;
         a.tpt = I.tpt;
         a.in = W2;
         a.out = out;
@@ -879,6 +892,7 @@ conv_status run_fused(conv_plan_s *p, const void *u, const void *mask, void *out
         else
             WSC_LAUNCH2(I, kf_c2c_rows_inv, (T, E, ED), false);
     }
+launched:
     if (ev) cudaEventRecord(ev[3], st);
 #undef WSC_LAUNCH_PP
 #undef WSC_LAUNCH2

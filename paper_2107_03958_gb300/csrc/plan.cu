@@ -551,6 +551,107 @@ conv_status conv_apply_kernels(conv_plan_t shape, const conv_plan_t *plans, cons
     return rc;
 }
 
+}  // extern "C"
+
+namespace wsc {
+
+// The plans of one conv_apply_multi: the same grid, precision, embedding and pass-1 configuration,
+// each R2R or split R2C (both start with the R2R row-pair pass into W[k2][j1]).
+static conv_status check_multi(const conv_plan_t *plans, int count)
+{
+    if (!plans || count < 1) return fail(CONV_EINVAL, "conv_apply_multi: plans is NULL or count < 1");
+    const conv_plan_s *p0 = plans[0];
+    for (int k = 0; k < count; ++k) {
+        const conv_plan_s *q = plans[k];
+        if (!q) return fail(CONV_EINVAL, "conv_apply_multi: a plan in the list is NULL");
+        if (!q->fused || q->long_lines || !(q->io == CONV_IO_R2R || q->r2c_split))
+            return fail(CONV_EUNSUPPORTED, "conv_apply_multi: every plan must run the fused R2R or split R2C passes");
+        if (q->timing) return fail(CONV_EINVAL, "conv_apply_multi: per-pass timing is on");
+        if (q->n != p0->n || q->Mb != p0->Mb || q->M != p0->M || q->prec != p0->prec || q->compact != p0->compact ||
+            q->device != p0->device || q->ed != p0->ed || q->elems != p0->elems || q->rows.tpt != p0->rows.tpt ||
+            q->rows.groups != p0->rows.groups)
+            return fail(CONV_EINVAL, "conv_apply_multi: every plan must share n, period, precision, embedding "
+                                     "and row-pass configuration");
+        for (int j = 0; j < k; ++j)
+            if (plans[j] == q) return fail(CONV_EINVAL, "conv_apply_multi: a plan appears twice");
+    }
+    return CONV_OK;
+}
+
+static size_t multi_w0_bytes(const conv_plan_s *p, int batch)
+{
+    const size_t esz = p->prec == CONV_P_FP64 ? 16 : 8;
+    return ((size_t)batch * p->h * p->n * esz + 255) & ~(size_t)255;
+}
+
+static size_t multi_ws_bytes(const conv_plan_t *plans, int count, int batch)
+{
+    size_t region = 0;
+    for (int k = 0; k < count; ++k) region = std::max(region, workspace_bytes(plans[k], batch));
+    return multi_w0_bytes(plans[0], batch) + region;
+}
+
+}  // namespace wsc
+
+extern "C" {
+
+conv_status conv_multi_workspace_size(const conv_plan_t *plans, int count, int batch, size_t *bytes)
+{
+    if (!bytes || batch < 0) return fail(CONV_EINVAL, "bad argument");
+    conv_status rc = check_multi(plans, count);
+    if (rc != CONV_OK) return rc;
+    *bytes = batch > 0 ? multi_ws_bytes(plans, count, batch) : 0;
+    return CONV_OK;
+}
+
+conv_status conv_apply_multi(const conv_plan_t *plans, int count, const void *u, const void *mask,
+                             void *const *outs, int batch, void *workspace, void *stream)
+{
+    conv_status rc = check_multi(plans, count);
+    if (rc != CONV_OK) return rc;
+    if (!outs) return fail(CONV_EINVAL, "conv_apply_multi: outs is NULL");
+    if (batch < 0) return fail(CONV_EINVAL, "batch must be >= 0");
+    if (batch == 0) return CONV_OK;
+    for (int k = 0; k < count; ++k) {
+        void *ignore = nullptr;
+        rc = check_apply(plans[k], u, mask, outs[k], batch, 0.0, workspace, &ignore);
+        if (rc != CONV_OK) return rc;
+        for (int j = 0; j < k; ++j)
+            if (outs[j] == outs[k]) return fail(CONV_EINVAL, "conv_apply_multi: two outputs alias");
+    }
+    int dev = 0;
+    WSC_CUDA(cudaGetDevice(&dev));
+    if (dev != plans[0]->device) return fail(CONV_EINVAL, "the current device is not the plans' device");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // without a caller's workspace: one from the memory pool, returned to it in stream order
+    void *ws = workspace;
+    const size_t need = multi_ws_bytes(plans, count, batch);
+    if (!ws && dev_alloc(&ws, need) != cudaSuccess) return fail(CONV_ENOMEM, "conv_apply_multi workspace");
+    char *W0 = static_cast<char *>(ws);
+    void *region = W0 + multi_w0_bytes(plans[0], batch);
+    // pass 1 once, into W0; then passes 2 and 3 of each plan from W0, in its own region
+    conv_plan_s *p0 = plans[0];
+    p0->run_passes = 1;
+    rc = launch_pipeline(p0, u, mask, outs[0], batch, 1.0, 0.0, 0.0, W0, st);
+    p0->run_passes = 7;
+    for (int k = 0; k < count && rc == CONV_OK; ++k) {
+        conv_plan_s *q = plans[k];
+        q->run_passes = 6;
+        q->w_in = W0;
+        rc = launch_pipeline(q, u, mask, outs[k], batch, 1.0, 0.0, 0.0, region, st);
+        q->run_passes = 7;
+        q->w_in = nullptr;
+    }
+    if (!workspace) {
+        if (cudaFreeAsync(ws, st) != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamSynchronize(st);
+            dev_free(ws);
+        }
+    }
+    return rc;
+}
+
 conv_status conv_get_info(conv_plan_t p, conv_plan_info *info)
 {
     if (!p || !info) return fail(CONV_EINVAL, "bad argument");

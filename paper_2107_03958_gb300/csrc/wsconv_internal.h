@@ -107,6 +107,8 @@ struct conv_plan_s {
     conv_moments moments{};  // how ghat is computed (closed forms by default)
     bool r2c_split = false;  // R2C with complex ghat on the split pipeline (fused passes)
     size_t split_scratch_elems = 0;  // split pass 2 with one buffer per CTA: its global lines
+    int run_passes = 7;              // passes a launch runs (bits 1, 2, 4); conv_apply_multi only
+    const void *w_in = nullptr;      // pass 2's input spectrum when not the workspace (conv_apply_multi)
     int device;
     cudaStream_t setup_stream = nullptr;  // private stream for plan-time device work
     int elems;  // complex elements per thread in the transform kernels
