@@ -84,17 +84,43 @@ __device__ double pow_moment_cc(double gamma, double s, double a)
 // by panel Clenshaw-Curtis.  The nodes' H0(kappa a u^4) do not depend on s; k_helm_band_table
 // tabulates them once per plan (tab: per node u, weight, Re H0, Im H0), so only J0 is evaluated
 // here.
-__device__ double2 helm_moment_cc(const double *__restrict__ tab, int nodes, double s, double a)
+// Entries in the resonance band |s - kappa| < HELM_BAND kappa, k1 >= k2 (k_ghat leaves them, and
+// their mirrors, to this kernel): one warp per entry, the lanes taking every 32nd node of the
+// table, the partial sums combined by shuffles.  Block k2 covers the band's k1 range of row k2.
+__global__ void k_ghat_band(double kappa, double scale, double b, double a, int h, double *out,
+                            const double *__restrict__ tab, int nodes)
 {
-    double sr = 0.0, si = 0.0;
-    for (int i = 0; i < nodes; ++i) {
-        const double u = tab[4 * i], u4 = u * u * u * u;
-        const double w = tab[4 * i + 1] * j0(s * a * u4) * u4 * u * u * u;
-        sr += w * tab[4 * i + 2];
-        si += w * tab[4 * i + 3];
+    const int k2 = blockIdx.x;
+    if (k2 >= h) return;
+    const double kr = kappa * b / (2.0 * M_PI);  // |k| where s = kappa
+    const double rlo = kr * (1.0 - HELM_BAND), rhi = kr * (1.0 + HELM_BAND), k2d = (double)k2;
+    const int lo = max(k2, (int)floor(sqrt(fmax(0.0, rlo * rlo - k2d * k2d))) - 1);
+    const int hi = min(h - 1, (int)ceil(sqrt(fmax(0.0, rhi * rhi - k2d * k2d))) + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k1 = lo + warp; k1 <= hi; k1 += nw) {
+        // the same test as k_ghat's, on the same arithmetic
+        const double km = hypot((double)k1, k2d);
+        const double s = 2.0 * M_PI * km / b;
+        if (km == 0.0 || !(fabs(s - kappa) < HELM_BAND * kappa)) continue;
+        double sr = 0.0, si = 0.0;
+        for (int i = lane; i < nodes; i += 32) {
+            const double u = tab[4 * i], u4 = u * u * u * u;
+            const double w = tab[4 * i + 1] * j0(s * a * u4) * u4 * u * u * u;
+            sr += w * tab[4 * i + 2];
+            si += w * tab[4 * i + 3];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+            const double c = 2.0 * M_PI * a * a;
+            const long long idx = (long long)k2 * h + k1, mirror = (long long)k1 * h + k2;
+            out[2 * idx] = out[2 * mirror] = scale * (-c * si);
+            out[2 * idx + 1] = out[2 * mirror + 1] = scale * (c * sr);
+        }
     }
-    const double c = 2.0 * M_PI * a * a;
-    return make_double2(-c * si, c * sr);
 }
 
 // The band quadrature's node table (per node u, weight, Re H0, Im H0 of H0(kappa a u^4)): P
@@ -115,9 +141,10 @@ __global__ void k_helm_band_table(double *__restrict__ tab, int P, double ka)
     }
 }
 
-// hka = (J0, Y0, J1, Y1)(kappa a), tabulated on the host.
+// hka = (J0, Y0, J1, Y1)(kappa a), tabulated on the host.  Helmholtz entries in the resonance band
+// are left to k_ghat_band.
 __global__ void k_ghat(int family, double gamma, double kappa, double scale, double b, double a,
-                       int h, double *out, double4 hka, const double *__restrict__ htab, int hnodes)
+                       int h, double *out, double4 hka)
 {
     const long long N = (long long)h * h;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
@@ -161,7 +188,7 @@ __global__ void k_ghat(int family, double gamma, double kappa, double scale, dou
                 double c = M_PI / (2.0 * kappa);
                 r = make_double2(c * (-a * hka.w - 2.0 / (kappa * M_PI)), c * a * hka.z);
             } else if (fabs(s - kappa) < HELM_BAND * kappa) {
-                r = helm_moment_cc(htab, hnodes, s, a);
+                continue;  // k_ghat_band
             } else {
                 // (i pi/2) (z J1(z) H0(ka) - ka J0(z) H1(ka) - 2i/pi) / (s^2 - kappa^2)
                 double J0z = j0(z), J1z = j1(z);
@@ -281,8 +308,10 @@ conv_status build_ghat(conv_plan_s *p)
     if (closed) {
         int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
         k_ghat<<<blocks, 256, 0, st>>>(p->kern.family, p->kern.gamma, p->kern.kappa, scale, p->b, p->a, hb,
-                                       p->ghat_paper, hka, htab, hnodes);
-        if (htab) cudaFreeAsync(htab, st);  // in stream order, after the kernel that reads it
+                                       p->ghat_paper, hka);
+        if (htab)  // the resonance band's entries
+            k_ghat_band<<<hb, 256, 0, st>>>(p->kern.kappa, scale, p->b, p->a, hb, p->ghat_paper, htab, hnodes);
+        if (htab) cudaFreeAsync(htab, st);  // in stream order, after the kernels that read it
         WSC_CUDA(cudaGetLastError());
     } else {
         conv_status rc = build_moments_numeric(p, scale, p->ghat_paper, st);
