@@ -68,3 +68,37 @@ def test_fault_injection_arguments_are_checked():
     assert lib.conv_fault_inject(N.FAULT["alloc"], -1) == 1
     for k in N.FAULT.values():
         assert lib.conv_fault_inject(k, 0) == 0
+
+
+def test_committed_traffic_records_match_the_current_kernels():
+    """The dominant kernels' traffic records in profiles/ were taken on the current pass-kernel
+    sources (so the benchmark reports them), and each record's algorithmic bytes are the column
+    pass's byte model: read and write the batch's n x (L/2 + 1) spectra, read the multiplier
+    quadrant once."""
+    import types
+    import bench
+    for prec, esz in (("fp64", 16), ("fp32", 8)):
+        name = "kf_r2r_cols_%s_compact_n4096.txt" % prec
+        assert bench.recorded_traffic(name) is not None, name
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        alg = int(next(l.split(":", 1)[1] for l in text.splitlines() if l.startswith("algorithmic_bytes_per_launch")))
+        n, L, B = 4096, 8192, 16
+        h = L // 2 + 1
+        assert alg == B * 2 * h * n * esz + h * h * (esz // 2)
+        fake = types.SimpleNamespace(n=n, precision=prec, info=types.SimpleNamespace(transform_len=L))
+        assert bench.r2r_bytes(fake, B) == alg
+
+
+def test_period3_schedule_bytes():
+    """The effective-bandwidth view: FP32 65 n^2 per R2R convolution and 102 n^2 per Helmholtz
+    one; the column pass 24 n^2 per density plus a 9 n^2 quadrant per launch; FP64 twice."""
+    import bench
+    n, B = 4096, 16
+    v32 = bench.period3_view(n, B, "fp32", col_ms=1.0, step_ms=1.0, hbm=1000.0)
+    v64 = bench.period3_view(n, B, "fp64", col_ms=1.0, step_ms=1.0, hbm=1000.0)
+    nn = n * n
+    assert v32["col_bytes_per_launch"] == (24 * B + 9) * nn
+    assert v32["step_bytes"] == B * (4 * 65 + 102) * nn
+    assert v64["step_bytes"] == 2 * v32["step_bytes"]
+    assert abs(v32["col_gbs"] - v32["col_bytes_per_launch"] / 1e-3 / 1e9) < 1e-6
+    assert abs(v32["step_frac"] - v32["step_gbs"] / 1000.0) < 1e-12
