@@ -264,22 +264,22 @@ def workload_config(args):
 
 
 # ---------------------------------------------------------------- GPU legs
-def make_plans(n, batch, precision, compact):
+def make_plans(n, batch, precision, compact, period=3):
     from paper_2107_03958_gb300.api import ConvPlan
     plans = []
     for kern, kw in SWEEP:
         io = "r2c" if kern == "helmholtz" else "r2r"
-        plans.append(ConvPlan(kern, n=n, period=3, precision=precision, io=io, batch_max=batch,
+        plans.append(ConvPlan(kern, n=n, period=period, precision=precision, io=io, batch_max=batch,
                               compact=compact, **kw))
     return plans
 
 
-def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, compact=True):
+def sweep_leg(n, batch, precision, steps, warmup, stream, timing=False, compact=True, period=3):
     """Time `steps` sweeps on device-resident inputs; returns dict with ms/step and the pass
     timings of the plans."""
     import torch
     from paper_2107_03958_gb300 import inputs
-    plans = make_plans(n, batch, precision, compact)
+    plans = make_plans(n, batch, precision, compact, period)
     dt = torch.float64 if precision == "fp64" else torch.float32
     u = torch.from_numpy(inputs.bump_sums(n, batch)).to(dt).cuda()
     outs = [torch.empty((batch, n, n), dtype=p.out_dtype(), device="cuda") for p in plans]
@@ -927,6 +927,21 @@ def main():
             "roofline_cols": {"bound": "hbm", "achieved": bpb / (cpb * 1e-3) / 1e9, "peak": hbm,
                               "unit": "GB/s", "frac": bpb / (cpb * 1e-3) / 1e9 / hbm,
                               "algorithmic_bytes_per_launch": bpb, "avg_launch_ms": cpb}}
+        # the non-integer period b = 5/2 (M = 2.5 n = 10240: radix-5 runtime stages), FP32
+        p25 = sweep_leg(args.n, args.batch, "fp32", kb, args.warmup, stream, timing=True, compact=False,
+                        period=2.5)
+        p25_ms = max_over_ranks(ws, p25["ms"])
+        r25 = [(p, t) for p, t in zip(p25["plans"], p25["passes"]) if p.io == "r2r"]
+        c25 = sum(t[0][1] for _, t in r25) / sum(t[1] for _, t in r25)
+        b25 = r2r_bytes(r25[0][0], args.batch)
+        extras["fp32_period_2.5"] = {
+            "value": job_throughput(ws, 5 * args.batch * kb, p25_ms), "unit": "conv/s", "steps": kb,
+            "ms_per_step": p25_ms / kb, "transform_len": r25[0][0].info.transform_len,
+            "roofline_cols": {"bound": "hbm", "achieved": b25 / (c25 * 1e-3) / 1e9, "peak": hbm,
+                              "unit": "GB/s", "frac": b25 / (c25 * 1e-3) / 1e9 / hbm,
+                              "algorithmic_bytes_per_launch": b25, "avg_launch_ms": c25}}
+        del p25, r25
+        torch.cuda.empty_cache()
         n2 = args.n // 2
         l2 = sweep_leg(n2, args.batch, "fp32", args.steps, args.warmup, stream)
         l2_ms = max_over_ranks(ws, l2["ms"])
