@@ -186,13 +186,79 @@ template <bool INV, typename V> __device__ __forceinline__ V cmulc(V x, decltype
     return cmk<V>(x.x * a - x.y * b, x.x * b + x.y * a);
 }
 
+// x (1 - i) (forward) or x (1 + i) (inverse): w16^2 without its 1/sqrt 2
+template <bool INV, typename V> __device__ __forceinline__ V q1(V x)
+{
+    return INV ? cmk<V>(x.x - x.y, x.x + x.y) : cmk<V>(x.x + x.y, x.y - x.x);
+}
+// x (-1 - i) (forward) or x (-1 + i) (inverse): w16^6 without its 1/sqrt 2
+template <bool INV, typename V> __device__ __forceinline__ V q3(V x)
+{
+    return INV ? cmk<V>(-(x.x + x.y), x.x - x.y) : cmk<V>(x.y - x.x, -(x.x + x.y));
+}
+// a + s b and a - s b, componentwise fused
+template <typename V> __device__ __forceinline__ V cfma(V a, decltype(V::x) s, V b)
+{
+    return cmk<V>(fma(s, b.x, a.x), fma(s, b.y, a.y));
+}
+template <typename V> __device__ __forceinline__ V cfms(V a, decltype(V::x) s, V b)
+{
+    return cmk<V>(fma(-s, b.x, a.x), fma(-s, b.y, a.y));
+}
+
 // 16 points as 4 x 4: length-4 transforms over n = r + 4t (t), twiddles w16^{r m}, length-4
 // transforms over r; X[m + 4 s] = sum_r w4^{r s} w16^{r m} sum_t w4^{t m} x[r + 4t].
-template <bool INV, typename V> __device__ __forceinline__ void dft16(V *x) {
+// dft16_layer2 does the twiddles and the second layer from y[r][m].  Four of its twiddles,
+// w16^2 and w16^6 (twice each), are (1 - i)/sqrt 2 and (-1 - i)/sqrt 2: their rotation is two
+// additions (q1, q3) and their 1/sqrt 2 rides in the second layer's sums as fused multiply-adds,
+// instead of two products and two multiply-adds each.
+template <bool INV, typename V> __device__ __forceinline__ void dft16_layer2(V (*y)[4], V *x)
+{
     typedef decltype(V::x) T;
     const T c = (T)0.9238795325112867561281831893967882;   // cos(pi/8)
     const T s = (T)0.3826834323650897717284599840303989;   // sin(pi/8)
     const T r2 = (T)0.7071067811865475244008443621048490;  // cos(pi/4)
+    {   // m = 0: no twiddles
+        V z[4] = {y[0][0], y[1][0], y[2][0], y[3][0]};
+        dft4<INV>(z);
+        x[0] = z[0];
+        x[4] = z[1];
+        x[8] = z[2];
+        x[12] = z[3];
+    }
+    {   // m = 1: w16^{r}: (c, -s), (r2, -r2) = w16^2, (s, -c)
+        const V z0 = y[0][1], z1 = cmulc<INV>(y[1][1], c, -s), z3 = cmulc<INV>(y[3][1], s, -c);
+        const V u2 = q1<INV>(y[2][1]);
+        const V a0 = cfma(z0, r2, u2), a1 = cfms(z0, r2, u2);
+        const V a2 = cadd(z1, z3), a3 = rot<INV>(csub(z1, z3));
+        x[1] = cadd(a0, a2);
+        x[9] = csub(a0, a2);
+        x[5] = cadd(a1, a3);
+        x[13] = csub(a1, a3);
+    }
+    {   // m = 2: w16^{2r}: w16^2, -i, w16^6
+        const V z0 = y[0][2], z2 = rot<INV>(y[2][2]);
+        const V u1 = q1<INV>(y[1][2]), u3 = q3<INV>(y[3][2]);
+        const V a0 = cadd(z0, z2), a1 = csub(z0, z2);
+        const V v2 = cadd(u1, u3), v3 = rot<INV>(csub(u1, u3));
+        x[2] = cfma(a0, r2, v2);
+        x[10] = cfms(a0, r2, v2);
+        x[6] = cfma(a1, r2, v3);
+        x[14] = cfms(a1, r2, v3);
+    }
+    {   // m = 3: w16^{3r}: (s, -c), (-r2, -r2) = w16^6, (-c, s)
+        const V z0 = y[0][3], z1 = cmulc<INV>(y[1][3], s, -c), z3 = cmulc<INV>(y[3][3], -c, s);
+        const V u2 = q3<INV>(y[2][3]);
+        const V a0 = cfma(z0, r2, u2), a1 = cfms(z0, r2, u2);
+        const V a2 = cadd(z1, z3), a3 = rot<INV>(csub(z1, z3));
+        x[3] = cadd(a0, a2);
+        x[11] = csub(a0, a2);
+        x[7] = cadd(a1, a3);
+        x[15] = csub(a1, a3);
+    }
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft16(V *x) {
     V y[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -202,34 +268,12 @@ template <bool INV, typename V> __device__ __forceinline__ void dft16(V *x) {
         y[r][3] = x[r + 12];
         dft4<INV>(y[r]);  // y[r][m], m = 0..3
     }
-    // w16^{r m}: forward w16 = e^{-i pi/8}
-    y[1][1] = cmulc<INV>(y[1][1], c, -s);
-    y[1][2] = cmulc<INV>(y[1][2], r2, -r2);
-    y[1][3] = cmulc<INV>(y[1][3], s, -c);
-    y[2][1] = cmulc<INV>(y[2][1], r2, -r2);
-    y[2][2] = rot<INV>(y[2][2]);
-    y[2][3] = cmulc<INV>(y[2][3], -r2, -r2);
-    y[3][1] = cmulc<INV>(y[3][1], s, -c);
-    y[3][2] = cmulc<INV>(y[3][2], -r2, -r2);
-    y[3][3] = cmulc<INV>(y[3][3], -c, s);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        V z[4] = {y[0][m], y[1][m], y[2][m], y[3][m]};
-        dft4<INV>(z);
-        x[m] = z[0];
-        x[m + 4] = z[1];
-        x[m + 8] = z[2];
-        x[m + 12] = z[3];
-    }
+    dft16_layer2<INV>(y, x);
 }
 
 // dft16 of x[0..7] followed by eight zeros (the first stage of a zero-extended transform):
 // the first layer's length-4 transforms see (x[r], x[r+4], 0, 0).
 template <bool INV, typename V> __device__ __forceinline__ void dft16_half_in(V *x) {
-    typedef decltype(V::x) T;
-    const T c = (T)0.9238795325112867561281831893967882;
-    const T s = (T)0.3826834323650897717284599840303989;
-    const T r2 = (T)0.7071067811865475244008443621048490;
     V y[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -239,24 +283,7 @@ template <bool INV, typename V> __device__ __forceinline__ void dft16_half_in(V 
         y[r][2] = csub(a, b);
         y[r][3] = csub(a, rb);
     }
-    y[1][1] = cmulc<INV>(y[1][1], c, -s);
-    y[1][2] = cmulc<INV>(y[1][2], r2, -r2);
-    y[1][3] = cmulc<INV>(y[1][3], s, -c);
-    y[2][1] = cmulc<INV>(y[2][1], r2, -r2);
-    y[2][2] = rot<INV>(y[2][2]);
-    y[2][3] = cmulc<INV>(y[2][3], -r2, -r2);
-    y[3][1] = cmulc<INV>(y[3][1], s, -c);
-    y[3][2] = cmulc<INV>(y[3][2], -r2, -r2);
-    y[3][3] = cmulc<INV>(y[3][3], -c, s);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        V z[4] = {y[0][m], y[1][m], y[2][m], y[3][m]};
-        dft4<INV>(z);
-        x[m] = z[0];
-        x[m + 4] = z[1];
-        x[m + 8] = z[2];
-        x[m + 12] = z[3];
-    }
+    dft16_layer2<INV>(y, x);
 }
 
 template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x) {
